@@ -1,0 +1,226 @@
+/*
+ * lns.h -- C ABI of the GB300 localized Newton solver (liblns.so).
+ *
+ * The library advances an oil-water fully implicit finite-volume model on a matrix +
+ * discrete-fracture-network connection graph by Newton's method, with the localized
+ * variants of Jiang, "Localized Nonlinear Solution Strategies for Efficient Simulation
+ * of Unconventional Reservoirs" (arXiv 2008.01539):
+ *   - standard Newton (Section 4.1),
+ *   - localized Newton, Algorithm 1 (Section 4.3),
+ *   - adaptive nonlinear domain decomposition, Algorithm 2 (Section 4.4).
+ * Every step of a Newton iteration runs in the library's CUDA kernels for sm_103a: the
+ * a-priori active-set estimate, compaction of the active cells, masked residual and
+ * Jacobian assembly (Appendix A), the BiCGStab solve of J_A du_A = -F_A and the scatter
+ * of the update.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns lns_status; no exception crosses the ABI.  On failure
+ *     lns_last_error() returns a message for the calling thread.
+ *   - Array arguments are plain pointers.  They are HOST pointers unless the argument
+ *     list says otherwise (a *_on_device flag).  Inputs are read during the call and
+ *     not retained; outputs are caller-allocated.
+ *   - Units are SI: Pa, m, m^2, m^3, Pa s, s.
+ *   - Bitsets are arrays of ceil(n/32) little-endian uint32 words, bit (i & 31) of word
+ *     (i >> 5) standing for cell i.
+ *   - Work is enqueued on the model's CUDA stream; every call below returns after that
+ *     work has completed (it synchronizes the stream).
+ *   - A model may be used by one host thread at a time.
+ */
+#ifndef LNS_H
+#define LNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lns_model lns_model; /* opaque, owned by the library */
+
+typedef enum {
+  LNS_OK = 0,
+  LNS_EINVAL = -1,   /* invalid argument (null pointer, size out of range, bad option) */
+  LNS_ENOMEM = -2,   /* device allocation failed */
+  LNS_ECUDA = -3,    /* a CUDA runtime call or kernel failed (message in lns_last_error) */
+  LNS_ENOCONV = -4,  /* Newton loop reached max_newton (or Algorithm 2 max_dd_outer) */
+  LNS_EKRYLOV = -5,  /* BiCGStab broke down or reached krylov_maxit above krylov_fail_rtol */
+  LNS_ETIMEOUT = -6, /* reserved: a bounded device-side wait gave up */
+  LNS_ESTATE = -7    /* call not valid in the model's current state */
+} lns_status;
+
+enum { LNS_MODE_FULL = 0, LNS_MODE_LOCAL = 1, LNS_MODE_DD = 2 };
+enum { LNS_PRECOND_BJAC = 0 /* block Jacobi; fracture segments as block-tridiagonal blocks */ };
+
+/* Fluid and rock.  b_l(p) = b_l_ref (1 + c_l (p - p_ref)) (inverse formation volume
+ * factor), rho_l = rho_l_ref b_l, pore volume PV_ref (1 + c_r (p - p_ref)), Corey
+ * relative permeabilities k_rw = Se^n_w, k_ro = (1 - Se)^n_o, Se = (Sw - Swc)/(1 - Swc - Sor)
+ * clamped to [0, 1], integer exponents 1..8.  (Appendix A reduced to two phases.) */
+typedef struct {
+  double p_ref, c_r, b_o_ref, c_o, b_w_ref, c_w, rho_o_ref, rho_w_ref, mu_o, mu_w, swc, sor;
+  int32_t n_w, n_o;
+  double gravity;
+} lns_fluid;
+
+/* Model description (Section 5 models; Appendix A TPFA).  The connection graph is CSR:
+ * row i lists the neighbours of cell i in ascending order, and every connection is stored
+ * at both endpoints with the same transmissibility.  Cells of one fracture segment are
+ * numbered consecutively along the segment and carry the same line_id (>= 0; -1 for
+ * matrix cells).  always_active marks cells never dropped from the active set (the paper
+ * keeps fractures active, Section 5.2.3; wells too).  All arrays are host, copied at create. */
+typedef struct {
+  int32_t n_cells;
+  int32_t n_adj;              /* number of CSR entries (twice the connections) */
+  const int32_t* row_ptr;     /* [n_cells + 1] */
+  const int32_t* nbr;         /* [n_adj] */
+  const double* trans;        /* [n_adj] transmissibility T_ij (m^3) */
+  const double* pv_ref;       /* [n_cells] pore volume at p_ref (m^3) */
+  const double* depth;        /* [n_cells] cell-centre depth, positive down (m) */
+  const int32_t* line_id;     /* [n_cells] fracture segment id or -1 */
+  const uint8_t* always_active; /* [n_cells] 0/1 */
+  int32_t n_wells;
+  const int32_t* well_cell;   /* [n_wells] producer perforation cell */
+  const double* well_wi;      /* [n_wells] well index (m^3) */
+  const double* well_bhp;     /* [n_wells] bottom-hole pressure (Pa) */
+  lns_fluid fluid;
+  const double* p0;           /* [n_cells] initial pressure */
+  const double* sw0;          /* [n_cells] initial water saturation */
+} lns_model_desc;
+
+/* Solver options.  Convergence of an iteration (Section 5: pressure increment; plus the
+ * scaled mass residual): max |dp| < tol_dp and CNV = max_{i,l} |R_l,i| dt / (PV_i b_l,i)
+ * < tol_cnv over the rows solved.  eps_p / eps_sw: the cutoff epsilon of the support set
+ * supp du = {i : |du_i| >= eps} (Section 4.1) on pressure and (if > 0) saturation. */
+typedef struct {
+  int32_t mode;          /* LNS_MODE_* */
+  double eps_p;          /* Pa */
+  double eps_sw;         /* <= 0 disables the saturation cutoff */
+  int32_t m_layers;      /* m of the neighbour set V_nbr^{i,m} (connection hops) */
+  double tol_dp;         /* Pa */
+  double tol_cnv;
+  int32_t max_newton;    /* iterations per timestep (Algorithm 2: expansion solves) */
+  int32_t max_dd_outer;  /* Algorithm 2 outer passes */
+  double sat_chop;       /* |dSw| limit per update; <= 0: none */
+  int32_t krylov_fp32;   /* 1: BiCGStab and Jacobian blocks in FP32 (inexact Newton) */
+  int32_t precond;       /* LNS_PRECOND_* */
+  double krylov_rtol;    /* stop when ||r|| <= krylov_rtol ||b|| (scaled system) */
+  int32_t krylov_maxit;
+  double krylov_fail_rtol; /* at krylov_maxit, fail with LNS_EKRYLOV if ||r||/||b|| is above this */
+  double p_scale;        /* pressure unknown scaling for the Krylov norm (1/Pa); <= 0: c_r + c_o */
+  int32_t profile;       /* 1: time every kernel class with CUDA events (lns_kernel_times) */
+} lns_options;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
+ * device pointer of at least `bytes` bytes (256-byte aligned) or NULL; free releases it.
+ * `stream` is the model's stream.  A NULL allocator means cudaMalloc / cudaFree. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*free)(void* ctx, void* ptr, void* stream);
+} lns_allocator;
+
+typedef struct {
+  int32_t n_active;      /* n_A of the iteration just done */
+  int32_t is_expand;     /* Algorithm 1 mode after the iteration */
+  int32_t converged;     /* convergence test of the iteration */
+  int32_t step_done;     /* the timestep closed after this iteration */
+  int32_t krylov_iters;
+  int32_t krylov_status; /* 0 ok, 1 max iterations, 2 breakdown */
+  double max_dp, max_dsw, cnv, krylov_relres;
+} lns_iter_stats;
+
+typedef struct {
+  int32_t status;        /* lns_status of the step */
+  int32_t iterations;    /* Newton iterations (Algorithm 2: local solves) */
+  int32_t krylov_iters;  /* summed over iterations */
+  int32_t n_subdomains;  /* Algorithm 2: N */
+  int32_t dd_outer;      /* Algorithm 2: outer passes */
+  int64_t cell_updates;  /* sum of n_A over iterations */
+  double last_max_dp, last_cnv;
+} lns_step_stats;
+
+typedef struct {
+  char name[24];
+  int64_t launches;
+  double total_ms;       /* summed CUDA-event durations */
+  double bytes;          /* algorithmic bytes moved, summed over launches */
+  double flops;          /* algorithmic FP64/FP32 flops, summed over launches */
+} lns_kernel_time;
+
+/* Default options: Algorithm 1, eps_p = tol_dp = 0.3 psi, m = 2, tol_cnv = 1e-6, FP64. */
+lns_status lns_options_default(lns_options* out);
+
+/* Copy the model to the device, set u = (p0, sw0).  cuda_stream: a cudaStream_t to run
+ * on (NULL: the legacy default stream).  allocator may be NULL.  The problem statement is
+ * Section 4.1: advance F(u^{n+1}) = 0 from u^n. */
+lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
+                            const lns_allocator* allocator, void* cuda_stream, lns_model** out);
+lns_status lns_model_destroy(lns_model* model);
+lns_status lns_set_options(lns_model* model, const lns_options* opts);
+
+/* One timestep u^n -> u^{n+1} of size dt (seconds) by the model's mode (Section 4.1;
+ * Algorithm 1 or 2).  On LNS_ENOCONV the state is left at the last iterate. */
+lns_status lns_timestep(lns_model* model, double dt, lns_step_stats* out);
+
+/* One Newton iteration of Algorithm 1 (or standard Newton): opens a timestep of size dt
+ * if none is open, runs lines 4-21 once, and closes the timestep once the loop condition
+ * (is_expand or not converged) is false.  Not available in LNS_MODE_DD. */
+lns_status lns_newton_iter(lns_model* model, double dt, lns_iter_stats* out);
+
+/* Algorithm 1, lines 8-20 (steps 3-4 of Section 4.3) on a caller-given update: with
+ * V_A = va_bits (in) and its boundary V_B, expand V_A by V_nbr^{i,m} of every boundary
+ * cell with |du_i| >= eps, or shrink it to supp du_A (fractures/wells kept; an empty
+ * support before convergence keeps V_A).  dp, dsw: [n_cells] update (entries outside V_A
+ * are ignored), host or device per du_on_device.  Outputs the new V_A (va_bits, in place),
+ * its boundary (vb_bits) and is_expand.  Bit-exact: pure integer/compare logic. */
+lns_status lns_active_set(lns_model* model, const double* dp, const double* dsw, int32_t du_on_device,
+                          int32_t converged, uint32_t* va_bits, uint32_t* vb_bits, int32_t* is_expand);
+
+/* Algorithm 2, lines 8-22: one expansion step of the dynamic partition build.  vb_k is the
+ * boundary set of the subdomain just solved, vt the total active set V_T (in/out).
+ * Outputs the next subdomain V_A^{k+1} = (union of V_nbr^{i,m}) minus the old V_T, its
+ * boundary set V_B^{k+1} = V_B(V_T) intersect V_A^{k+1}, its outer halo V_dB^{k+1}, and
+ * is_expand (0 when no boundary update is >= eps or no new cell was reached). */
+lns_status lns_dd_expand(lns_model* model, const double* dp, const double* dsw, int32_t du_on_device,
+                         const uint32_t* vb_k, uint32_t* vt, uint32_t* va_next, uint32_t* vb_next,
+                         uint32_t* vdb_next, int32_t* is_expand);
+
+/* One localized Newton step without changing the state: solve J_A du_A = -F_A
+ * (J_A = R_A J R_A^T, Section 4.3) at the current state u over V_A = va_bits, with the
+ * time level u^n set by lns_set_state, and return du (dp, dsw: [n_cells] host, zero
+ * outside V_A, saturation chop applied). */
+lns_status lns_solve_local(lns_model* model, double dt, const uint32_t* va_bits, double* dp, double* dsw,
+                           lns_iter_stats* out);
+
+/* The residual F_A and Jacobian blocks of the active rows at the current state
+ * (Appendix A).  F: [2 n_cells] (oil, water), Jd: [4 n_cells] diagonal blocks,
+ * Jo: [4 n_adj] off-diagonal blocks (row i, column nbr[e]); blocks row-major
+ * [dRo/dp, dRo/dSw, dRw/dp, dRw/dSw], FP64, unscaled.  Rows outside V_A and blocks of
+ * inactive columns are left untouched.  Any output may be NULL. */
+lns_status lns_assemble(lns_model* model, double dt, const uint32_t* va_bits, double* F, double* Jd,
+                        double* Jo);
+
+/* State transfer (host arrays of n_cells).  set_state sets u and the time level u^n
+ * (pn/swn NULL: u^n = u) and forgets the previous timestep's support. */
+lns_status lns_get_state(const lns_model* model, double* p, double* sw);
+lns_status lns_set_state(lns_model* model, const double* p, const double* sw, const double* pn,
+                         const double* swn);
+/* Device-to-device variants for device-resident callers (pointers are device memory). */
+lns_status lns_get_state_device(const lns_model* model, double* p, double* sw);
+/* Return to the initial state (p0, sw0) without host transfers; forget the support. */
+lns_status lns_reset(lns_model* model);
+/* The previous timestep's support set (the next step's initial active set before the
+ * always-active cells are added). */
+lns_status lns_get_support(const lns_model* model, uint32_t* bits);
+
+/* Kernel timing (options.profile = 1): up to cap entries, *count gets the number. */
+lns_status lns_kernel_times(const lns_model* model, lns_kernel_time* out, int32_t cap, int32_t* count);
+lns_status lns_reset_kernel_times(lns_model* model);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lns_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LNS_H */

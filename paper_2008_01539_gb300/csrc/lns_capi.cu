@@ -1,0 +1,1035 @@
+// lns_capi.cu -- C ABI and host driver of the localized Newton solver.
+//
+// The host side only sequences kernels and reads back one small counter block per Newton
+// iteration (n_A, convergence, expand/shrink, Krylov outcome); every step of the
+// iteration -- active-set estimate, compaction, assembly, BiCGStab, update scatter -- runs
+// in the kernels of k_sets.cu, k_assemble.cu and k_krylov.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lns_internal.cuh"
+
+using lns::Dev;
+using lns::IterCounters;
+using lns::LaunchCfg;
+
+namespace {
+thread_local std::string g_err;
+
+lns_status fail(lns_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail(LNS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(call)                   \
+  do {                              \
+    lns_status s_ = (call);         \
+    if (s_ != LNS_OK) return s_;    \
+  } while (0)
+
+enum KClass { KC_COMPACT = 0, KC_SETS, KC_ASSEMBLE, KC_LINES, KC_KRYLOV, KC_UPDATE, KC_COUNT };
+const char* kClassName[KC_COUNT] = {"compact", "active_set", "assemble", "line_setup", "bicgstab", "update"};
+
+struct PendingEvent {
+  int kc;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+
+}  // namespace
+
+struct lns_model {
+  Dev d{};
+  lns_options o{};
+  lns_allocator alloc{};
+  bool has_alloc = false;
+  cudaStream_t stream = nullptr;
+  int sms = 1;
+  int device = 0;
+  std::vector<void*> owned;
+  double avg_degree = 0.0;
+  int kgrid[2] = {0, 0};  // cooperative BiCGStab grid (FP64, FP32)
+  // timestep state
+  bool step_open = false;
+  double dt = 0.0;
+  int has_prev = 0;
+  int is_expand = 1;
+  int converged = 0;
+  lns_step_stats cur{};
+  // Algorithm 2 storage: per subdomain V_A^k, V_B^k, V_dB^k bitsets
+  std::vector<uint32_t*> dd_va, dd_vb, dd_vdb;
+  uint32_t* dd_vt = nullptr;
+  std::vector<uint32_t> stage;  // host staging of caller bitsets
+  // profiling
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<PendingEvent> pending;
+  lns_kernel_time kt[KC_COUNT]{};
+};
+
+namespace {
+
+LaunchCfg cfg(const lns_model* m) { return LaunchCfg{m->sms, m->stream}; }
+
+lns_status dalloc(lns_model* m, size_t bytes, void** out) {
+  bytes = std::max<size_t>(bytes, 256);
+  void* p = nullptr;
+  if (m->has_alloc) {
+    p = m->alloc.alloc(m->alloc.ctx, bytes, (void*)m->stream);
+    if (!p) return fail(LNS_ENOMEM, "device allocator returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(LNS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  m->owned.push_back(p);
+  *out = p;
+  return LNS_OK;
+}
+
+template <typename T>
+lns_status dalloc_t(lns_model* m, size_t count, T** out) {
+  void* p = nullptr;
+  TRY(dalloc(m, count * sizeof(T), &p));
+  *out = (T*)p;
+  return LNS_OK;
+}
+
+double eff_p_scale(const lns_model* m) {
+  if (m->o.p_scale > 0.0) return m->o.p_scale;
+  double c = m->d.fl.c_r + m->d.fl.c_o;
+  return c > 0.0 ? c : 1e-7;
+}
+
+// ---- profiling ----
+lns_status ev_begin(lns_model* m, int kc, PendingEvent* pe) {
+  pe->kc = kc;
+  pe->bytes = pe->flops = 0.0;
+  if (!m->o.profile) return LNS_OK;
+  if (m->ev_pool.size() < 2) {
+    for (int k = 0; k < 32; k++) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      m->ev_pool.push_back(e);
+    }
+  }
+  pe->a = m->ev_pool.back();
+  m->ev_pool.pop_back();
+  pe->b = m->ev_pool.back();
+  m->ev_pool.pop_back();
+  CK(cudaEventRecord(pe->a, m->stream));
+  return LNS_OK;
+}
+
+lns_status ev_end(lns_model* m, PendingEvent* pe, double bytes, double flops) {
+  if (!m->o.profile) return LNS_OK;
+  pe->bytes = bytes;
+  pe->flops = flops;
+  CK(cudaEventRecord(pe->b, m->stream));
+  m->pending.push_back(*pe);
+  return LNS_OK;
+}
+
+// After a stream synchronization: accumulate the recorded intervals.
+lns_status ev_flush(lns_model* m) {
+  for (auto& pe : m->pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, pe.a, pe.b));
+    lns_kernel_time& k = m->kt[pe.kc];
+    k.launches += 1;
+    k.total_ms += ms;
+    k.bytes += pe.bytes;
+    k.flops += pe.flops;
+    m->ev_pool.push_back(pe.a);
+    m->ev_pool.push_back(pe.b);
+  }
+  m->pending.clear();
+  return LNS_OK;
+}
+
+// Algorithmic traffic models (bytes and flops per launch) from the row count; sT = 8 or 4.
+double bytes_assemble(double nA, double deg, double sT) { return nA * (52.0 + 2 * sT + deg * (20.0 + 4 * sT)); }
+double flops_assemble(double nA, double deg) { return nA * (90.0 + deg * 60.0); }
+double bytes_krylov_iter(double nA, double deg, double sT) {
+  return nA * (2.0 * (12.0 + deg * (4.0 + 6.0 * sT) + 2.0 * sT) + 34.0 * sT);
+}
+double flops_krylov_iter(double nA, double deg) { return nA * (2.0 * (8.0 * deg + 2.0) + 70.0); }
+
+lns_status sync(lns_model* m) {
+  CK(cudaStreamSynchronize(m->stream));
+  return ev_flush(m);
+}
+
+lns_status read_counters(lns_model* m) {
+  CK(cudaMemcpyAsync(m->d.ctr_h, m->d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+  return sync(m);
+}
+
+double bits2d(unsigned long long b) {
+  double v;
+  std::memcpy(&v, &b, sizeof(v));
+  return v;
+}
+
+lns_status reset_iter(lns_model* m) {
+  const Dev& d = m->d;
+  CK(cudaMemsetAsync(d.ctr, 0, sizeof(IterCounters), m->stream));
+  CK(cudaMemsetAsync(d.supp, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+  CK(cudaMemsetAsync(d.reach, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+  return LNS_OK;
+}
+
+// Caller bitsets are copied with the bits past n_cells cleared, so no kernel sees a cell >= n.
+lns_status bits_to_device(lns_model* m, uint32_t* dst, const uint32_t* host) {
+  const int W = m->d.W, n = m->d.n;
+  if (W == 0) return LNS_OK;
+  m->stage.assign(host, host + W);
+  const int rem = n - 32 * (W - 1);
+  if (rem < 32) m->stage[W - 1] &= (1u << rem) - 1u;
+  CK(cudaMemcpyAsync(dst, m->stage.data(), sizeof(uint32_t) * (size_t)W, cudaMemcpyHostToDevice, m->stream));
+  CK(cudaStreamSynchronize(m->stream));  // the staging buffer is reused
+  return LNS_OK;
+}
+
+lns_status bits_to_host(lns_model* m, uint32_t* host, const uint32_t* src) {
+  CK(cudaMemcpyAsync(host, src, sizeof(uint32_t) * (size_t)m->d.W, cudaMemcpyDeviceToHost, m->stream));
+  return LNS_OK;
+}
+
+// Solve the local system on the set currently in d.va at the current state: compaction,
+// assembly, line factors, BiCGStab.  Leaves the Krylov solution in d.kx.
+lns_status local_solve(lns_model* m, int debug) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  const int fp32 = m->o.krylov_fp32;
+  PendingEvent pe;
+  TRY(ev_begin(m, KC_COMPACT, &pe));
+  CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, c));
+  TRY(ev_end(m, &pe, d.W * 4.0 * 2 + 0.0, 0.0));
+  TRY(ev_begin(m, KC_ASSEMBLE, &pe));
+  CK(lns::launch_assemble(d, m->dt, eff_p_scale(m), fp32, debug, c));
+  TRY(ev_end(m, &pe, 0.0, 0.0));
+  TRY(ev_begin(m, KC_LINES, &pe));
+  CK(lns::launch_line_setup(d, fp32, c));
+  TRY(ev_end(m, &pe, 0.0, 0.0));
+  TRY(ev_begin(m, KC_KRYLOV, &pe));
+  CK(lns::launch_bicgstab(d, fp32, m->o.krylov_rtol, m->o.krylov_maxit, m->kgrid[fp32 ? 1 : 0], c));
+  TRY(ev_end(m, &pe, 0.0, 0.0));
+  return LNS_OK;
+}
+
+// Fill in the byte/flop models of the events recorded by local_solve once n_A and the
+// Krylov iteration count are known (after the counter read-back).
+void annotate_pending(lns_model* m) {
+  const IterCounters& h = *m->d.ctr_h;
+  const double sT = m->o.krylov_fp32 ? 4.0 : 8.0;
+  const double nA = h.n_active;
+  for (auto& pe : m->pending) {
+    if (pe.kc == KC_ASSEMBLE) {
+      pe.bytes = bytes_assemble(nA, m->avg_degree, sT);
+      pe.flops = flops_assemble(nA, m->avg_degree);
+    } else if (pe.kc == KC_KRYLOV) {
+      pe.bytes = h.krylov_iters * bytes_krylov_iter(nA, m->avg_degree, sT);
+      pe.flops = h.krylov_iters * flops_krylov_iter(nA, m->avg_degree);
+    } else if (pe.kc == KC_UPDATE) {
+      pe.bytes = nA * (4.0 + 2 * sT + 48.0);
+      pe.flops = nA * 6.0;
+    }
+  }
+}
+
+lns_status krylov_outcome(lns_model* m) {
+  const IterCounters& h = *m->d.ctr_h;
+  if (h.krylov_status == 2) return fail(LNS_EKRYLOV, "BiCGStab breakdown");
+  if (h.krylov_status == 1 && !(h.krylov_relres <= m->o.krylov_fail_rtol))
+    return fail(LNS_EKRYLOV, "BiCGStab reached krylov_maxit with relative residual " + std::to_string(h.krylov_relres));
+  return LNS_OK;
+}
+
+// m rounds of frontier expansion of d.reach (frontier list 0 already seeded).  Rounds run in
+// chunks of 8; between chunks the frontier size is read and an empty frontier ends the
+// expansion early (so m larger than the graph diameter costs no more than the diameter).
+lns_status dilate(lns_model* m, int layers) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  int done = 0;
+  while (done < layers) {
+    const int chunk = std::min(8, layers - done);
+    CK(lns::launch_dilate(d, d.reach, chunk, c));
+    done += chunk;
+    if (done >= layers) break;
+    // chunk == 8 (even): the current frontier is list 0
+    int cnt = 0;
+    CK(cudaMemcpyAsync(&m->d.ctr_h->n_frontier[0], &d.ctr->n_frontier[0], sizeof(int), cudaMemcpyDeviceToHost,
+                       m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    cnt = m->d.ctr_h->n_frontier[0];
+    if (cnt == 0) break;
+  }
+  return LNS_OK;
+}
+
+// Initial active set of a timestep (Section 4.3 step 1, Section 5.2): previous step's
+// support plus always-active cells, or on the first step the always-active cells and their
+// m-layer neighbours.
+lns_status initial_set(lns_model* m, uint32_t* out) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  if (m->has_prev) {
+    CK(lns::launch_words_op(d, lns::kOr, out, d.prev, d.always, c));
+    return LNS_OK;
+  }
+  CK(cudaMemsetAsync(d.reach, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+  CK(cudaMemsetAsync(d.ctr, 0, sizeof(IterCounters), m->stream));
+  if (d.n_always > 0) {
+    CK(lns::launch_seed_frontier(d, d.always_list, d.n_always, d.reach, c));
+    TRY(dilate(m, m->o.m_layers));
+  }
+  CK(lns::launch_words_op(d, lns::kCopy, out, d.reach, nullptr, c));
+  return LNS_OK;
+}
+
+lns_status open_step(lns_model* m, double dt) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(LNS_EINVAL, "dt must be positive and finite");
+  m->dt = dt;
+  CK(cudaMemcpyAsync(d.pn, d.p, sizeof(double) * (size_t)d.n, cudaMemcpyDeviceToDevice, m->stream));
+  CK(cudaMemcpyAsync(d.swn, d.sw, sizeof(double) * (size_t)d.n, cudaMemcpyDeviceToDevice, m->stream));
+  if (m->o.mode == LNS_MODE_FULL) {
+    CK(lns::launch_words_op(d, lns::kAll, d.va, nullptr, nullptr, c));
+    CK(lns::launch_words_op(d, lns::kAll, d.uni, nullptr, nullptr, c));
+  } else {
+    CK(cudaMemsetAsync(d.uni, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+    TRY(initial_set(m, d.va));
+  }
+  m->step_open = true;
+  m->is_expand = 1;
+  m->converged = 0;
+  std::memset(&m->cur, 0, sizeof(m->cur));
+  return LNS_OK;
+}
+
+lns_status close_step(lns_model* m) {
+  CK(lns::launch_step_support(m->d, m->o.eps_p, m->o.eps_sw, cfg(m)));
+  m->has_prev = 1;
+  m->step_open = false;
+  return LNS_OK;
+}
+
+// One pass of Algorithm 1 lines 4-21 (or of standard Newton).
+lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  const bool local = m->o.mode == LNS_MODE_LOCAL;
+  TRY(reset_iter(m));
+  if (local) {
+    PendingEvent pe;
+    TRY(ev_begin(m, KC_SETS, &pe));
+    CK(lns::launch_boundary(d, d.va, d.vb, c));  // V_B of the set being solved
+    TRY(ev_end(m, &pe, 0.0, 0.0));
+  }
+  TRY(local_solve(m, 0));
+  PendingEvent pe;
+  TRY(ev_begin(m, KC_UPDATE, &pe));
+  // u^{nu+1} = u^nu + R_A^T du_A, and the flags of Algorithm 1 lines 8-14
+  CK(lns::launch_flag(d, local ? d.vb : nullptr, 1, 0, 0, m->o.eps_p, m->o.eps_sw, eff_p_scale(m), m->o.sat_chop,
+                      m->o.krylov_fp32, d.kx, m->o.krylov_fail_rtol, c));
+  TRY(ev_end(m, &pe, 0.0, 0.0));
+  if (local) {
+    TRY(ev_begin(m, KC_SETS, &pe));
+    TRY(dilate(m, m->o.m_layers));
+    CK(lns::launch_alg1_combine(d, m->o.tol_dp, m->o.tol_cnv, -1, c));
+    TRY(ev_end(m, &pe, 0.0, 0.0));
+  }
+  CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  annotate_pending(m);
+  TRY(ev_flush(m));
+  const IterCounters& h = *d.ctr_h;
+  const double maxdp = bits2d(h.max_dp_bits), cnv = bits2d(h.cnv_bits);
+  m->converged = local ? h.converged : (maxdp < m->o.tol_dp && cnv < m->o.tol_cnv);
+  m->is_expand = local ? h.is_expand : 0;
+  m->cur.iterations += 1;
+  m->cur.krylov_iters += h.krylov_iters;
+  m->cur.cell_updates += h.n_active;
+  m->cur.last_max_dp = maxdp;
+  m->cur.last_cnv = cnv;
+  if (st) {
+    st->n_active = h.n_active;
+    st->is_expand = m->is_expand;
+    st->converged = m->converged;
+    st->krylov_iters = h.krylov_iters;
+    st->krylov_status = h.krylov_status;
+    st->krylov_relres = h.krylov_relres;
+    st->max_dp = maxdp;
+    st->max_dsw = bits2d(h.max_dsw_bits);
+    st->cnv = cnv;
+    st->step_done = 0;
+  }
+  return krylov_outcome(m);
+}
+
+// ---------------------------------------------------------------------------------------
+// Algorithm 2 (Section 4.4).
+// ---------------------------------------------------------------------------------------
+lns_status dd_ensure(lns_model* m, size_t k) {
+  while (m->dd_va.size() <= k) {
+    uint32_t *a, *b, *c;
+    TRY(dalloc_t(m, (size_t)m->d.W, &a));
+    TRY(dalloc_t(m, (size_t)m->d.W, &b));
+    TRY(dalloc_t(m, (size_t)m->d.W, &c));
+    m->dd_va.push_back(a);
+    m->dd_vb.push_back(b);
+    m->dd_vdb.push_back(c);
+  }
+  return LNS_OK;
+}
+
+// Local solve of subdomain k (one Newton step with Dirichlet values from the current u),
+// update scatter with Algorithm 2 stamps; vb: boundary set whose large updates seed the
+// next expansion (nullptr in the Schwarz loop).  Returns own_big / converged via outputs.
+lns_status dd_solve(lns_model* m, uint32_t* va_k, const uint32_t* vb, int solve_id, int* own_big, int* conv) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  TRY(reset_iter(m));
+  CK(lns::launch_words_op(d, lns::kCopy, d.va, va_k, nullptr, c));
+  CK(lns::launch_words_op(d, lns::kOr, d.uni, d.uni, va_k, c));
+  TRY(local_solve(m, 0));
+  PendingEvent pe;
+  TRY(ev_begin(m, KC_UPDATE, &pe));
+  CK(lns::launch_flag(d, vb, 1, 1, solve_id, m->o.eps_p, m->o.eps_sw, eff_p_scale(m), m->o.sat_chop, m->o.krylov_fp32,
+                      d.kx, m->o.krylov_fail_rtol, c));
+  TRY(ev_end(m, &pe, 0.0, 0.0));
+  if (vb) TRY(dilate(m, m->o.m_layers));
+  CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  annotate_pending(m);
+  TRY(ev_flush(m));
+  const IterCounters& h = *d.ctr_h;
+  const double maxdp = bits2d(h.max_dp_bits), cnv = bits2d(h.cnv_bits);
+  *own_big = h.any_s;
+  *conv = maxdp < m->o.tol_dp && cnv < m->o.tol_cnv;
+  m->cur.iterations += 1;
+  m->cur.krylov_iters += h.krylov_iters;
+  m->cur.cell_updates += h.n_active;
+  m->cur.last_max_dp = maxdp;
+  m->cur.last_cnv = cnv;
+  return krylov_outcome(m);
+}
+
+// Algorithm 2 lines 8-22 on the update already flagged (reach holds the m-layer expansion of
+// E): next subdomain, V_T, boundary and halo sets.  Reads is_expand back.
+lns_status dd_expand_sets(lns_model* m, uint32_t* vt, uint32_t* va_next, uint32_t* vb_next, uint32_t* vdb_next,
+                          int* is_expand) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  CK(cudaMemsetAsync(&d.ctr->any_new, 0, sizeof(int), m->stream));
+  CK(lns::launch_dd_combine(d, d.reach, vt, va_next, c));
+  CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+  TRY(sync(m));
+  *is_expand = (d.ctr_h->any_e && d.ctr_h->any_new) ? 1 : 0;
+  if (*is_expand) {
+    CK(lns::launch_boundary(d, vt, d.tmp0, c));  // V_B of V_T
+    CK(lns::launch_words_op(d, lns::kAnd, vb_next, d.tmp0, va_next, c));
+    CK(lns::launch_compact(d, va_next, d.fr1, nullptr, &d.ctr->n_frontier[1], c));
+    CK(lns::launch_outer_halo(d, va_next, d.fr1, &d.ctr->n_frontier[1], vdb_next, c));
+  } else {
+    CK(cudaMemsetAsync(vb_next, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+    CK(cudaMemsetAsync(vdb_next, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+  }
+  return LNS_OK;
+}
+
+lns_status dd_timestep(lns_model* m, double dt, lns_step_stats* out) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  TRY(open_step(m, dt));
+  if (!m->dd_vt) TRY(dalloc_t(m, (size_t)d.W, &m->dd_vt));
+  TRY(dd_ensure(m, 0));
+  CK(lns::launch_words_op(d, lns::kCopy, m->dd_va[0], d.va, nullptr, c));
+  CK(lns::launch_words_op(d, lns::kCopy, m->dd_vt, d.va, nullptr, c));
+  CK(lns::launch_boundary(d, d.va, m->dd_vb[0], c));
+  CK(lns::launch_compact(d, d.va, d.fr1, nullptr, &d.ctr->n_frontier[1], c));
+  CK(lns::launch_outer_halo(d, d.va, d.fr1, &d.ctr->n_frontier[1], m->dd_vdb[0], c));
+  CK(cudaMemsetAsync(d.stamp, 0, sizeof(int) * (size_t)d.n, m->stream));
+  std::vector<int> last_solve, own_big;
+  int solve_id = 0, k = 0, is_expand = 1;
+  lns_status st = LNS_OK;
+  // expansion phase
+  while (is_expand) {
+    if (k >= m->o.max_newton) {
+      st = fail(LNS_ENOCONV, "Algorithm 2 expansion reached max_newton subdomains");
+      break;
+    }
+    TRY(dd_ensure(m, (size_t)k + 1));
+    int ob = 0, conv = 0;
+    solve_id++;
+    TRY(dd_solve(m, m->dd_va[k], m->dd_vb[k], solve_id, &ob, &conv));
+    last_solve.push_back(solve_id);
+    own_big.push_back(ob);
+    TRY(dd_expand_sets(m, m->dd_vt, m->dd_va[k + 1], m->dd_vb[k + 1], m->dd_vdb[k + 1], &is_expand));
+    k++;
+  }
+  const int N = k;
+  m->cur.n_subdomains = N;
+  // nonlinear DD loop (multiplicative Schwarz)
+  int nu = 0;
+  bool converged = false;
+  while (st == LNS_OK && !converged) {
+    if (nu >= m->o.max_dd_outer) {
+      st = fail(LNS_ENOCONV, "Algorithm 2 reached max_dd_outer passes");
+      break;
+    }
+    bool all_ok = true;
+    for (int s = 0; s < N; s++) {
+      CK(lns::launch_halo_check(d, m->dd_vdb[s], last_solve[s], c));
+      CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+      TRY(sync(m));
+      const int halo = d.ctr_h->halo_flag;
+      if (!(own_big[s] || halo)) continue;
+      int ob = 0, conv = 0;
+      solve_id++;
+      TRY(dd_solve(m, m->dd_va[s], nullptr, solve_id, &ob, &conv));
+      last_solve[s] = solve_id;
+      own_big[s] = ob;
+      if (!conv) all_ok = false;
+    }
+    nu++;
+    converged = all_ok;
+  }
+  m->cur.dd_outer = nu;
+  TRY(close_step(m));
+  TRY(sync(m));
+  m->cur.status = st;
+  if (out) *out = m->cur;
+  return st;
+}
+
+lns_status check_model(const lns_model* m) {
+  if (!m) return fail(LNS_EINVAL, "model is NULL");
+  return LNS_OK;
+}
+
+lns_status validate_options(const lns_options* o) {
+  if (!o) return fail(LNS_EINVAL, "options is NULL");
+  if (o->mode < 0 || o->mode > 2) return fail(LNS_EINVAL, "mode must be 0, 1 or 2");
+  if (o->m_layers < 0 || o->m_layers > 100000) return fail(LNS_EINVAL, "m_layers out of range");
+  if (o->max_newton < 1 || o->max_dd_outer < 1) return fail(LNS_EINVAL, "max_newton and max_dd_outer must be >= 1");
+  if (o->krylov_maxit < 1) return fail(LNS_EINVAL, "krylov_maxit must be >= 1");
+  if (!(o->krylov_rtol > 0.0) || !(o->eps_p >= 0.0)) return fail(LNS_EINVAL, "krylov_rtol > 0 and eps_p >= 0 required");
+  if (o->precond != LNS_PRECOND_BJAC) return fail(LNS_EINVAL, "unknown preconditioner");
+  return LNS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lns_last_error(void) { return g_err.c_str(); }
+
+lns_status lns_options_default(lns_options* o) {
+  if (!o) return fail(LNS_EINVAL, "options is NULL");
+  const double psi = 6894.757293168;
+  std::memset(o, 0, sizeof(*o));
+  o->mode = LNS_MODE_LOCAL;
+  o->eps_p = 0.3 * psi;
+  o->eps_sw = 0.0;
+  o->m_layers = 2;
+  o->tol_dp = 0.3 * psi;
+  o->tol_cnv = 1e-6;
+  o->max_newton = 25;
+  o->max_dd_outer = 25;
+  o->sat_chop = 0.2;
+  o->krylov_fp32 = 0;
+  o->precond = LNS_PRECOND_BJAC;
+  o->krylov_rtol = 1e-8;
+  o->krylov_maxit = 2000;
+  o->krylov_fail_rtol = 1e-3;
+  o->p_scale = 0.0;
+  o->profile = 0;
+  return LNS_OK;
+}
+
+lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts, const lns_allocator* allocator,
+                            void* cuda_stream, lns_model** out) {
+  if (!desc || !out) return fail(LNS_EINVAL, "desc and out must be non-NULL");
+  *out = nullptr;
+  TRY(validate_options(opts));
+  const int n = desc->n_cells, na = desc->n_adj;
+  if (n < 0 || na < 0) return fail(LNS_EINVAL, "negative sizes");
+  if (n > 0 && (!desc->row_ptr || !desc->pv_ref || !desc->depth || !desc->line_id || !desc->always_active ||
+                !desc->p0 || !desc->sw0))
+    return fail(LNS_EINVAL, "missing cell array");
+  if (na > 0 && (!desc->nbr || !desc->trans)) return fail(LNS_EINVAL, "missing connection array");
+  if (desc->n_wells < 0 || (desc->n_wells > 0 && (!desc->well_cell || !desc->well_wi || !desc->well_bhp)))
+    return fail(LNS_EINVAL, "bad well arrays");
+  const lns_fluid& f = desc->fluid;
+  if (f.n_w < 1 || f.n_w > 8 || f.n_o < 1 || f.n_o > 8) return fail(LNS_EINVAL, "Corey exponents must be 1..8");
+  if (!(f.swc + f.sor < 1.0) || !(f.mu_o > 0.0) || !(f.mu_w > 0.0)) return fail(LNS_EINVAL, "bad fluid constants");
+  // graph checks: row_ptr monotone, neighbours in range, no self loops, ascending rows
+  if (n > 0) {
+    if (desc->row_ptr[0] != 0 || desc->row_ptr[n] != na) return fail(LNS_EINVAL, "row_ptr must run from 0 to n_adj");
+    for (int i = 0; i < n; i++) {
+      if (desc->row_ptr[i + 1] < desc->row_ptr[i]) return fail(LNS_EINVAL, "row_ptr not monotone");
+      for (int e = desc->row_ptr[i]; e < desc->row_ptr[i + 1]; e++) {
+        const int j = desc->nbr[e];
+        if (j < 0 || j >= n || j == i) return fail(LNS_EINVAL, "neighbour index out of range or self loop");
+        if (e > desc->row_ptr[i] && desc->nbr[e - 1] >= j) return fail(LNS_EINVAL, "row neighbours not ascending");
+      }
+    }
+    // every connection stored at both endpoints with the same transmissibility
+    for (int i = 0; i < n; i++)
+      for (int e = desc->row_ptr[i]; e < desc->row_ptr[i + 1]; e++) {
+        const int j = desc->nbr[e];
+        const int* b = desc->nbr + desc->row_ptr[j];
+        const int* t = desc->nbr + desc->row_ptr[j + 1];
+        const int* f = std::lower_bound(b, t, i);
+        if (f == t || *f != i || desc->trans[f - desc->nbr] != desc->trans[e])
+          return fail(LNS_EINVAL, "connection graph is not symmetric (each connection must be stored at both ends)");
+      }
+  } else if (na != 0) {
+    return fail(LNS_EINVAL, "n_adj must be 0 when n_cells is 0");
+  }
+  for (int w = 0; w < desc->n_wells; w++)
+    if (desc->well_cell[w] < 0 || desc->well_cell[w] >= n) return fail(LNS_EINVAL, "well cell out of range");
+
+  lns_model* m = new lns_model();
+  m->o = *opts;
+  if (allocator && allocator->alloc && allocator->free) {
+    m->alloc = *allocator;
+    m->has_alloc = true;
+  }
+  m->stream = (cudaStream_t)cuda_stream;
+  auto cleanup_fail = [&](lns_status s) {
+    lns_model_destroy(m);
+    return s;
+  };
+  if (cudaGetDevice(&m->device) != cudaSuccess) return cleanup_fail(fail(LNS_ECUDA, "no CUDA device"));
+  if (cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess)
+    return cleanup_fail(fail(LNS_ECUDA, "cannot query SM count"));
+  m->kgrid[0] = lns::krylov_grid(0, m->sms);
+  m->kgrid[1] = lns::krylov_grid(1, m->sms);
+  Dev& d = m->d;
+  d.n = n;
+  d.n_adj = na;
+  d.W = (n + 31) / 32;
+  d.n_wells = desc->n_wells;
+  d.fl = lns::Fluid{f.p_ref, f.c_r, f.b_o_ref, f.c_o, f.b_w_ref, f.c_w, f.rho_o_ref, f.rho_w_ref, f.mu_o, f.mu_w,
+                    f.swc, f.sor, f.n_w, f.n_o, f.gravity};
+  m->avg_degree = n > 0 ? (double)na / n : 0.0;
+  const size_t N = std::max(n, 1), A = std::max(na, 1), W = std::max(d.W, 1), NW = std::max(desc->n_wells, 1);
+  lns_status s = LNS_OK;
+#define AL(ptr, cnt)                                  \
+  do {                                                \
+    s = dalloc_t(m, (size_t)(cnt), &ptr);             \
+    if (s != LNS_OK) return cleanup_fail(s);          \
+  } while (0)
+  AL(d.row_ptr, N + 1);
+  AL(d.nbr, A);
+  AL(d.trans, A);
+  AL(d.depth, N);
+  AL(d.pv_ref, N);
+  AL(d.line_id, N);
+  AL(d.well_cell, NW);
+  AL(d.well_wi, NW);
+  AL(d.well_bhp, NW);
+  AL(d.well_of_cell, N);
+  AL(d.well_next, NW);
+  AL(d.always_list, N);
+  AL(d.always, W);
+  AL(d.p, N);
+  AL(d.sw, N);
+  AL(d.pn, N);
+  AL(d.swn, N);
+  AL(d.p0, N);
+  AL(d.sw0, N);
+  AL(d.dp, N);
+  AL(d.dsw, N);
+  AL(d.stamp, N);
+  AL(d.va, W);
+  AL(d.vb, W);
+  AL(d.supp, W);
+  AL(d.reach, W);
+  AL(d.uni, W);
+  AL(d.prev, W);
+  AL(d.tmp0, W);
+  AL(d.tmp1, W);
+  AL(d.tmp2, W);
+  AL(d.act, N);
+  AL(d.inv, N);
+  AL(d.fr0, N);
+  AL(d.fr1, N);
+  AL(d.blk_sums, (W + 255) / 256 + 1);
+  {
+    double* t;
+    AL(t, A * 4);
+    d.blocks = t;
+    AL(d.colA, A);
+    AL(t, N * 2);
+    d.rhs = t;
+    AL(t, N * 4);
+    d.line_dinv = t;
+    AL(t, N * 4);
+    d.line_a = t;
+    AL(t, N * 4);
+    d.line_g = t;
+    AL(d.line_start, N);
+    AL(d.line_len, N);
+    AL(d.line_row_flag, N);
+    double** vecs[9] = {(double**)&d.kx, (double**)&d.kr, (double**)&d.krh, (double**)&d.kp, (double**)&d.kv,
+                        (double**)&d.ks, (double**)&d.kt, (double**)&d.kph, (double**)&d.ksh};
+    for (auto v : vecs) AL(*v, N * 2);
+    AL(d.partials, (size_t)8 * 4 * m->sms + 64);
+  }
+  AL(d.ctr, 1);
+#undef AL
+  if (cudaMallocHost((void**)&d.ctr_h, sizeof(IterCounters)) != cudaSuccess) {
+    d.ctr_h = nullptr;
+    return cleanup_fail(fail(LNS_ENOMEM, "cudaMallocHost failed"));
+  }
+  // host-side derived tables
+  std::vector<int> woc(N, -1), wnext(NW, -1), alist;
+  for (int w = desc->n_wells - 1; w >= 0; w--) {
+    wnext[w] = woc[desc->well_cell[w]];
+    woc[desc->well_cell[w]] = w;
+  }
+  std::vector<uint32_t> abits(W, 0u);
+  for (int i = 0; i < n; i++)
+    if (desc->always_active[i]) {
+      abits[i >> 5] |= 1u << (i & 31);
+      alist.push_back(i);
+    }
+  d.n_always = (int)alist.size();
+  auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0 || !src) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, m->stream);
+  };
+  cudaError_t e = cudaSuccess;
+  e = e ? e : up(d.row_ptr, desc->row_ptr, sizeof(int) * (size_t)(n + 1) * (n > 0));
+  e = e ? e : up(d.nbr, desc->nbr, sizeof(int) * (size_t)na);
+  e = e ? e : up(d.trans, desc->trans, sizeof(double) * (size_t)na);
+  e = e ? e : up(d.depth, desc->depth, sizeof(double) * (size_t)n);
+  e = e ? e : up(d.pv_ref, desc->pv_ref, sizeof(double) * (size_t)n);
+  e = e ? e : up(d.line_id, desc->line_id, sizeof(int) * (size_t)n);
+  e = e ? e : up(d.well_cell, desc->well_cell, sizeof(int) * (size_t)desc->n_wells);
+  e = e ? e : up(d.well_wi, desc->well_wi, sizeof(double) * (size_t)desc->n_wells);
+  e = e ? e : up(d.well_bhp, desc->well_bhp, sizeof(double) * (size_t)desc->n_wells);
+  e = e ? e : up(d.well_of_cell, woc.data(), sizeof(int) * (size_t)n);
+  e = e ? e : up(d.well_next, wnext.data(), sizeof(int) * (size_t)desc->n_wells);
+  e = e ? e : up(d.always_list, alist.data(), sizeof(int) * alist.size());
+  e = e ? e : up(d.always, abits.data(), sizeof(uint32_t) * (size_t)d.W);
+  e = e ? e : up(d.p0, desc->p0, sizeof(double) * (size_t)n);
+  e = e ? e : up(d.sw0, desc->sw0, sizeof(double) * (size_t)n);
+  if (n == 0 && e == cudaSuccess) e = cudaMemsetAsync(d.row_ptr, 0, sizeof(int), m->stream);
+  if (e != cudaSuccess) return cleanup_fail(fail(LNS_ECUDA, std::string("upload: ") + cudaGetErrorString(e)));
+  *out = m;
+  lns_status r = lns_reset(m);
+  if (r != LNS_OK) {
+    *out = nullptr;
+    return cleanup_fail(r);
+  }
+  return LNS_OK;
+}
+
+lns_status lns_model_destroy(lns_model* m) {
+  if (!m) return LNS_OK;
+  cudaStreamSynchronize(m->stream);
+  for (void* p : m->owned) {
+    if (m->has_alloc)
+      m->alloc.free(m->alloc.ctx, p, (void*)m->stream);
+    else
+      cudaFree(p);
+  }
+  if (m->d.ctr_h) cudaFreeHost(m->d.ctr_h);
+  for (auto e : m->ev_pool) cudaEventDestroy(e);
+  for (auto& pe : m->pending) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  delete m;
+  return LNS_OK;
+}
+
+lns_status lns_set_options(lns_model* m, const lns_options* o) {
+  TRY(check_model(m));
+  TRY(validate_options(o));
+  if (m->step_open && o->mode != m->o.mode) return fail(LNS_ESTATE, "cannot change mode inside an open timestep");
+  m->o = *o;
+  return LNS_OK;
+}
+
+lns_status lns_reset(lns_model* m) {
+  TRY(check_model(m));
+  Dev& d = m->d;
+  const size_t nb = sizeof(double) * (size_t)d.n;
+  if (d.n > 0) {
+    CK(cudaMemcpyAsync(d.p, d.p0, nb, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.sw, d.sw0, nb, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.pn, d.p0, nb, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.swn, d.sw0, nb, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemsetAsync(d.prev, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+  }
+  m->has_prev = 0;
+  m->step_open = false;
+  return sync(m);
+}
+
+lns_status lns_set_state(lns_model* m, const double* p, const double* sw, const double* pn, const double* swn) {
+  TRY(check_model(m));
+  if (!p || !sw) return fail(LNS_EINVAL, "p and sw must be non-NULL");
+  Dev& d = m->d;
+  const size_t nb = sizeof(double) * (size_t)d.n;
+  if (d.n > 0) {
+    CK(cudaMemcpyAsync(d.p, p, nb, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.sw, sw, nb, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.pn, pn ? pn : p, nb, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.swn, swn ? swn : sw, nb, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemsetAsync(d.prev, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+  }
+  m->has_prev = 0;
+  m->step_open = false;
+  return sync(m);
+}
+
+lns_status lns_get_state(const lns_model* cm, double* p, double* sw) {
+  lns_model* m = const_cast<lns_model*>(cm);
+  TRY(check_model(m));
+  const size_t nb = sizeof(double) * (size_t)m->d.n;
+  if (m->d.n > 0) {
+    if (p) CK(cudaMemcpyAsync(p, m->d.p, nb, cudaMemcpyDeviceToHost, m->stream));
+    if (sw) CK(cudaMemcpyAsync(sw, m->d.sw, nb, cudaMemcpyDeviceToHost, m->stream));
+  }
+  return sync(m);
+}
+
+lns_status lns_get_state_device(const lns_model* cm, double* p, double* sw) {
+  lns_model* m = const_cast<lns_model*>(cm);
+  TRY(check_model(m));
+  const size_t nb = sizeof(double) * (size_t)m->d.n;
+  if (m->d.n > 0) {
+    if (p) CK(cudaMemcpyAsync(p, m->d.p, nb, cudaMemcpyDeviceToDevice, m->stream));
+    if (sw) CK(cudaMemcpyAsync(sw, m->d.sw, nb, cudaMemcpyDeviceToDevice, m->stream));
+  }
+  return sync(m);
+}
+
+lns_status lns_get_support(const lns_model* cm, uint32_t* bits) {
+  lns_model* m = const_cast<lns_model*>(cm);
+  TRY(check_model(m));
+  if (!bits) return fail(LNS_EINVAL, "bits is NULL");
+  TRY(bits_to_host(m, bits, m->d.prev));
+  return sync(m);
+}
+
+lns_status lns_newton_iter(lns_model* m, double dt, lns_iter_stats* out) {
+  TRY(check_model(m));
+  if (m->o.mode == LNS_MODE_DD) return fail(LNS_ESTATE, "lns_newton_iter is not available in LNS_MODE_DD");
+  if (m->d.n == 0) return fail(LNS_EINVAL, "empty model");
+  if (!m->step_open) TRY(open_step(m, dt));
+  lns_iter_stats st{};
+  lns_status s = alg1_iteration(m, &st);
+  if (s != LNS_OK) {
+    m->step_open = false;
+    if (out) *out = st;
+    return s;
+  }
+  const bool done = m->o.mode == LNS_MODE_FULL ? m->converged : (!m->is_expand && m->converged);
+  if (done) {
+    TRY(close_step(m));
+    TRY(sync(m));
+    st.step_done = 1;
+  } else if (m->cur.iterations >= m->o.max_newton) {
+    TRY(close_step(m));
+    TRY(sync(m));
+    st.step_done = 1;
+    if (out) *out = st;
+    return fail(LNS_ENOCONV, "Newton loop reached max_newton");
+  }
+  if (out) *out = st;
+  return LNS_OK;
+}
+
+lns_status lns_timestep(lns_model* m, double dt, lns_step_stats* out) {
+  TRY(check_model(m));
+  if (m->d.n == 0) {
+    if (out) std::memset(out, 0, sizeof(*out));
+    return LNS_OK;
+  }
+  if (m->o.mode == LNS_MODE_DD) return dd_timestep(m, dt, out);
+  if (m->step_open) return fail(LNS_ESTATE, "a timestep opened by lns_newton_iter is still open");
+  TRY(open_step(m, dt));
+  lns_status s = LNS_OK;
+  for (;;) {
+    lns_iter_stats st{};
+    s = lns_newton_iter(m, dt, &st);
+    if (s != LNS_OK || st.step_done) break;
+  }
+  m->cur.status = s;
+  if (out) *out = m->cur;
+  return s;
+}
+
+lns_status lns_active_set(lns_model* m, const double* dp, const double* dsw, int32_t du_on_device, int32_t converged,
+                          uint32_t* va_bits, uint32_t* vb_bits, int32_t* is_expand) {
+  TRY(check_model(m));
+  if (!dp || !va_bits) return fail(LNS_EINVAL, "dp and va_bits must be non-NULL");
+  if (m->step_open) return fail(LNS_ESTATE, "a timestep is open");
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  const size_t nb = sizeof(double) * (size_t)d.n;
+  if (d.n == 0) {
+    if (is_expand) *is_expand = 0;
+    return LNS_OK;
+  }
+  const cudaMemcpyKind kind = du_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(d.dp, dp, nb, kind, m->stream));
+  if (dsw)
+    CK(cudaMemcpyAsync(d.dsw, dsw, nb, kind, m->stream));
+  else
+    CK(cudaMemsetAsync(d.dsw, 0, nb, m->stream));
+  TRY(bits_to_device(m, d.va, va_bits));
+  TRY(reset_iter(m));
+  CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, c));
+  CK(lns::launch_boundary(d, d.va, d.vb, c));
+  CK(lns::launch_flag(d, d.vb, 0, 0, 0, m->o.eps_p, m->o.eps_sw, 1.0, 0.0, 0, nullptr, -1.0, c));
+  TRY(dilate(m, m->o.m_layers));
+  // the union accumulator is scratch here
+  CK(lns::launch_alg1_combine(d, m->o.tol_dp, m->o.tol_cnv, converged ? 1 : 0, c));
+  CK(lns::launch_boundary(d, d.va, d.vb, c));
+  TRY(bits_to_host(m, va_bits, d.va));
+  if (vb_bits) TRY(bits_to_host(m, vb_bits, d.vb));
+  TRY(read_counters(m));
+  if (is_expand) *is_expand = d.ctr_h->is_expand;
+  return LNS_OK;
+}
+
+lns_status lns_dd_expand(lns_model* m, const double* dp, const double* dsw, int32_t du_on_device, const uint32_t* vb_k,
+                         uint32_t* vt, uint32_t* va_next, uint32_t* vb_next, uint32_t* vdb_next, int32_t* is_expand) {
+  TRY(check_model(m));
+  if (!dp || !vb_k || !vt || !va_next) return fail(LNS_EINVAL, "dp, vb_k, vt and va_next must be non-NULL");
+  if (m->step_open) return fail(LNS_ESTATE, "a timestep is open");
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  const size_t nb = sizeof(double) * (size_t)d.n;
+  if (d.n == 0) {
+    if (is_expand) *is_expand = 0;
+    return LNS_OK;
+  }
+  const cudaMemcpyKind kind = du_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(d.dp, dp, nb, kind, m->stream));
+  if (dsw)
+    CK(cudaMemcpyAsync(d.dsw, dsw, nb, kind, m->stream));
+  else
+    CK(cudaMemsetAsync(d.dsw, 0, nb, m->stream));
+  TRY(bits_to_device(m, d.tmp1, vb_k));
+  TRY(bits_to_device(m, d.tmp2, vt));
+  TRY(reset_iter(m));
+  // flag the cells of V_B^k: E = {i in V_B^k : |du_i| >= eps}
+  CK(lns::launch_compact(d, d.tmp1, d.act, nullptr, &d.ctr->n_active, c));
+  CK(lns::launch_flag(d, d.tmp1, 0, 0, 0, m->o.eps_p, m->o.eps_sw, 1.0, 0.0, 0, nullptr, -1.0, c));
+  TRY(dilate(m, m->o.m_layers));
+  int ie = 0;
+  TRY(dd_expand_sets(m, d.tmp2, d.va, d.vb, d.supp, &ie));
+  TRY(bits_to_host(m, vt, d.tmp2));
+  TRY(bits_to_host(m, va_next, d.va));
+  if (vb_next) TRY(bits_to_host(m, vb_next, d.vb));
+  if (vdb_next) TRY(bits_to_host(m, vdb_next, d.supp));
+  TRY(sync(m));
+  if (is_expand) *is_expand = ie;
+  return LNS_OK;
+}
+
+lns_status lns_solve_local(lns_model* m, double dt, const uint32_t* va_bits, double* dp, double* dsw,
+                           lns_iter_stats* out) {
+  TRY(check_model(m));
+  if (!va_bits) return fail(LNS_EINVAL, "va_bits is NULL");
+  if (m->step_open) return fail(LNS_ESTATE, "a timestep is open");
+  if (!(dt > 0.0)) return fail(LNS_EINVAL, "dt must be positive");
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  if (d.n == 0) return LNS_OK;
+  m->dt = dt;
+  const size_t nb = sizeof(double) * (size_t)d.n;
+  TRY(bits_to_device(m, d.va, va_bits));
+  TRY(reset_iter(m));
+  TRY(local_solve(m, 0));
+  CK(cudaMemsetAsync(d.dp, 0, nb, m->stream));
+  CK(cudaMemsetAsync(d.dsw, 0, nb, m->stream));
+  CK(lns::launch_flag(d, nullptr, 0, 0, 0, m->o.eps_p, m->o.eps_sw, eff_p_scale(m), m->o.sat_chop, m->o.krylov_fp32,
+                      d.kx, -1.0, c));
+  if (dp) CK(cudaMemcpyAsync(dp, d.dp, nb, cudaMemcpyDeviceToHost, m->stream));
+  if (dsw) CK(cudaMemcpyAsync(dsw, d.dsw, nb, cudaMemcpyDeviceToHost, m->stream));
+  TRY(read_counters(m));
+  const IterCounters& h = *d.ctr_h;
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->n_active = h.n_active;
+    out->krylov_iters = h.krylov_iters;
+    out->krylov_status = h.krylov_status;
+    out->krylov_relres = h.krylov_relres;
+    out->max_dp = bits2d(h.max_dp_bits);
+    out->max_dsw = bits2d(h.max_dsw_bits);
+    out->cnv = bits2d(h.cnv_bits);
+  }
+  return krylov_outcome(m);
+}
+
+lns_status lns_assemble(lns_model* m, double dt, const uint32_t* va_bits, double* F, double* Jd, double* Jo) {
+  TRY(check_model(m));
+  if (!va_bits) return fail(LNS_EINVAL, "va_bits is NULL");
+  if (m->step_open) return fail(LNS_ESTATE, "a timestep is open");
+  if (!(dt > 0.0)) return fail(LNS_EINVAL, "dt must be positive");
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  if (d.n == 0) return LNS_OK;
+  if (!d.resid) {
+    TRY(dalloc_t(m, (size_t)d.n * 2, &d.resid));
+    TRY(dalloc_t(m, (size_t)d.n * 4, &d.dbg_diag));
+    TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.dbg_off));
+  }
+  CK(cudaMemsetAsync(d.resid, 0, sizeof(double) * 2 * (size_t)d.n, m->stream));
+  CK(cudaMemsetAsync(d.dbg_diag, 0, sizeof(double) * 4 * (size_t)d.n, m->stream));
+  CK(cudaMemsetAsync(d.dbg_off, 0, sizeof(double) * 4 * (size_t)std::max(d.n_adj, 1), m->stream));
+  m->dt = dt;
+  TRY(bits_to_device(m, d.va, va_bits));
+  TRY(reset_iter(m));
+  CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, c));
+  CK(lns::launch_assemble(d, dt, eff_p_scale(m), m->o.krylov_fp32, 1, c));
+  if (F) CK(cudaMemcpyAsync(F, d.resid, sizeof(double) * 2 * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));
+  if (Jd) CK(cudaMemcpyAsync(Jd, d.dbg_diag, sizeof(double) * 4 * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));
+  if (Jo && d.n_adj > 0)
+    CK(cudaMemcpyAsync(Jo, d.dbg_off, sizeof(double) * 4 * (size_t)d.n_adj, cudaMemcpyDeviceToHost, m->stream));
+  return sync(m);
+}
+
+lns_status lns_kernel_times(const lns_model* m, lns_kernel_time* out, int32_t cap, int32_t* count) {
+  TRY(check_model(m));
+  int k = 0;
+  for (int c = 0; c < KC_COUNT && k < cap; c++) {
+    if (!out) break;
+    out[k] = m->kt[c];
+    std::snprintf(out[k].name, sizeof(out[k].name), "%s", kClassName[c]);
+    k++;
+  }
+  if (count) *count = k;
+  return LNS_OK;
+}
+
+lns_status lns_reset_kernel_times(lns_model* m) {
+  TRY(check_model(m));
+  std::memset(m->kt, 0, sizeof(m->kt));
+  return LNS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// lns_internal.cuh -- device data layout and kernel launchers of liblns (sm_103a).
+//
+// Layout in HBM (n cells, E2 = CSR entries, W = ceil(n/32) bitset words):
+//   static graph : row_ptr[n+1], nbr[E2] (int32), trans[E2] (f64), depth/pv_ref[n] (f64),
+//                  line_id[n] (int32), always bitset[W], well table
+//   state        : p, sw (iterate u^nu), pn, swn (time level u^n), p0, sw0 (initial), f64[n]
+//   sets         : va, vb, supp, reach, step union, previous-step support  (bitsets[W])
+//   compaction   : act[n] ascending active cells, inv[n] cell -> compact row (valid where
+//                  va is set), frontier lists fr0/fr1[n]
+//   system       : blocks[E2] 2x2 off-diagonal blocks stored at the CSR entry of their
+//                  row (f64 or f32), colA[E2] compact column or -1, rhs[2n]; the diagonal
+//                  blocks are scaled to the identity and not stored
+//   Krylov       : x, r, rhat, p, v, s, t, phat, shat [2n] (f64 or f32), partial sums
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lns.h"
+
+namespace lns {
+
+constexpr int kMaxLinesPerRow = 1;
+
+struct Fluid {
+  double p_ref, c_r, b_o_ref, c_o, b_w_ref, c_w, rho_o_ref, rho_w_ref, mu_o, mu_w, swc, sor;
+  int n_w, n_o;
+  double gravity;
+};
+
+// Device scalars written by kernels and read back to the host once per iteration.
+struct IterCounters {
+  int n_active;        // compaction output
+  int n_frontier[2];   // frontier list sizes (ping-pong)
+  int any_e;           // some boundary cell had a non-negligible update
+  int any_s;           // the support of du_A is non-empty
+  int any_new;         // Algorithm 2: the next subdomain is non-empty
+  int n_lines;         // fracture line blocks in the compacted system
+  int krylov_iters;
+  int krylov_status;   // 0 ok, 1 maxit, 2 breakdown
+  int converged;
+  int is_expand;
+  int halo_flag;       // Algorithm 2 halo test result
+  unsigned long long max_dp_bits;   // max |dp| as the bit pattern of a non-negative double
+  unsigned long long max_dsw_bits;
+  unsigned long long cnv_bits;
+  double krylov_relres;
+  double pad[3];
+};
+
+struct Dev {
+  int n, n_adj, W, n_wells, n_always;
+  Fluid fl;
+  // static graph
+  int *row_ptr, *nbr, *line_id, *well_cell, *well_of_cell, *well_next, *always_list;
+  double *trans, *depth, *pv_ref, *well_wi, *well_bhp;
+  uint32_t* always;
+  // state
+  double *p, *sw, *pn, *swn, *p0, *sw0, *dp, *dsw;
+  int* stamp;  // Algorithm 2: solve id of the last non-negligible update of each cell
+  // sets
+  uint32_t *va, *vb, *supp, *reach, *uni, *prev, *tmp0, *tmp1, *tmp2;
+  // compaction
+  int *act, *inv, *fr0, *fr1, *blk_sums;
+  // system
+  void* blocks;  // E2 * 4 * sizeof(T)
+  int* colA;
+  void* rhs;     // 2n * sizeof(T)
+  double* resid; // 2n (diagnostics), f64
+  double* dbg_diag;  // 4n (diagnostics), f64
+  double* dbg_off;   // 4 E2 (diagnostics), f64
+  // fracture-line blocks of the preconditioner (per compact row, T)
+  void *line_dinv, *line_a, *line_g;
+  int *line_start, *line_len, *line_row_flag;
+  // Krylov vectors
+  void *kx, *kr, *krh, *kp, *kv, *ks, *kt, *kph, *ksh;
+  double* partials;
+  IterCounters* ctr;   // device
+  IterCounters* ctr_h; // pinned host mirror
+};
+
+// ---- launchers (defined in the .cu files) ----
+struct LaunchCfg {
+  int sms;
+  cudaStream_t stream;
+};
+
+// k_sets.cu
+cudaError_t launch_compact(const Dev& d, const uint32_t* bits, int* list, int* inv, int* count_out,
+                           LaunchCfg c);
+cudaError_t launch_boundary(const Dev& d, const uint32_t* set, uint32_t* out, LaunchCfg c);
+cudaError_t launch_outer_halo(const Dev& d, const uint32_t* set, const int* list, const int* count,
+                              uint32_t* out, LaunchCfg c);
+cudaError_t launch_flag(const Dev& d, const uint32_t* vb, int apply, int record_stamp, int solve_id,
+                        double eps_p, double eps_sw, double p_scale, double sat_chop, int fp32,
+                        const void* x, double fail_rtol, LaunchCfg c);
+cudaError_t launch_dilate(const Dev& d, uint32_t* reach, int layers, LaunchCfg c);
+cudaError_t launch_seed_frontier(const Dev& d, const int* list, int count_host, uint32_t* reach,
+                                 LaunchCfg c);
+cudaError_t launch_alg1_combine(const Dev& d, double tol_dp, double tol_cnv, int converged_override,
+                                LaunchCfg c);
+cudaError_t launch_dd_combine(const Dev& d, const uint32_t* reach, uint32_t* vt, uint32_t* va_next,
+                              LaunchCfg c);
+cudaError_t launch_words_op(const Dev& d, int op, uint32_t* out, const uint32_t* a, const uint32_t* b,
+                            LaunchCfg c);
+cudaError_t launch_step_support(const Dev& d, double eps_p, double eps_sw, LaunchCfg c);
+cudaError_t launch_halo_check(const Dev& d, const uint32_t* vdb, int since, LaunchCfg c);
+
+enum WordsOp { kCopy = 0, kOr = 1, kAnd = 2, kAndNot = 3, kAll = 5 };
+
+// k_assemble.cu
+cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, int debug, LaunchCfg c);
+cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c);
+
+// k_krylov.cu
+cudaError_t launch_bicgstab(const Dev& d, int fp32, double rtol, int maxit, int grid, LaunchCfg c);
+int krylov_grid(int fp32, int sms);
+
+}  // namespace lns

@@ -1,0 +1,356 @@
+"""Python binding of liblns (the C ABI in include/lns.h): argument marshalling only.
+
+Every entry point keeps its C name (``lns_timestep``, ``lns_active_set`` ...).  Device
+memory comes from PyTorch's caching allocator and work runs on the current PyTorch CUDA
+stream; every computation runs in the library's CUDA kernels.  There is no CPU fallback:
+loading fails loudly when the library is not built or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+PSI = 6894.757293168
+
+LNS_OK, LNS_EINVAL, LNS_ENOMEM, LNS_ECUDA, LNS_ENOCONV, LNS_EKRYLOV, LNS_ETIMEOUT, LNS_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+LNS_MODE_FULL, LNS_MODE_LOCAL, LNS_MODE_DD = 0, 1, 2
+LNS_PRECOND_BJAC = 0
+_STATUS = {0: "LNS_OK", -1: "LNS_EINVAL", -2: "LNS_ENOMEM", -3: "LNS_ECUDA", -4: "LNS_ENOCONV",
+           -5: "LNS_EKRYLOV", -6: "LNS_ETIMEOUT", -7: "LNS_ESTATE"}
+
+
+class LnsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lns_fluid(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("p_ref", "c_r", "b_o_ref", "c_o", "b_w_ref", "c_w", "rho_o_ref",
+                                           "rho_w_ref", "mu_o", "mu_w", "swc", "sor")] + \
+               [("n_w", C.c_int32), ("n_o", C.c_int32), ("gravity", C.c_double)]
+
+
+class lns_model_desc(C.Structure):
+    _fields_ = [("n_cells", C.c_int32), ("n_adj", C.c_int32), ("row_ptr", C.c_void_p), ("nbr", C.c_void_p),
+                ("trans", C.c_void_p), ("pv_ref", C.c_void_p), ("depth", C.c_void_p), ("line_id", C.c_void_p),
+                ("always_active", C.c_void_p), ("n_wells", C.c_int32), ("well_cell", C.c_void_p),
+                ("well_wi", C.c_void_p), ("well_bhp", C.c_void_p), ("fluid", lns_fluid), ("p0", C.c_void_p),
+                ("sw0", C.c_void_p)]
+
+
+class lns_options(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("eps_p", C.c_double), ("eps_sw", C.c_double), ("m_layers", C.c_int32),
+                ("tol_dp", C.c_double), ("tol_cnv", C.c_double), ("max_newton", C.c_int32),
+                ("max_dd_outer", C.c_int32), ("sat_chop", C.c_double), ("krylov_fp32", C.c_int32),
+                ("precond", C.c_int32), ("krylov_rtol", C.c_double), ("krylov_maxit", C.c_int32),
+                ("krylov_fail_rtol", C.c_double), ("p_scale", C.c_double), ("profile", C.c_int32)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class lns_allocator(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
+
+
+class lns_iter_stats(C.Structure):
+    _fields_ = [("n_active", C.c_int32), ("is_expand", C.c_int32), ("converged", C.c_int32),
+                ("step_done", C.c_int32), ("krylov_iters", C.c_int32), ("krylov_status", C.c_int32),
+                ("max_dp", C.c_double), ("max_dsw", C.c_double), ("cnv", C.c_double), ("krylov_relres", C.c_double)]
+
+
+class lns_step_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("krylov_iters", C.c_int32),
+                ("n_subdomains", C.c_int32), ("dd_outer", C.c_int32), ("cell_updates", C.c_int64),
+                ("last_max_dp", C.c_double), ("last_cnv", C.c_double)]
+
+
+class lns_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("total_ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
+def _as_dict(s: C.Structure) -> Dict:
+    return {k: (getattr(s, k).decode() if isinstance(getattr(s, k), bytes) else getattr(s, k)) for k, _ in s._fields_}
+
+
+_lib = None
+EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_set_options", "lns_timestep",
+           "lns_newton_iter", "lns_active_set", "lns_dd_expand", "lns_solve_local", "lns_assemble",
+           "lns_get_state", "lns_set_state", "lns_get_state_device", "lns_reset", "lns_get_support",
+           "lns_kernel_times", "lns_reset_kernel_times", "lns_last_error"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> C.CDLL:
+    """Load liblns.so (building it first when asked).  Raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblns.so is not built ({path}); run __graft_entry__.build() first")
+    L = C.CDLL(path)
+    vp, i32, f64 = C.c_void_p, C.c_int32, C.c_double
+    P = C.POINTER
+    sig = {
+        "lns_options_default": [P(lns_options)],
+        "lns_model_create": [P(lns_model_desc), P(lns_options), P(lns_allocator), vp, P(vp)],
+        "lns_model_destroy": [vp],
+        "lns_set_options": [vp, P(lns_options)],
+        "lns_timestep": [vp, f64, P(lns_step_stats)],
+        "lns_newton_iter": [vp, f64, P(lns_iter_stats)],
+        "lns_active_set": [vp, vp, vp, i32, i32, vp, vp, P(i32)],
+        "lns_dd_expand": [vp, vp, vp, i32, vp, vp, vp, vp, vp, P(i32)],
+        "lns_solve_local": [vp, f64, vp, vp, vp, P(lns_iter_stats)],
+        "lns_assemble": [vp, f64, vp, vp, vp, vp],
+        "lns_get_state": [vp, vp, vp],
+        "lns_set_state": [vp, vp, vp, vp, vp],
+        "lns_get_state_device": [vp, vp, vp],
+        "lns_reset": [vp],
+        "lns_get_support": [vp, vp],
+        "lns_kernel_times": [vp, P(lns_kernel_time), i32, P(i32)],
+        "lns_reset_kernel_times": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.lns_last_error.argtypes = []
+    L.lns_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow=()) -> int:
+    if rc != LNS_OK and rc not in allow:
+        msg = load().lns_last_error().decode(errors="replace")
+        raise LnsError(rc, msg)
+    return rc
+
+
+@dataclasses.dataclass
+class Options:
+    """Mirror of lns_options (SI units).  Defaults: Algorithm 1, eps = tol_dp = 0.3 psi, m = 2."""
+    mode: int = LNS_MODE_LOCAL
+    eps_p: float = 0.3 * PSI
+    eps_sw: float = 0.0
+    m_layers: int = 2
+    tol_dp: float = 0.3 * PSI
+    tol_cnv: float = 1e-6
+    max_newton: int = 25
+    max_dd_outer: int = 25
+    sat_chop: float = 0.2
+    krylov_fp32: int = 0
+    precond: int = LNS_PRECOND_BJAC
+    krylov_rtol: float = 1e-8
+    krylov_maxit: int = 2000
+    krylov_fail_rtol: float = 1e-3
+    p_scale: float = 0.0
+    profile: int = 0
+
+    def c(self) -> lns_options:
+        return lns_options(*[getattr(self, f.name) for f in dataclasses.fields(self)])
+
+
+def nwords(n: int) -> int:
+    return (n + 31) // 32
+
+
+def mask_to_bits(mask: np.ndarray) -> np.ndarray:
+    """Byte mask (n,) -> little-endian uint32 bitset words."""
+    mask = np.asarray(mask).astype(bool)
+    n = mask.shape[0]
+    pad = np.zeros(nwords(n) * 32, dtype=bool)
+    pad[:n] = mask
+    return np.packbits(pad.reshape(-1, 8), axis=1, bitorder="little").reshape(-1, 4).copy().view(np.uint32).ravel()
+
+
+def bits_to_mask(bits: np.ndarray, n: int) -> np.ndarray:
+    b = np.ascontiguousarray(bits, dtype=np.uint32).view(np.uint8)
+    return np.unpackbits(b, bitorder="little")[:n].astype(np.uint8)
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class Model:
+    """A model resident on the GPU (lns_model).  Methods call the C entry points."""
+
+    def __init__(self, case, opts: Optional[Options] = None, use_torch_allocator: bool = True, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblns needs a CUDA GPU")
+        L = load()
+        self.n = int(case.n)
+        self.n_adj = int(case.nbr.shape[0])
+        self.opts = opts or Options()
+        keep = dict(
+            row_ptr=np.ascontiguousarray(case.row_ptr, np.int32), nbr=np.ascontiguousarray(case.nbr, np.int32),
+            trans=np.ascontiguousarray(case.trans, np.float64), pv_ref=np.ascontiguousarray(case.pv_ref, np.float64),
+            depth=np.ascontiguousarray(case.depth, np.float64), line_id=np.ascontiguousarray(case.line_id, np.int32),
+            always=np.ascontiguousarray(case.always_active, np.uint8),
+            well_cell=np.ascontiguousarray(case.well_cell, np.int32),
+            well_wi=np.ascontiguousarray(case.well_wi, np.float64),
+            well_bhp=np.ascontiguousarray(case.well_bhp, np.float64),
+            p0=np.ascontiguousarray(case.p0, np.float64), sw0=np.ascontiguousarray(case.sw0, np.float64))
+        fl = case.fluid
+        desc = lns_model_desc(
+            self.n, self.n_adj, _ptr(keep["row_ptr"]), _ptr(keep["nbr"]), _ptr(keep["trans"]), _ptr(keep["pv_ref"]),
+            _ptr(keep["depth"]), _ptr(keep["line_id"]), _ptr(keep["always"]), int(case.well_cell.shape[0]),
+            _ptr(keep["well_cell"]), _ptr(keep["well_wi"]), _ptr(keep["well_bhp"]),
+            lns_fluid(fl.p_ref, fl.c_r, fl.b_o_ref, fl.c_o, fl.b_w_ref, fl.c_w, fl.rho_o_ref, fl.rho_w_ref,
+                      fl.mu_o, fl.mu_w, fl.swc, fl.sor, int(fl.n_w), int(fl.n_o), fl.gravity),
+            _ptr(keep["p0"]), _ptr(keep["sw0"]))
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self._alloc = None
+        if use_torch_allocator:
+            dev = torch.cuda.current_device()
+            tstream = self._stream
+
+            def _a(ctx, nbytes, s):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, tstream)
+                except Exception:  # out of memory is reported to the library as NULL
+                    return None
+
+            def _f(ctx, ptr, s):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (ALLOC_FN(_a), FREE_FN(_f))
+            self._alloc = lns_allocator(None, self._cb[0], self._cb[1])
+        h = C.c_void_p()
+        oc = self.opts.c()
+        _check(L.lns_model_create(C.byref(desc), C.byref(oc), C.byref(self._alloc) if self._alloc else None,
+                                  C.c_void_p(self._stream.cuda_stream), C.byref(h)))
+        self.h = h
+
+    # ---- lifecycle ----
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().lns_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, opts: Options) -> None:
+        self.opts = opts
+        oc = opts.c()
+        _check(load().lns_set_options(self.h, C.byref(oc)))
+
+    # ---- Newton ----
+    def lns_timestep(self, dt: float, allow_noconv: bool = False) -> Dict:
+        st = lns_step_stats()
+        rc = load().lns_timestep(self.h, float(dt), C.byref(st))
+        _check(rc, allow=(LNS_ENOCONV,) if allow_noconv else ())
+        d = _as_dict(st)
+        d["rc"] = rc
+        return d
+
+    def lns_newton_iter(self, dt: float) -> Dict:
+        st = lns_iter_stats()
+        _check(load().lns_newton_iter(self.h, float(dt), C.byref(st)))
+        return _as_dict(st)
+
+    def run(self, dts) -> List[Dict]:
+        return [self.lns_timestep(float(dt)) for dt in dts]
+
+    # ---- set logic ----
+    def lns_active_set(self, va_mask, dp, dsw=None, converged: bool = False) -> Tuple[np.ndarray, np.ndarray, int]:
+        va = mask_to_bits(va_mask)
+        vb = np.zeros_like(va)
+        dp = np.ascontiguousarray(dp, np.float64)
+        dsw = None if dsw is None else np.ascontiguousarray(dsw, np.float64)
+        ie = C.c_int32(0)
+        _check(load().lns_active_set(self.h, _ptr(dp), None if dsw is None else _ptr(dsw), 0, int(bool(converged)),
+                                     _ptr(va), _ptr(vb), C.byref(ie)))
+        return bits_to_mask(va, self.n), bits_to_mask(vb, self.n), int(ie.value)
+
+    def lns_dd_expand(self, vb_k_mask, dp, vt_mask, dsw=None):
+        vb = mask_to_bits(vb_k_mask)
+        vt = mask_to_bits(vt_mask)
+        va_n = np.zeros_like(vt)
+        vb_n = np.zeros_like(vt)
+        vd_n = np.zeros_like(vt)
+        dp = np.ascontiguousarray(dp, np.float64)
+        dsw = None if dsw is None else np.ascontiguousarray(dsw, np.float64)
+        ie = C.c_int32(0)
+        _check(load().lns_dd_expand(self.h, _ptr(dp), None if dsw is None else _ptr(dsw), 0, _ptr(vb), _ptr(vt),
+                                    _ptr(va_n), _ptr(vb_n), _ptr(vd_n), C.byref(ie)))
+        n = self.n
+        return (bits_to_mask(vt, n), bits_to_mask(va_n, n), bits_to_mask(vb_n, n), bits_to_mask(vd_n, n),
+                int(ie.value))
+
+    # ---- local solve / assembly ----
+    def lns_solve_local(self, dt: float, va_mask) -> Tuple[np.ndarray, np.ndarray, Dict]:
+        va = mask_to_bits(va_mask)
+        dp = np.zeros(self.n)
+        dsw = np.zeros(self.n)
+        st = lns_iter_stats()
+        _check(load().lns_solve_local(self.h, float(dt), _ptr(va), _ptr(dp), _ptr(dsw), C.byref(st)))
+        return dp, dsw, _as_dict(st)
+
+    def lns_assemble(self, dt: float, va_mask):
+        va = mask_to_bits(va_mask)
+        F = np.zeros((self.n, 2))
+        Jd = np.zeros((self.n, 2, 2))
+        Jo = np.zeros((max(self.n_adj, 1), 2, 2))
+        _check(load().lns_assemble(self.h, float(dt), _ptr(va), _ptr(F), _ptr(Jd), _ptr(Jo)))
+        return F, Jd, Jo[: self.n_adj]
+
+    # ---- state ----
+    def lns_get_state(self) -> Tuple[np.ndarray, np.ndarray]:
+        p = np.zeros(self.n)
+        sw = np.zeros(self.n)
+        _check(load().lns_get_state(self.h, _ptr(p), _ptr(sw)))
+        return p, sw
+
+    def lns_set_state(self, p, sw, pn=None, swn=None) -> None:
+        arrs = [None if a is None else np.ascontiguousarray(a, np.float64) for a in (p, sw, pn, swn)]
+        _check(load().lns_set_state(self.h, *[None if a is None else _ptr(a) for a in arrs]))
+
+    def lns_set_state_ptrs(self, p_ptr: int, sw_ptr: int) -> None:
+        """Host pointers (e.g. pinned torch tensors) of n doubles each."""
+        _check(load().lns_set_state(self.h, C.c_void_p(p_ptr), C.c_void_p(sw_ptr), None, None))
+
+    def lns_get_state_ptrs(self, p_ptr: int, sw_ptr: int) -> None:
+        _check(load().lns_get_state(self.h, C.c_void_p(p_ptr), C.c_void_p(sw_ptr)))
+
+    def lns_get_state_device(self, p_ptr: int, sw_ptr: int) -> None:
+        _check(load().lns_get_state_device(self.h, C.c_void_p(p_ptr), C.c_void_p(sw_ptr)))
+
+    def lns_reset(self) -> None:
+        _check(load().lns_reset(self.h))
+
+    def lns_get_support(self) -> np.ndarray:
+        bits = np.zeros(nwords(self.n), np.uint32)
+        _check(load().lns_get_support(self.h, _ptr(bits)))
+        return bits_to_mask(bits, self.n)
+
+    def lns_kernel_times(self) -> List[Dict]:
+        arr = (lns_kernel_time * 16)()
+        cnt = C.c_int32(0)
+        _check(load().lns_kernel_times(self.h, arr, 16, C.byref(cnt)))
+        return [_as_dict(arr[k]) for k in range(cnt.value)]
+
+    def lns_reset_kernel_times(self) -> None:
+        _check(load().lns_reset_kernel_times(self.h))

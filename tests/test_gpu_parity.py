@@ -1,0 +1,322 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact for the integer/set work (active sets, boundary sets, partitions); FP64 fields
+within 1e-7 relative of the oracle (tight Newton tolerance on both sides); FP32 Krylov
+(inexact Newton) within 1e-6.  Sizes span several tiles and ragged tails (n not a multiple
+of 32 or of the block size), plus the full-size 400x400 DFN model on sampled outputs.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2008_01539_gb300 import casegen as cg
+from paper_2008_01539_gb300 import lns
+
+pytestmark = pytest.mark.gpu
+PSI = cg.PSI
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need cuda:0"
+    lns.load(build_if_missing=True)
+    O.build()
+
+
+def _random_state(case, seed, mobile=True):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(3000.0, 5000.0, case.n) * PSI
+    sw = rng.uniform(0.3, 0.6, case.n) if mobile else np.full(case.n, 0.25)
+    pn = p + rng.uniform(-50.0, 50.0, case.n) * PSI
+    swn = sw + rng.uniform(-0.02, 0.02, case.n)
+    return p, sw, pn, swn
+
+
+def _cases():
+    c2 = cg.small_dfn()
+    c2.depth[:] = np.random.default_rng(4).uniform(2490.0, 2510.0, c2.n)  # gravity active
+    return [cg.small_dfn(), c2, cg.config0(), cg.grid_2d(7, 5)]
+
+
+# ---------------------------------------------------------------------------------------
+# Assembly (Appendix A) on a masked set of rows.
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("ci", range(4))
+def test_assembly_matches_oracle(ci):
+    case = _cases()[ci]
+    m = O.Model(case)
+    g = lns.Model(case, lns.Options())
+    rng = np.random.default_rng(ci)
+    p, sw, pn, swn = _random_state(case, ci)
+    dt = 3.0 * cg.DAY
+    F, Jd, Jo = O.assemble(m, p, sw, pn, swn, dt)
+    rows = np.repeat(np.arange(case.n), np.diff(case.row_ptr))
+    for frac in (1.0, 0.3, 0.0):
+        va = (rng.random(case.n) < frac).astype(np.uint8)
+        g.lns_set_state(p, sw, pn, swn)
+        Fg, Jdg, Jog = g.lns_assemble(dt, va)
+        act = va == 1
+        sF = np.abs(F).max(axis=0) + 1e-300
+        assert np.all(np.abs(Fg[act] - F[act]) <= 1e-11 * sF + 1e-12 * np.abs(F[act]))
+        assert np.all(Fg[~act] == 0.0)
+        sD = np.abs(Jd[act]).max(axis=(1, 2))[:, None, None] + 1e-300
+        assert np.all(np.abs(Jdg[act] - Jd[act]) <= 1e-11 * sD)
+        ea = act[rows]
+        sO = np.abs(Jd[rows[ea]]).max(axis=(1, 2))[:, None, None] + 1e-300
+        assert np.all(np.abs(Jog[ea] - Jo[ea]) <= 1e-11 * sO)
+    g.close()
+
+
+# ---------------------------------------------------------------------------------------
+# Active-set logic (Algorithm 1 lines 8-20): bit-exact on the same update vector.
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("ci", range(4))
+@pytest.mark.parametrize("layers", [0, 1, 2, 3])
+def test_active_set_bit_exact(ci, layers):
+    case = _cases()[ci]
+    om = O.Model(case)
+    oo = O.Options(mode=1, eps_p=2.0, m_layers=layers, eps_sw=0.05 if layers == 3 else 0.0)
+    g = lns.Model(case, lns.Options(mode=1, eps_p=2.0, m_layers=layers, eps_sw=oo.eps_sw))
+    rng = np.random.default_rng(10 * ci + layers)
+    for trial in range(5):
+        if trial == 0:
+            va = np.ones(case.n, np.uint8)
+        elif trial == 1:
+            va = np.zeros(case.n, np.uint8)
+        else:
+            va = O.dilate(om, case.always_active, trial - 2) | (rng.random(case.n) < 0.05).astype(np.uint8)
+        dp = rng.uniform(-4, 4, case.n) * (rng.random(case.n) < 0.4)
+        dsw = rng.uniform(-0.1, 0.1, case.n)
+        for conv in (False, True):
+            ref = O.active_set_update(om, oo, va, dp, dsw, conv)
+            got = g.lns_active_set(va, dp, dsw, conv)
+            assert np.array_equal(got[0], ref[0]), (trial, conv)
+            assert np.array_equal(got[1], ref[1]), (trial, conv)
+            assert got[2] == ref[2]
+    g.close()
+
+
+@pytest.mark.parametrize("ci", range(3))
+def test_dd_expand_bit_exact(ci):
+    case = _cases()[ci]
+    om = O.Model(case)
+    oo = O.Options(mode=2, eps_p=2.0, m_layers=2)
+    g = lns.Model(case, lns.Options(mode=2, eps_p=2.0, m_layers=2))
+    rng = np.random.default_rng(ci)
+    va = O.dilate(om, case.always_active, 1)
+    vt = va.copy()
+    vb = O.boundary(om, va)
+    for step in range(5):
+        dp = rng.uniform(-4, 4, case.n) * (rng.random(case.n) < 0.7)
+        ref = O.dd_expand(om, oo, vb, dp, np.zeros(case.n), vt)
+        got = g.lns_dd_expand(vb, dp, vt)
+        for a, b in zip(got[:4], ref[:4]):
+            assert np.array_equal(a, b), step
+        assert got[4] == ref[4]
+        if not ref[4]:
+            break
+        vt, vb = ref[0], ref[2]
+    g.close()
+
+
+# ---------------------------------------------------------------------------------------
+# Local solve J_A du_A = -F_A (Section 4.3) against the oracle's sparse LU.
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("ci", range(4))
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_solve_local_matches_oracle(ci, fp32):
+    case = _cases()[ci]
+    om = O.Model(case)
+    g = lns.Model(case, lns.Options(krylov_fp32=fp32, krylov_rtol=1e-6 if fp32 else 1e-12, krylov_maxit=5000))
+    p, sw = case.p0.copy(), case.sw0.copy()
+    pn, swn = p.copy(), sw.copy()
+    p = p - 30.0 * PSI * np.random.default_rng(ci).random(case.n)  # a non-trivial iterate
+    dt = 2.0 * cg.DAY
+    for va in (np.ones(case.n, np.uint8), O.dilate(om, case.always_active, 2)):
+        dpo, dso, _, _ = O.local_solve(om, O.Options(), p, sw, pn, swn, dt, va)
+        g.lns_set_state(p, sw, pn, swn)
+        dpg, dsg, st = g.lns_solve_local(dt, va)
+        assert st["n_active"] == int(va.sum())
+        tol = 2e-5 if fp32 else 1e-8
+        assert np.max(np.abs(dpg - dpo)) <= tol * np.max(np.abs(dpo)) + 1e-9
+        assert np.max(np.abs(dsg - dso)) <= tol * max(np.max(np.abs(dso)), 1e-12) + 1e-12
+        assert np.all(dpg[va == 0] == 0.0)
+    g.close()
+
+
+# ---------------------------------------------------------------------------------------
+# Whole timesteps: standard Newton, Algorithm 1, Algorithm 2.
+# ---------------------------------------------------------------------------------------
+TIGHT = dict(tol_dp=1.0, tol_cnv=1e-10)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_timesteps_match_oracle_fp64(mode):
+    case = cg.config0()
+    ref = O.Sim(case, O.Options(mode=mode, **TIGHT))
+    g = lns.Model(case, lns.Options(mode=mode, krylov_rtol=1e-12, krylov_maxit=5000, **TIGHT))
+    for dt in case.dt_schedule:
+        a = g.lns_timestep(dt)
+        b = ref.timestep(dt)
+        assert a["status"] == 0 and b["status"] == 0
+        assert abs(a["iterations"] - b["iterations"]) <= 1, (a, b)
+        p, sw = g.lns_get_state()
+        assert np.max(np.abs(p - ref.p) / ref.p) < 1e-7
+        assert np.max(np.abs(sw - ref.sw)) < 1e-7 * 0.25
+    assert np.array_equal(g.lns_get_support(), ref.prev_supp)
+    g.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_timesteps_fp32_krylov_within_1e6(mode):
+    case = cg.config0()
+    ref = O.Sim(case, O.Options(mode=mode, **TIGHT))
+    g = lns.Model(case, lns.Options(mode=mode, krylov_fp32=1, krylov_rtol=1e-5, **TIGHT))
+    for dt in case.dt_schedule:
+        assert g.lns_timestep(dt)["status"] == 0
+        ref.timestep(dt)
+    p, sw = g.lns_get_state()
+    assert np.max(np.abs(p - ref.p) / ref.p) < 1e-6
+    assert np.max(np.abs(sw - ref.sw)) < 1e-6 * 0.25
+    g.close()
+
+
+def test_newton_iter_steps_through_algorithm1():
+    case = cg.small_dfn(n_steps=2)
+    ref = O.Sim(case, O.Options(mode=1, **TIGHT))
+    g = lns.Model(case, lns.Options(mode=1, krylov_rtol=1e-12, **TIGHT))
+    b = ref.timestep(case.dt_schedule[0])
+    sizes = []
+    while True:
+        st = g.lns_newton_iter(case.dt_schedule[0])
+        sizes.append(st["n_active"])
+        if st["step_done"]:
+            break
+    assert sizes == b["trace"]
+    g.close()
+
+
+def test_localized_matches_full_newton_gpu():
+    case = cg.config0()
+    full = lns.Model(case, lns.Options(mode=0))
+    loc = lns.Model(case, lns.Options(mode=1))
+    it_f = it_l = 0
+    cu_l = 0
+    for dt in case.dt_schedule:
+        a = full.lns_timestep(dt)
+        b = loc.lns_timestep(dt)
+        it_f += a["iterations"]
+        it_l += b["iterations"]
+        cu_l += b["cell_updates"]
+    pf, swf = full.lns_get_state()
+    pl, swl = loc.lns_get_state()
+    assert np.max(np.abs(pf - pl)) < 0.3 * PSI  # within the Newton tolerance
+    assert abs(it_f - it_l) <= max(2, it_f // 10)
+    assert cu_l < 0.2 * it_f * case.n
+    full.close()
+    loc.close()
+
+
+# ---------------------------------------------------------------------------------------
+# Edge cases.
+# ---------------------------------------------------------------------------------------
+def test_empty_active_set_and_no_well_equilibrium():
+    case = cg.grid_2d(6, 5, with_well=False)
+    g = lns.Model(case, lns.Options(mode=1))
+    dp, dsw, st = g.lns_solve_local(cg.DAY, np.zeros(case.n, np.uint8))
+    assert st["n_active"] == 0 and not dp.any()
+    for mode in (0, 1, 2):
+        g.set_options(lns.Options(mode=mode))
+        g.lns_reset()
+        st = g.lns_timestep(cg.DAY)
+        assert st["status"] == 0 and st["iterations"] == 1
+        p, sw = g.lns_get_state()
+        assert np.array_equal(p, case.p0) and np.array_equal(sw, case.sw0)
+    g.close()
+
+
+def test_empty_model():
+    case = cg.grid_2d(2, 2, with_well=False)
+    empty = dataclasses.replace(case, n=0, row_ptr=np.zeros(1, np.int32), nbr=np.zeros(0, np.int32),
+                                trans=np.zeros(0), pv_ref=np.zeros(0), depth=np.zeros(0),
+                                line_id=np.zeros(0, np.int32), always_active=np.zeros(0, np.uint8),
+                                p0=np.zeros(0), sw0=np.zeros(0))
+    g = lns.Model(empty, lns.Options())
+    st = g.lns_timestep(cg.DAY)
+    assert st["status"] == 0 and st["iterations"] == 0
+    g.close()
+
+
+def test_invalid_inputs_are_rejected():
+    case = cg.small_dfn()
+    bad = dataclasses.replace(case, nbr=case.nbr.copy())
+    bad.nbr[3] = case.n + 5
+    with pytest.raises(lns.LnsError) as e:
+        lns.Model(bad, lns.Options())
+    assert e.value.status == lns.LNS_EINVAL
+    g = lns.Model(case, lns.Options())
+    with pytest.raises(lns.LnsError):
+        g.lns_timestep(-1.0)
+    with pytest.raises(lns.LnsError):
+        g.set_options(lns.Options(mode=7))
+    g.close()
+
+
+# ---------------------------------------------------------------------------------------
+# Full-size 400x400 DFN model (the benchmark workload), same launch configuration.
+# ---------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def big():
+    return cg.config1()
+
+
+def test_config1_assembly_sampled_rows(big):
+    case = big
+    m = O.Model(case)
+    p, sw, pn, swn = _random_state(case, 7, mobile=False)
+    dt = 10 * cg.DAY
+    F, Jd, Jo = O.assemble(m, p, sw, pn, swn, dt)
+    g = lns.Model(case, lns.Options())
+    g.lns_set_state(p, sw, pn, swn)
+    va = np.ones(case.n, np.uint8)
+    Fg, Jdg, Jog = g.lns_assemble(dt, va)
+    rows = np.random.default_rng(0).choice(case.n, 4000, replace=False)
+    sF = np.abs(F).max(axis=0)
+    assert np.all(np.abs(Fg[rows] - F[rows]) <= 1e-11 * sF + 1e-12 * np.abs(F[rows]))
+    sD = np.abs(Jd[rows]).max(axis=(1, 2))[:, None, None]
+    assert np.all(np.abs(Jdg[rows] - Jd[rows]) <= 1e-11 * sD)
+    g.close()
+
+
+def test_config1_active_set_bit_exact(big):
+    case = big
+    om = O.Model(case)
+    oo = O.Options(mode=1)
+    g = lns.Model(case, lns.Options(mode=1))
+    rng = np.random.default_rng(3)
+    va = O.dilate(om, case.always_active, 2)
+    dp = rng.uniform(-2, 2, case.n) * oo.eps_p
+    for conv in (False, True):
+        ref = O.active_set_update(om, oo, va, dp, np.zeros(case.n), conv)
+        got = g.lns_active_set(va, dp, None, conv)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]) and got[2] == ref[2]
+    g.close()
+
+
+def test_config1_first_steps_match_oracle(big):
+    case = big
+    ref = O.Sim(case, O.Options(mode=1, tol_dp=1.0, tol_cnv=1e-9))
+    g = lns.Model(case, lns.Options(mode=1, tol_dp=1.0, tol_cnv=1e-9, krylov_rtol=1e-12, krylov_maxit=10000))
+    for dt in case.dt_schedule[:3]:
+        a = g.lns_timestep(dt)
+        b = ref.timestep(dt)
+        assert a["status"] == 0 and b["status"] == 0
+        assert abs(a["iterations"] - b["iterations"]) <= 1
+    p, sw = g.lns_get_state()
+    assert np.max(np.abs(p - ref.p) / ref.p) < 1e-7
+    assert np.max(np.abs(sw - ref.sw)) < 1e-7 * 0.25
+    g.close()
