@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark of the localized Newton solver (Algorithm 1) on the 400x400 + DFN model.
+
+One step = one whole simulation case: the 40 timesteps (0.01 d growing to 30 d, 365 d in
+total) of the 400x400-cell matrix with a 300-segment natural fracture network and four
+80-cell hydraulic fractures on a producer at 1500 psi (166,659 cells), FP64 throughout,
+started from the initial state.  The headline value is cell-Newton-updates per second
+(the sum over Newton iterations of the active-set size n_A, divided by the case time).
+The same case with standard (full-domain) Newton on the same GPU, the end-to-end figure
+through the C ABI with host buffers, the roofline of the dominant kernel, the CPU oracle
+on a bounded sample of the same workload, and the SM clocks are reported beside it.
+
+Multi-GPU: the path does not shard (one model per process), so N GPUs run N independent
+replicas ("weak" scaling); rank 0 prints the aggregate.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-Newton-updates/s & case time, localized vs full Newton; p99 req latency"
+UNIT = "cell-Newton-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (vector and tensor), see the design doc
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["local", "full", "dd"], default="local",
+                    help="solver whose case is the headline (default: Algorithm 1)")
+    ap.add_argument("--case", choices=["config1", "config0"], default="config1")
+    ap.add_argument("--fp32-krylov", action="store_true", help="FP32 BiCGStab (inexact Newton)")
+    ap.add_argument("--precond", choices=["lines", "cells"], default="lines",
+                    help="block Jacobi with fracture-segment blocks (default) or single-cell blocks")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="run only the headline case (for profiler launch lists)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    return ap.parse_args()
+
+
+def make_case(name):
+    from paper_2008_01539_gb300 import casegen as cg
+
+    return cg.config1() if name == "config1" else cg.config0()
+
+
+def workload_name(case, args):
+    mode = {"local": "localized Newton (Algorithm 1, m=2, eps=0.3 psi)", "full": "standard Newton",
+            "dd": "adaptive nonlinear DD (Algorithm 2, m=2)"}[args.mode]
+    meta = case.meta
+    return (f"{meta['nx']}x{meta['ny']} matrix ({meta['dx']:.0f} m cells) + {meta['n_segments'] - meta['n_hf']}-segment "
+            f"DFN + {meta['n_hf']} hydraulic fractures, n={case.n} cells, {len(case.dt_schedule)} timesteps to "
+            f"{case.dt_schedule.sum() / 86400:.0f} d, {mode}, {'FP32 Krylov' if args.fp32_krylov else 'FP64'}")
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------------------
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    return _reduce(x, world, "max")
+
+
+def reduce_sum(x, world):
+    return _reduce(x, world, "sum")
+
+
+def _reduce(x, world, op):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_krylov.cu", "k_assemble.cu", "k_sets.cu", "lns_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2008_01539_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class, alg_bytes_per_launch):
+    """DRAM bytes per launch: the ncu capture's DRAM/algorithmic byte ratio (profiles/
+    traffic.json) applied to this launch's algorithmic bytes, i.e. scaled by the rows and
+    iterations the launch processes.  None when absent or when the kernel sources changed
+    since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    k = d.get("kernels", {}).get(kernel_class)
+    if not k or d.get("source_hash") != kernel_source_hash():
+        return None
+    return k["dram_over_algorithmic"] * alg_bytes_per_launch
+
+
+def run_case(model, case):
+    """All timesteps of the case from the model's current state; returns the step stats."""
+    out = []
+    for dt in case.dt_schedule:
+        st = model.lns_timestep(float(dt))
+        out.append(st)
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle: bounded sample of the same workload
+# ---------------------------------------------------------------------------------------
+def oracle_sample(case, mode, budget_s, max_steps=None):
+    import oracle as O
+
+    mode_id = {"local": 1, "full": 0, "dd": 2}[mode]
+    sim = O.Sim(case, O.Options(mode=mode_id))
+    updates = 0
+    steps = 0
+    t0 = time.perf_counter()
+    for dt in case.dt_schedule:
+        st = sim.timestep(float(dt))
+        updates += st["cell_updates"]
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s or (max_steps and steps >= max_steps):
+            break
+    el = time.perf_counter() - t0
+    return updates, el, steps
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the CPU oracle, timed on the host cores
+# ---------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    case = make_case(args.case)
+    # one step = the first `steps_per_sample` timesteps of the case, sized to a few seconds
+    probe_u, probe_t, probe_steps = oracle_sample(case, args.mode, 4.0)
+    n_ts = max(1, probe_steps)
+    for _ in range(args.warmup):
+        oracle_sample(case, args.mode, 1e9, max_steps=n_ts)
+    times, ups = [], []
+    for _ in range(args.steps):
+        u, t, _ = oracle_sample(case, args.mode, 1e9, max_steps=n_ts)
+        times.append(t)
+        ups.append(u)
+    value = sum(ups) / sum(times)
+    sample = f"first {n_ts} of {len(case.dt_schedule)} timesteps of the case, oracle mode {args.mode}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(case, args) + "; CPU oracle (plain C, hand-written sparse LU)",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    from paper_2008_01539_gb300 import lns
+
+    rank, world, local = dist_setup(args)
+    lns.load(build_if_missing=True)
+    case = make_case(args.case)
+    mode_id = {"local": lns.LNS_MODE_LOCAL, "full": lns.LNS_MODE_FULL, "dd": lns.LNS_MODE_DD}[args.mode]
+    opts = lns.Options(mode=mode_id, krylov_fp32=int(args.fp32_krylov),
+                       krylov_rtol=1e-5 if args.fp32_krylov else 1e-8,
+                       precond=lns.LNS_PRECOND_BJAC if args.precond == "lines" else lns.LNS_PRECOND_BJAC_CELL)
+    stream = torch.cuda.current_stream()
+    model = lns.Model(case, opts)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        model.lns_reset()
+        run_case(model, case)
+    torch.cuda.synchronize()
+
+    # timed region: K cases, inputs resident, L2 flushed before each case
+    model.set_options(lns.Options(**{**opts.__dict__, "profile": 1}))
+    model.lns_reset_kernel_times()
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lns.lns_launch_count()
+    ev = []
+    updates = 0
+    iters = 0
+    kry = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        model.lns_reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = run_case(model, case)
+        e1.record(stream)
+        ev.append((e0, e1))
+        updates += sum(s["cell_updates"] for s in stats)
+        iters += sum(s["iterations"] for s in stats)
+        kry += sum(s["krylov_iters"] for s in stats)
+    torch.cuda.synchronize()
+    launches = lns.lns_launch_count() - launches0
+    clk = clocks.stop()
+    barrier(world)
+    t_rank = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    t_max = reduce_max(t_rank, world)
+    updates_all = reduce_sum(updates, world)
+    value = updates_all / t_max
+    ktimes = model.lns_kernel_times()
+    model.set_options(opts)
+    p_final, sw_final = model.lns_get_state()
+
+    # roofline of the dominant kernel (live CUDA-event timing inside the timed region)
+    hbm, hbm_src = measured_peaks()
+    dom = max(ktimes, key=lambda k: k["total_ms"])
+    per_launch_s = dom["total_ms"] / 1e3 / max(dom["launches"], 1)
+    bytes_per_launch = dom["bytes"] / max(dom["launches"], 1)
+    achieved = bytes_per_launch / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": ncu_traffic(dom["name"], bytes_per_launch), "kernel": dom["name"],
+            "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
+            "fp64_tflops": dom["flops"] / max(dom["total_ms"], 1e-9) / 1e9,
+            "fp64_frac_of_nominal": dom["flops"] / max(dom["total_ms"], 1e-9) / 1e9 / FP64_PEAK_TFLOPS,
+            "share_of_case": dom["total_ms"] / 1e3 / max(t_rank, 1e-12)}
+    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
+                           "GBps": (k["bytes"] / (k["total_ms"] / 1e3) / 1e9) if k["total_ms"] > 0 else None}
+               for k in ktimes}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32-krylov/f64" if args.fp32_krylov else "f64",
+            "data": "synthetic (seeded generator shaped like the paper's DFN models)",
+            "config": {"workload": workload_name(case, args), "cells": case.n, "timesteps": len(case.dt_schedule),
+                       "l2": "flushed (256 MB write) before every timed case", "parallelism": f"replicas x{world}"},
+            "case_time_s": t_max / max(args.steps, 1),
+            "newton_iterations_per_case": iters / max(args.steps, 1),
+            "krylov_iterations_per_case": kry / max(args.steps, 1),
+            "M_A_per_case": updates / max(args.steps, 1) / case.n,
+            "gpu_launches": launches, "kernels": kernels, "roofline": roof, "clocks": clk}
+
+    if not args.headline_only:
+        # standard Newton on the same GPU, same case
+        if args.mode != "full":
+            fopts = lns.Options(**{**opts.__dict__, "mode": lns.LNS_MODE_FULL})
+            fm = lns.Model(case, fopts)
+            fm.lns_reset()
+            run_case(fm, case)  # warm-up
+            ft, fu, fi = [], 0, 0
+            for _ in range(max(1, min(args.steps, 3))):
+                flush.zero_()
+                fm.lns_reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = run_case(fm, case)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ft.append(e0.elapsed_time(e1) / 1e3)
+                fu += sum(s["cell_updates"] for s in st)
+                fi += sum(s["iterations"] for s in st)
+            pf, _ = fm.lns_get_state()
+            fm.close()
+            tf = statistics.mean(ft)
+            line["full_newton"] = {"case_time_s": tf, "value": fu / sum(ft), "unit": UNIT,
+                                   "newton_iterations_per_case": fi / len(ft),
+                                   "max_abs_dp_vs_localized_psi": float(np.max(np.abs(pf - p_final))) / lns.PSI}
+            line["speedup_vs_full_newton"] = tf / line["case_time_s"]
+        # end to end through the C ABI with host buffers
+        p_h = torch.from_numpy(np.ascontiguousarray(case.p0)).pin_memory()
+        s_h = torch.from_numpy(np.ascontiguousarray(case.sw0)).pin_memory()
+        po = torch.empty(case.n, dtype=torch.float64).pin_memory()
+        so = torch.empty(case.n, dtype=torch.float64).pin_memory()
+        e2e_t, e2e_u = [], 0
+        barrier(world)
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            model.lns_set_state_ptrs(p_h.data_ptr(), s_h.data_ptr())
+            st = run_case(model, case)
+            model.lns_get_state_ptrs(po.data_ptr(), so.data_ptr())
+            e2e_t.append(time.perf_counter() - t0)
+            e2e_u += sum(s["cell_updates"] for s in st)
+        te = reduce_max(sum(e2e_t), world)
+        line["e2e"] = {"value": reduce_sum(e2e_u, world) / te, "unit": UNIT,
+                       "h2d_bytes_per_step": 2 * 8 * case.n, "d2h_bytes_per_step": 2 * 8 * case.n,
+                       "case_time_s": te / max(args.steps, 1)}
+        # CPU oracle on the host cores, bounded sample (rank 0, N = 1)
+        if rank == 0 and world == 1:
+            u, t, n_ts = oracle_sample(case, args.mode, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": u / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"first {n_ts} of {len(case.dt_schedule)} timesteps of the same case, "
+                                              f"oracle mode {args.mode} (plain C, single thread), {t:.1f} s"}
+    model.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -50,7 +50,11 @@ typedef enum {
 } lns_status;
 
 enum { LNS_MODE_FULL = 0, LNS_MODE_LOCAL = 1, LNS_MODE_DD = 2 };
-enum { LNS_PRECOND_BJAC = 0 /* block Jacobi; fracture segments as block-tridiagonal blocks */ };
+enum {
+  LNS_PRECOND_BJAC = 0,     /* block Jacobi whose blocks are single cells and whole fracture segments
+                               (block tridiagonal along each segment) */
+  LNS_PRECOND_BJAC_CELL = 1 /* block Jacobi with 2x2 single-cell blocks only */
+};
 
 /* Fluid and rock.  b_l(p) = b_l_ref (1 + c_l (p - p_ref)) (inverse formation volume
  * factor), rho_l = rho_l_ref b_l, pore volume PV_ref (1 + c_r (p - p_ref)), Corey
@@ -216,6 +220,9 @@ lns_status lns_get_support(const lns_model* model, uint32_t* bits);
 /* Kernel timing (options.profile = 1): up to cap entries, *count gets the number. */
 lns_status lns_kernel_times(const lns_model* model, lns_kernel_time* out, int32_t cap, int32_t* count);
 lns_status lns_reset_kernel_times(lns_model* model);
+
+/* Number of CUDA kernels the library has launched in this process (all models). */
+int64_t lns_launch_count(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* lns_last_error(void);

@@ -14,8 +14,10 @@
 // (p_scale dp, dSw).  All residual, flux and accumulation arithmetic is FP64; the scaled
 // blocks and right-hand side are stored in T (FP64, or FP32 for the inexact-Newton path).
 //
-// Mapping: LPR lanes per row (one lane per connection of the row), warp-uniform loops so the
-// lane groups can reduce with shuffles.
+// Mapping: one thread per active row (each cell's properties evaluated once per use, no
+// redundant FP64 work: FP64 issues at a small fraction of the FP32 rate on this GPU).  The
+// boundary set V_B of the solved set (rows with an inactive neighbour) falls out of the
+// column scan and is written here too.
 #include <cuda_runtime.h>
 
 #include "lns_internal.cuh"
@@ -24,7 +26,6 @@ namespace lns {
 
 namespace {
 
-constexpr int kLPR = 8;   // lanes per row
 constexpr int kAsmBlk = 256;
 
 struct FluidK {
@@ -76,168 +77,135 @@ __device__ __forceinline__ void cell_props(const FluidK& F, double pv_ref, doubl
 __device__ __forceinline__ bool bit(const uint32_t* s, int i) { return (s[i >> 5] >> (i & 31)) & 1u; }
 
 template <typename T>
-struct Blk4 {
+struct alignas(4 * sizeof(T)) Blk4 {
   T a, b, c, d;
 };
 
-template <typename T, int LPR>
+// One thread per active row.  Pass 1 evaluates the row's fluxes, accumulation and wells in
+// FP64, writes the raw off-diagonal blocks and marks the row as a boundary cell (V_B: an
+// inactive neighbour); pass 2 scales the row by S D^{-1} in place.
+template <typename T>
 __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt, double p_scale, int debug) {
   const int nA = d.ctr->n_active;
-  const int lane = threadIdx.x & 31;
-  const int q = lane % LPR;                       // lane within the row group
-  const int grp = lane / LPR;                     // row group within the warp
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const double inv_dt = 1.0 / dt;
   const double g = F.f.gravity;
   T* blocks = (T*)d.blocks;
+  double* raw = sizeof(T) == sizeof(double) ? (double*)d.blocks : d.raw;
   T* rhs = (T*)d.rhs;
   double cnv_max = 0.0;
-  for (int base = gwarp * (32 / LPR); base < nA; base += warps * (32 / LPR)) {
-    const int k = base + grp;
-    const bool valid = k < nA;
-    double R0 = 0.0, R1 = 0.0, D00 = 0.0, D01 = 0.0, D10 = 0.0, D11 = 0.0;
-    double O00 = 0.0, O01 = 0.0, O10 = 0.0, O11 = 0.0;
-    int i = 0, e0 = 0, e1 = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nA; k += gridDim.x * blockDim.x) {
+    const int i = d.act[k];
+    const int e0 = d.row_ptr[i], e1 = d.row_ptr[i + 1];
+    const double p_i = d.p[i], sw_i = d.sw[i], z_i = d.depth[i];
     Props qi;
-    if (valid) {
-      i = d.act[k];
-      e0 = d.row_ptr[i];
-      e1 = d.row_ptr[i + 1];
-      const double p_i = d.p[i], sw_i = d.sw[i], z_i = d.depth[i];
-      cell_props(F, d.pv_ref[i], p_i, sw_i, qi);
-      for (int e = e0 + q, round = 0; e < e1; e += LPR, round++) {
-        const int j = d.nbr[e];
-        const double T_e = d.trans[e];
-        Props qj;
-        const double p_j = d.p[j];
-        cell_props(F, d.pv_ref[j], p_j, d.sw[j], qj);
-        const double dz = z_i - d.depth[j];
-        const double dpp = p_i - p_j;
-        double o[4] = {0.0, 0.0, 0.0, 0.0};
-        double Rl[2] = {0.0, 0.0}, Dl[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    cell_props(F, d.pv_ref[i], p_i, sw_i, qi);
+    double R0, R1, D00, D01, D10, D11;
+    {  // accumulation
+      Props qn;
+      const double swn = d.swn[i];
+      cell_props(F, d.pv_ref[i], d.pn[i], swn, qn);
+      const double so = 1.0 - sw_i, son = 1.0 - swn;
+      R0 = (qi.pv * qi.b[0] * so - qn.pv * qn.b[0] * son) * inv_dt;
+      R1 = (qi.pv * qi.b[1] * sw_i - qn.pv * qn.b[1] * swn) * inv_dt;
+      D00 = (qi.dpv * qi.b[0] + qi.pv * qi.db[0]) * so * inv_dt;
+      D01 = -qi.pv * qi.b[0] * inv_dt;
+      D10 = (qi.dpv * qi.b[1] + qi.pv * qi.db[1]) * sw_i * inv_dt;
+      D11 = qi.pv * qi.b[1] * inv_dt;
+    }
+    bool edge = false;
+    for (int e = e0; e < e1; e++) {
+      const int j = d.nbr[e];
+      const double T_e = d.trans[e];
+      const double p_j = d.p[j];
+      Props qj;
+      cell_props(F, d.pv_ref[j], p_j, d.sw[j], qj);
+      const double dz = z_i - d.depth[j];
+      const double dpp = p_i - p_j;
+      double o[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int l = 0; l < 2; l++) {
-          const double rho_avg = 0.5 * (qi.rho[l] + qj.rho[l]);
-          const double dphi = dpp - (g * rho_avg) * dz;
-          const bool up_i = dphi > 0.0 || (dphi == 0.0 && i < j);
-          const double tm = T_e * (up_i ? qi.mob[l] : qj.mob[l]);
-          Rl[l] = tm * dphi;
-          Dl[l][0] = tm * (1.0 - g * dz * 0.5 * qi.drho[l]);
-          o[2 * l] = tm * (-1.0 - g * dz * 0.5 * qj.drho[l]);
-          if (up_i) {
-            Dl[l][0] += T_e * qi.dmob_dp[l] * dphi;
-            Dl[l][1] = T_e * qi.dmob_ds[l] * dphi;
-          } else {
-            o[2 * l] += T_e * qj.dmob_dp[l] * dphi;
-            o[2 * l + 1] = T_e * qj.dmob_ds[l] * dphi;
-          }
+      for (int l = 0; l < 2; l++) {
+        const double rho_avg = 0.5 * (qi.rho[l] + qj.rho[l]);
+        const double dphi = dpp - (g * rho_avg) * dz;
+        const bool up_i = dphi > 0.0 || (dphi == 0.0 && i < j);
+        const double tm = T_e * (up_i ? qi.mob[l] : qj.mob[l]);
+        const double rl = tm * dphi;
+        const double dl0 = tm * (1.0 - g * dz * 0.5 * qi.drho[l]);
+        o[2 * l] = tm * (-1.0 - g * dz * 0.5 * qj.drho[l]);
+        double dl0u = 0.0, dl1 = 0.0;
+        if (up_i) {
+          dl0u = T_e * qi.dmob_dp[l] * dphi;
+          dl1 = T_e * qi.dmob_ds[l] * dphi;
+        } else {
+          o[2 * l] += T_e * qj.dmob_dp[l] * dphi;
+          o[2 * l + 1] = T_e * qj.dmob_ds[l] * dphi;
         }
-        R0 += Rl[0];
-        R1 += Rl[1];
-        D00 += Dl[0][0];
-        D01 += Dl[0][1];
-        D10 += Dl[1][0];
-        D11 += Dl[1][1];
-        d.colA[e] = bit(d.va, j) ? d.inv[j] : -1;
-        if (debug) {
-          d.dbg_off[4 * (size_t)e + 0] = o[0];
-          d.dbg_off[4 * (size_t)e + 1] = o[1];
-          d.dbg_off[4 * (size_t)e + 2] = o[2];
-          d.dbg_off[4 * (size_t)e + 3] = o[3];
-        }
-        if (round == 0) {
-          O00 = o[0];
-          O01 = o[1];
-          O10 = o[2];
-          O11 = o[3];
-        } else {  // rows with more than LPR connections: park the raw block, scale it below
-          Blk4<T> bk = {(T)o[0], (T)o[1], (T)o[2], (T)o[3]};
-          *(Blk4<T>*)&blocks[4 * (size_t)e] = bk;
+        if (l == 0) {
+          R0 += rl;
+          D00 += dl0 + dl0u;
+          D01 += dl1;
+        } else {
+          R1 += rl;
+          D10 += dl0 + dl0u;
+          D11 += dl1;
         }
       }
-      if (q == 0) {
-        // accumulation
-        Props qn;
-        const double sw_i2 = d.sw[i], swn = d.swn[i];
-        cell_props(F, d.pv_ref[i], d.pn[i], swn, qn);
-        const double so = 1.0 - sw_i2, son = 1.0 - swn;
-        R0 += (qi.pv * qi.b[0] * so - qn.pv * qn.b[0] * son) * inv_dt;
-        R1 += (qi.pv * qi.b[1] * sw_i2 - qn.pv * qn.b[1] * swn) * inv_dt;
-        D00 += (qi.dpv * qi.b[0] + qi.pv * qi.db[0]) * so * inv_dt;
-        D01 += -qi.pv * qi.b[0] * inv_dt;
-        D10 += (qi.dpv * qi.b[1] + qi.pv * qi.db[1]) * sw_i2 * inv_dt;
-        D11 += qi.pv * qi.b[1] * inv_dt;
-        // producers
-        for (int w = d.well_of_cell[i]; w >= 0; w = d.well_next[w]) {
-          const double dpw = d.p[i] - d.well_bhp[w];
-          if (dpw > 0.0) {
-            const double wi = d.well_wi[w];
-            R0 += wi * qi.mob[0] * dpw;
-            R1 += wi * qi.mob[1] * dpw;
-            D00 += wi * (qi.dmob_dp[0] * dpw + qi.mob[0]);
-            D01 += wi * qi.dmob_ds[0] * dpw;
-            D10 += wi * (qi.dmob_dp[1] * dpw + qi.mob[1]);
-            D11 += wi * qi.dmob_ds[1] * dpw;
-          }
-        }
-      }
-    }
-    // sum the row over its lane group
-#pragma unroll
-    for (int o = LPR / 2; o > 0; o >>= 1) {
-      R0 += __shfl_xor_sync(0xffffffffu, R0, o, LPR);
-      R1 += __shfl_xor_sync(0xffffffffu, R1, o, LPR);
-      D00 += __shfl_xor_sync(0xffffffffu, D00, o, LPR);
-      D01 += __shfl_xor_sync(0xffffffffu, D01, o, LPR);
-      D10 += __shfl_xor_sync(0xffffffffu, D10, o, LPR);
-      D11 += __shfl_xor_sync(0xffffffffu, D11, o, LPR);
-    }
-    if (!valid) continue;
-    const double det = D00 * D11 - D01 * D10;
-    const double id = 1.0 / det;
-    const double I00 = D11 * id, I01 = -D01 * id, I10 = -D10 * id, I11 = D00 * id;
-    if (q == 0) {
-      rhs[2 * (size_t)k] = (T)(-p_scale * (I00 * R0 + I01 * R1));
-      rhs[2 * (size_t)k + 1] = (T)(-(I10 * R0 + I11 * R1));
-      const double c0 = fabs(R0) * dt / (qi.pv * qi.b[0]);
-      const double c1 = fabs(R1) * dt / (qi.pv * qi.b[1]);
-      cnv_max = fmax(cnv_max, fmax(c0, c1));
+      const bool in = bit(d.va, j);
+      edge |= !in;
+      d.colA[e] = in ? d.inv[j] : -1;
       if (debug) {
-        d.resid[2 * (size_t)i] = R0;
-        d.resid[2 * (size_t)i + 1] = R1;
-        d.dbg_diag[4 * (size_t)i + 0] = D00;
-        d.dbg_diag[4 * (size_t)i + 1] = D01;
-        d.dbg_diag[4 * (size_t)i + 2] = D10;
-        d.dbg_diag[4 * (size_t)i + 3] = D11;
+        d.dbg_off[4 * (size_t)e + 0] = o[0];
+        d.dbg_off[4 * (size_t)e + 1] = o[1];
+        d.dbg_off[4 * (size_t)e + 2] = o[2];
+        d.dbg_off[4 * (size_t)e + 3] = o[3];
+      }
+      if (in) {  // raw block in FP64 until it is scaled (FP32 rounding before D^{-1} could cancel)
+        Blk4<double> bk = {o[0], o[1], o[2], o[3]};
+        *(Blk4<double>*)&raw[4 * (size_t)e] = bk;
       }
     }
-    const double sp = p_scale, isp = 1.0 / p_scale;
-    for (int e = e0 + q, round = 0; e < e1; e += LPR, round++) {
-      double o0, o1, o2, o3;
-      if (round == 0) {
-        o0 = O00;
-        o1 = O01;
-        o2 = O10;
-        o3 = O11;
-      } else {
-        Blk4<T> bk = *(const Blk4<T>*)&blocks[4 * (size_t)e];
-        o0 = bk.a;
-        o1 = bk.b;
-        o2 = bk.c;
-        o3 = bk.d;
+    if (edge) atomicOr(&d.vb[i >> 5], 1u << (i & 31));
+    // producers
+    for (int w = d.well_of_cell[i]; w >= 0; w = d.well_next[w]) {
+      const double dpw = p_i - d.well_bhp[w];
+      if (dpw > 0.0) {
+        const double wi = d.well_wi[w];
+        R0 += wi * qi.mob[0] * dpw;
+        R1 += wi * qi.mob[1] * dpw;
+        D00 += wi * (qi.dmob_dp[0] * dpw + qi.mob[0]);
+        D01 += wi * qi.dmob_ds[0] * dpw;
+        D10 += wi * (qi.dmob_dp[1] * dpw + qi.mob[1]);
+        D11 += wi * qi.dmob_ds[1] * dpw;
       }
-      // S D^{-1} O S^{-1}
+    }
+    const double id = 1.0 / (D00 * D11 - D01 * D10);
+    const double I00 = D11 * id, I01 = -D01 * id, I10 = -D10 * id, I11 = D00 * id;
+    rhs[2 * (size_t)k] = (T)(-p_scale * (I00 * R0 + I01 * R1));
+    rhs[2 * (size_t)k + 1] = (T)(-(I10 * R0 + I11 * R1));
+    cnv_max = fmax(cnv_max, fmax(fabs(R0) * dt / (qi.pv * qi.b[0]), fabs(R1) * dt / (qi.pv * qi.b[1])));
+    if (debug) {
+      d.resid[2 * (size_t)i] = R0;
+      d.resid[2 * (size_t)i + 1] = R1;
+      d.dbg_diag[4 * (size_t)i + 0] = D00;
+      d.dbg_diag[4 * (size_t)i + 1] = D01;
+      d.dbg_diag[4 * (size_t)i + 2] = D10;
+      d.dbg_diag[4 * (size_t)i + 3] = D11;
+    }
+    // pass 2: S D^{-1} O S^{-1} on the blocks of active columns
+    const double sp = p_scale, isp = 1.0 / p_scale;
+    for (int e = e0; e < e1; e++) {
+      if (d.colA[e] < 0) continue;
+      const Blk4<double> bk = *(const Blk4<double>*)&raw[4 * (size_t)e];
+      const double o0 = bk.a, o1 = bk.b, o2 = bk.c, o3 = bk.d;
       const double m00 = I00 * o0 + I01 * o2, m01 = I00 * o1 + I01 * o3;
       const double m10 = I10 * o0 + I11 * o2, m11 = I10 * o1 + I11 * o3;
-      Blk4<T> bk = {(T)m00, (T)(m01 * sp), (T)(m10 * isp), (T)m11};
-      *(Blk4<T>*)&blocks[4 * (size_t)e] = bk;
+      Blk4<T> sk = {(T)m00, (T)(m01 * sp), (T)(m10 * isp), (T)m11};
+      *(Blk4<T>*)&blocks[4 * (size_t)e] = sk;
     }
   }
   // CNV maximum over the block, one atomic per block
   __shared__ double sh[kAsmBlk / 32];
   for (int o = 16; o > 0; o >>= 1) cnv_max = fmax(cnv_max, __shfl_xor_sync(0xffffffffu, cnv_max, o));
-  if (lane == 0) sh[threadIdx.x >> 5] = cnv_max;
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = cnv_max;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
@@ -250,7 +218,8 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt
 // Fracture-line blocks: consecutive compact rows that are consecutive cells of one fracture
 // segment form a block-tridiagonal block of the preconditioner (block Jacobi whose blocks
 // are single cells or whole fracture segments).  Pass 1 marks line rows and lists line
-// starts; pass 2 factors each line (block Thomas algorithm):
+// starts; pass 2 factors each line in FP32 (block Thomas algorithm; a preconditioner's
+// rounding changes the Krylov convergence rate, not the accuracy of the solution):
 //   D'_0 = I, D'_t = I - L_t D'_{t-1}^{-1} U_{t-1},  A_t = -D'_t^{-1} L_t,  G_t = D'_t^{-1} U_t
 // so that M^{-1} r is  w_t = D'_t^{-1} r_t + A_t w_{t-1},  z_t = w_t - G_t z_{t+1}.
 // ---------------------------------------------------------------------------------------
@@ -280,81 +249,110 @@ __global__ void k_line_mark(Dev d) {
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void inv2(const double* a, double* r) {
-  const double id = 1.0 / (a[0] * a[3] - a[1] * a[2]);
-  r[0] = a[3] * id;
-  r[1] = -a[1] * id;
-  r[2] = -a[2] * id;
-  r[3] = a[0] * id;
-}
-
-__device__ __forceinline__ void mul2(const double* a, const double* b, double* c) {
-  c[0] = a[0] * b[0] + a[1] * b[2];
-  c[1] = a[0] * b[1] + a[1] * b[3];
-  c[2] = a[2] * b[0] + a[3] * b[2];
-  c[3] = a[2] * b[1] + a[3] * b[3];
-}
+// One warp per line.  The lanes find and load the line's coupling blocks (U_t: row t -> t+1,
+// L_t: row t -> t-1) 32 rows at a time into shared memory, in FP32; lane 0 runs the block
+// Thomas recurrence over the staged rows; the warp stores D'^{-1}, A and G (FP32) per row.
+constexpr int kLineWarps = 4;
 
 template <typename T>
-__device__ __forceinline__ void load4(const T* p, double* v) {
-  Blk4<T> b = *(const Blk4<T>*)p;
-  v[0] = b.a;
-  v[1] = b.b;
-  v[2] = b.c;
-  v[3] = b.d;
-}
-
-template <typename T>
-__device__ __forceinline__ void store4(T* p, const double* v) {
-  Blk4<T> b = {(T)v[0], (T)v[1], (T)v[2], (T)v[3]};
-  *(Blk4<T>*)p = b;
-}
-
-template <typename T>
-__global__ void k_line_factor(Dev d) {
+__global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
+  __shared__ float s_in[kLineWarps][32][8];
+  __shared__ float s_out[kLineWarps][32][12];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int nl = d.ctr->n_lines;
   const int nA = d.ctr->n_active;
   const T* blocks = (const T*)d.blocks;
-  T* ldinv = (T*)d.line_dinv;
-  T* la = (T*)d.line_a;
-  T* lg = (T*)d.line_g;
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
-    int k = d.line_start[l];
-    double dinv[4] = {1.0, 0.0, 0.0, 1.0};
-    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
-    store4<T>(&ldinv[4 * (size_t)k], dinv);
-    store4<T>(&la[4 * (size_t)k], zero);
+  float* ldinv = (float*)d.line_dinv;
+  float* la = (float*)d.line_a;
+  float* lg = (float*)d.line_g;
+  for (int l = gwarp; l < nl; l += nwarps) {
+    const int k0 = d.line_start[l];
+    // line length: the start row plus the continuation rows that follow it
     int len = 1;
-    while (k + 1 < nA && d.line_row_flag[k + 1] == 2) {
-      const int i = d.act[k], i1 = d.act[k + 1];
-      double U[4], L[4], G[4], LG[4], Dp[4], Dn[4], A[4];
-      load4<T>(&blocks[4 * (size_t)find_entry(d.row_ptr, d.nbr, i, i1)], U);
-      load4<T>(&blocks[4 * (size_t)find_entry(d.row_ptr, d.nbr, i1, i)], L);
-      mul2(dinv, U, G);
-      store4<T>(&lg[4 * (size_t)k], G);
-      mul2(L, G, LG);
-      Dp[0] = 1.0 - LG[0];
-      Dp[1] = -LG[1];
-      Dp[2] = -LG[2];
-      Dp[3] = 1.0 - LG[3];
-      inv2<T>(Dp, Dn);
-      mul2(Dn, L, A);
-      A[0] = -A[0];
-      A[1] = -A[1];
-      A[2] = -A[2];
-      A[3] = -A[3];
-      k++;
-      store4<T>(&ldinv[4 * (size_t)k], Dn);
-      store4<T>(&la[4 * (size_t)k], A);
-      dinv[0] = Dn[0];
-      dinv[1] = Dn[1];
-      dinv[2] = Dn[2];
-      dinv[3] = Dn[3];
-      len++;
+    for (int base = k0 + 1;; base += 32) {
+      const int k = base + lane;
+      const bool cont = k < nA && d.line_row_flag[k] == 2;
+      const unsigned m = __ballot_sync(0xffffffffu, cont);
+      if (m == 0xffffffffu) {
+        len += 32;
+        continue;
+      }
+      len += __ffs(~m) - 1;
+      break;
     }
-    store4<T>(&lg[4 * (size_t)k], zero);
-    d.line_len[l] = len;
+    float Gp[4] = {0.f, 0.f, 0.f, 0.f};  // G of the previous row (lane 0)
+    for (int base = 0; base < len; base += 32) {
+      const int t = base + lane;
+      float U[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
+      if (t < len) {
+        const int i = d.act[k0 + t];
+        if (t + 1 < len) {
+          const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)find_entry(d.row_ptr, d.nbr, i, i + 1)];
+          U[0] = (float)b.a, U[1] = (float)b.b, U[2] = (float)b.c, U[3] = (float)b.d;
+        }
+        if (t >= 1) {
+          const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)find_entry(d.row_ptr, d.nbr, i, i - 1)];
+          L[0] = (float)b.a, L[1] = (float)b.b, L[2] = (float)b.c, L[3] = (float)b.d;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        s_in[wib][lane][q] = U[q];
+        s_in[wib][lane][4 + q] = L[q];
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const int cnt = min(32, len - base);
+        for (int j = 0; j < cnt; j++) {
+          const int tt = base + j;
+          float Di[4], A[4];
+          if (tt == 0) {
+            Di[0] = 1.f, Di[1] = 0.f, Di[2] = 0.f, Di[3] = 1.f;
+            A[0] = A[1] = A[2] = A[3] = 0.f;
+          } else {
+            const float* Lt = &s_in[wib][j][4];
+            // D' = I - L G_{t-1}
+            const float p0 = 1.f - (Lt[0] * Gp[0] + Lt[1] * Gp[2]);
+            const float p1 = -(Lt[0] * Gp[1] + Lt[1] * Gp[3]);
+            const float p2 = -(Lt[2] * Gp[0] + Lt[3] * Gp[2]);
+            const float p3 = 1.f - (Lt[2] * Gp[1] + Lt[3] * Gp[3]);
+            const float id = 1.f / (p0 * p3 - p1 * p2);
+            Di[0] = p3 * id, Di[1] = -p1 * id, Di[2] = -p2 * id, Di[3] = p0 * id;
+            A[0] = -(Di[0] * Lt[0] + Di[1] * Lt[2]);
+            A[1] = -(Di[0] * Lt[1] + Di[1] * Lt[3]);
+            A[2] = -(Di[2] * Lt[0] + Di[3] * Lt[2]);
+            A[3] = -(Di[2] * Lt[1] + Di[3] * Lt[3]);
+          }
+          const float* Ut = &s_in[wib][j][0];
+          float G[4];
+          G[0] = Di[0] * Ut[0] + Di[1] * Ut[2];
+          G[1] = Di[0] * Ut[1] + Di[1] * Ut[3];
+          G[2] = Di[2] * Ut[0] + Di[3] * Ut[2];
+          G[3] = Di[2] * Ut[1] + Di[3] * Ut[3];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            s_out[wib][j][q] = Di[q];
+            s_out[wib][j][4 + q] = A[q];
+            s_out[wib][j][8 + q] = G[q];
+            Gp[q] = G[q];
+          }
+        }
+      }
+      __syncwarp();
+      if (t < len) {
+        const size_t k = (size_t)(k0 + t);
+        *(float4*)&ldinv[4 * k] = make_float4(s_out[wib][lane][0], s_out[wib][lane][1], s_out[wib][lane][2],
+                                               s_out[wib][lane][3]);
+        *(float4*)&la[4 * k] = make_float4(s_out[wib][lane][4], s_out[wib][lane][5], s_out[wib][lane][6],
+                                            s_out[wib][lane][7]);
+        *(float4*)&lg[4 * k] = make_float4(s_out[wib][lane][8], s_out[wib][lane][9], s_out[wib][lane][10],
+                                            s_out[wib][lane][11]);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) d.line_len[l] = len;
   }
 }
 
@@ -367,21 +365,24 @@ cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, i
   F.inv_mu[0] = 1.0 / d.fl.mu_o;
   F.inv_mu[1] = 1.0 / d.fl.mu_w;
   const int grid = 4 * c.sms;
+  count_launches(1);
   if (fp32)
-    k_assemble<float, kLPR><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, p_scale, debug);
+    k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, p_scale, debug);
   else
-    k_assemble<double, kLPR><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, p_scale, debug);
+    k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, p_scale, debug);
   return cudaGetLastError();
 }
 
 cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c) {
   cudaError_t e = cudaMemsetAsync(&d.ctr->n_lines, 0, sizeof(int), c.stream);
   if (e != cudaSuccess) return e;
+  count_launches(1);
   k_line_mark<<<4 * c.sms, 256, 0, c.stream>>>(d);
+  count_launches(1);
   if (fp32)
-    k_line_factor<float><<<c.sms, 128, 0, c.stream>>>(d);
+    k_line_factor<float><<<c.sms, 32 * kLineWarps, 0, c.stream>>>(d);
   else
-    k_line_factor<double><<<c.sms, 128, 0, c.stream>>>(d);
+    k_line_factor<double><<<c.sms, 32 * kLineWarps, 0, c.stream>>>(d);
   return cudaGetLastError();
 }
 

@@ -24,7 +24,6 @@ namespace lns {
 namespace {
 
 constexpr int kKryBlk = 512;
-constexpr int kSlots = 8;  // partial-sum slots per block
 
 template <typename T>
 struct V2;
@@ -54,21 +53,24 @@ __device__ __forceinline__ typename V2<T>::t mk(T x, T y) {
   return v;
 }
 
-// Block-reduce up to two doubles into partial slots (slot, slot+1) of this block.
-__device__ __forceinline__ void block_store2(double a, double b, double* sh, double* part, int slot, int nb) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
+// Block-reduce up to two doubles into partial slots (slot, slot+1) of this block.  Only the
+// first `nw` warps hold rows; the others skip the FP64 shuffles (FP64 issues slowly here).
+__device__ __forceinline__ void block_store2(double a, double b, double* sh, double* part, int slot, int nb, int nw) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    sh[2 * w] = a;
-    sh[2 * w + 1] = b;
+  if (w < nw) {
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      sh[2 * w] = a;
+      sh[2 * w + 1] = b;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double sa = 0.0, sb = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+    for (int k = 0; k < nw; k++) {
       sa += sh[2 * k];
       sb += sh[2 * k + 1];
     }
@@ -139,34 +141,39 @@ __device__ __forceinline__ M2<T> ld2(const T* p) {
   return {b.a, b.b, b.c, b.d};
 }
 
-// Apply M^{-1} to one fracture line (rows k0 .. k0+len-1) by one warp.  `src` is produced
-// per row by `make(k)` (the row's value of the vector being preconditioned, which the warp
-// also stores); the result goes to dst.  Forward: w_t = Dinv_t src_t + A_t w_{t-1};
-// backward: z_t = w_t - G_t z_{t+1}; both as affine-map scans.
+// Apply M^{-1} to one fracture line (rows k0 .. k0+len-1) by one warp, in FP32.  The input
+// vector is produced per row by `make(k)` (the warp also stores it); the result goes to dst.
+// Forward: w_t = Dinv_t src_t + A_t w_{t-1}; backward: z_t = w_t - G_t z_{t+1}; both as
+// inclusive scans of 2x2 affine maps, carried across chunks of 32 rows.
+__device__ __forceinline__ float4 ldf4(const float* p) { return *(const float4*)p; }
+
 template <typename T, typename MakeF>
 __device__ __forceinline__ void line_apply(const Dev& d, int k0, int len, typename V2<T>::t* __restrict__ dst,
                                            MakeF make) {
   using V = typename V2<T>::t;
   const int lane = threadIdx.x & 31;
-  const T* ldinv = (const T*)d.line_dinv;
-  const T* la = (const T*)d.line_a;
-  const T* lg = (const T*)d.line_g;
-  V carry = mk<T>(0, 0);
+  const float* ldinv = (const float*)d.line_dinv;
+  const float* la = (const float*)d.line_a;
+  const float* lg = (const float*)d.line_g;
+  float2 carry = make_float2(0.f, 0.f);
   for (int base = 0; base < len; base += 32) {
     const int t = base + lane;
     const bool valid = t < len;
-    M2<T> A = {0, 0, 0, 0};
-    V c = mk<T>(0, 0);
+    M2<float> A = {0.f, 0.f, 0.f, 0.f};
+    float2 c = make_float2(0.f, 0.f);
     if (valid) {
       const int k = k0 + t;
       const V s = make(k);
-      c = mv(ld2(&ldinv[4 * (size_t)k]), s);
-      A = ld2(&la[4 * (size_t)k]);
+      const float4 Di = ldf4(&ldinv[4 * (size_t)k]);
+      const float sx = (float)s.x, sy = (float)s.y;
+      c = make_float2(Di.x * sx + Di.y * sy, Di.z * sx + Di.w * sy);
+      const float4 a4 = ldf4(&la[4 * (size_t)k]);
+      A = {a4.x, a4.y, a4.z, a4.w};
     }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      M2<T> Ap;
-      V cp;
+      M2<float> Ap;
+      float2 cp;
       Ap.a = __shfl_up_sync(0xffffffffu, A.a, o);
       Ap.b = __shfl_up_sync(0xffffffffu, A.b, o);
       Ap.c = __shfl_up_sync(0xffffffffu, A.c, o);
@@ -174,38 +181,36 @@ __device__ __forceinline__ void line_apply(const Dev& d, int k0, int len, typena
       cp.x = __shfl_up_sync(0xffffffffu, c.x, o);
       cp.y = __shfl_up_sync(0xffffffffu, c.y, o);
       if (lane >= o) {
-        const V nc = mv(A, cp);
-        c.x += nc.x;
-        c.y += nc.y;
+        c.x += A.a * cp.x + A.b * cp.y;
+        c.y += A.c * cp.x + A.d * cp.y;
         A = mm(A, Ap);
       }
     }
-    const V ac = mv(A, carry);
-    V w = mk<T>(c.x + ac.x, c.y + ac.y);
-    if (valid) dst[k0 + t] = w;
+    const float2 w = make_float2(c.x + A.a * carry.x + A.b * carry.y, c.y + A.c * carry.x + A.d * carry.y);
+    if (valid) dst[k0 + t] = mk<T>((T)w.x, (T)w.y);
     const int last = min(31, len - 1 - base);
     carry.x = __shfl_sync(0xffffffffu, w.x, last);
     carry.y = __shfl_sync(0xffffffffu, w.y, last);
   }
   __syncwarp();
-  carry = mk<T>(0, 0);
+  carry = make_float2(0.f, 0.f);
   const int nchunk = (len + 31) / 32;
   for (int ch = nchunk - 1; ch >= 0; ch--) {
-    const int base = ch * 32;
-    const int t = base + lane;
+    const int t = ch * 32 + lane;
     const bool valid = t < len;
-    M2<T> B = {0, 0, 0, 0};
-    V c = mk<T>(0, 0);
+    M2<float> B = {0.f, 0.f, 0.f, 0.f};
+    float2 c = make_float2(0.f, 0.f);
     if (valid) {
       const int k = k0 + t;
-      c = ldv(&dst[k]);
-      const M2<T> G = ld2(&lg[4 * (size_t)k]);
-      B = {-G.a, -G.b, -G.c, -G.d};
+      const V wv = ldv(&dst[k]);
+      c = make_float2((float)wv.x, (float)wv.y);
+      const float4 g4 = ldf4(&lg[4 * (size_t)k]);
+      B = {-g4.x, -g4.y, -g4.z, -g4.w};
     }
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      M2<T> Bp;
-      V cp;
+      M2<float> Bp;
+      float2 cp;
       Bp.a = __shfl_down_sync(0xffffffffu, B.a, o);
       Bp.b = __shfl_down_sync(0xffffffffu, B.b, o);
       Bp.c = __shfl_down_sync(0xffffffffu, B.c, o);
@@ -213,15 +218,13 @@ __device__ __forceinline__ void line_apply(const Dev& d, int k0, int len, typena
       cp.x = __shfl_down_sync(0xffffffffu, c.x, o);
       cp.y = __shfl_down_sync(0xffffffffu, c.y, o);
       if (lane + o < 32) {
-        const V nc = mv(B, cp);
-        c.x += nc.x;
-        c.y += nc.y;
+        c.x += B.a * cp.x + B.b * cp.y;
+        c.y += B.c * cp.x + B.d * cp.y;
         B = mm(B, Bp);
       }
     }
-    const V bc = mv(B, carry);
-    const V z = mk<T>(c.x + bc.x, c.y + bc.y);
-    if (valid) dst[k0 + t] = z;
+    const float2 z = make_float2(c.x + B.a * carry.x + B.b * carry.y, c.y + B.c * carry.x + B.d * carry.y);
+    if (valid) dst[k0 + t] = mk<T>((T)z.x, (T)z.y);
     carry.x = __shfl_sync(0xffffffffu, z.x, 0);
     carry.y = __shfl_sync(0xffffffffu, z.y, 0);
   }
@@ -229,7 +232,7 @@ __device__ __forceinline__ void line_apply(const Dev& d, int k0, int len, typena
 }
 
 template <typename T, bool LINES>
-__global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int maxit) {
+__global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int maxit) {
   using V = typename V2<T>::t;
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[72];
@@ -238,7 +241,14 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const int gwarp = tid >> 5, nwarps = nth >> 5;
+  // rows: a contiguous chunk per block, spread over all SMs (FP64 throughput is per SM)
+  const int rpb = (nA + nb - 1) / nb;
+  const int r0 = min(nA, blockIdx.x * rpb), r1 = min(nA, r0 + rpb);
+  const int kbeg = r0 + (int)threadIdx.x, kstep = blockDim.x;
+  const int nw = min((int)(blockDim.x >> 5), (r1 - r0 + 31) / 32);
   const int nlines = LINES ? d.ctr->n_lines : 0;
+  // (s, s) also collects the line rows' contributions from the line warps: every warp may hold some
+  const int nw_ss = LINES ? (int)(blockDim.x >> 5) : nw;
   V* x = (V*)d.kx;
   V* r = (V*)d.kr;
   V* rh = (V*)d.krh;
@@ -254,7 +264,7 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
   double* part = d.partials;
 
   double l_bb = 0.0;
-  for (int k = tid; k < nA; k += nth) {
+  for (int k = kbeg; k < r1; k += kstep) {
     const V bk = b[k];
     x[k] = mk<T>(0, 0);
     r[k] = bk;
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
     v[k] = mk<T>(0, 0);
     l_bb += (double)bk.x * bk.x + (double)bk.y * bk.y;
   }
-  block_store2(l_bb, 0.0, sh, part, 0, nb);
+  block_store2(l_bb, 0.0, sh, part, 0, nb, nw);
   grid.sync();
   double bb, dummy;
   grid_sum2(part, 0, nb, sh, bb, dummy);
@@ -277,7 +287,7 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
       const T beta = (T)(it == 1 ? 0.0 : (rho / rho_old) * (alpha / omega));
       const T om = (T)omega;
       // Phase A: p = r + beta (p - omega v);  ph = M^{-1} p
-      for (int k = tid; k < nA; k += nth) {
+      for (int k = kbeg; k < r1; k += kstep) {
         if (LINES && lflag[k]) continue;
         const V rk = ldv(&r[k]), pk = ldv(&p[k]), vk = ldv(&v[k]);
         const V np = mk<T>(rk.x + beta * (pk.x - om * vk.x), rk.y + beta * (pk.y - om * vk.y));
@@ -296,13 +306,13 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
       grid.sync();
       // Phase B: v = A ph, (rh, v)
       double l_rv = 0.0;
-      for (int k = tid; k < nA; k += nth) {
+      for (int k = kbeg; k < r1; k += kstep) {
         const V vk = spmv_row<T>(d, k, ph, blocks);
         v[k] = vk;
         const V rk = ldv(&rh[k]);
         l_rv += (double)rk.x * vk.x + (double)rk.y * vk.y;
       }
-      block_store2(l_rv, 0.0, sh, part, 2, nb);
+      block_store2(l_rv, 0.0, sh, part, 2, nb, nw);
       grid.sync();
       double rv;
       grid_sum2(part, 2, nb, sh, rv, dummy);
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
       const T al = (T)alpha;
       // Phase C: s = r - alpha v; shv = M^{-1} s; (s, s)
       double l_ss = 0.0;
-      for (int k = tid; k < nA; k += nth) {
+      for (int k = kbeg; k < r1; k += kstep) {
         if (LINES && lflag[k]) continue;
         const V rk = ldv(&r[k]), vk = ldv(&v[k]);
         const V sk = mk<T>(rk.x - al * vk.x, rk.y - al * vk.y);
@@ -334,12 +344,12 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
           });
           l_ss += acc;
         }
-      block_store2(l_ss, 0.0, sh, part, 4, nb);
+      block_store2(l_ss, 0.0, sh, part, 4, nb, nw_ss);
       grid.sync();
       double ss;
       grid_sum2(part, 4, nb, sh, ss, dummy);
       if (ss <= stop2) {
-        for (int k = tid; k < nA; k += nth) {
+        for (int k = kbeg; k < r1; k += kstep) {
           const V xk = ldv(&x[k]), pk = ldv(&ph[k]);
           x[k] = mk<T>(xk.x + al * pk.x, xk.y + al * pk.y);
         }
@@ -349,14 +359,14 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
       }
       // Phase D: t = A shv; (t, s), (t, t)
       double l_ts = 0.0, l_tt = 0.0;
-      for (int k = tid; k < nA; k += nth) {
+      for (int k = kbeg; k < r1; k += kstep) {
         const V tk = spmv_row<T>(d, k, shv, blocks);
         t[k] = tk;
         const V sk = ldv(&s[k]);
         l_ts += (double)tk.x * sk.x + (double)tk.y * sk.y;
         l_tt += (double)tk.x * tk.x + (double)tk.y * tk.y;
       }
-      block_store2(l_ts, l_tt, sh, part, 6, nb);
+      block_store2(l_ts, l_tt, sh, part, 6, nb, nw);
       grid.sync();
       double ts, tt;
       grid_sum2(part, 6, nb, sh, ts, tt);
@@ -368,7 +378,7 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
       const T omg = (T)omega;
       // Phase E: x += alpha ph + omega shv; r = s - omega t; (rh, r), (r, r)
       double l_rr = 0.0, l_rhr = 0.0;
-      for (int k = tid; k < nA; k += nth) {
+      for (int k = kbeg; k < r1; k += kstep) {
         const V xk = ldv(&x[k]), pk = ldv(&ph[k]), sk2 = ldv(&shv[k]), sk = ldv(&s[k]), tk = ldv(&t[k]), rhk = ldv(&rh[k]);
         x[k] = mk<T>(xk.x + al * pk.x + omg * sk2.x, xk.y + al * pk.y + omg * sk2.y);
         const V rk = mk<T>(sk.x - omg * tk.x, sk.y - omg * tk.y);
@@ -376,7 +386,7 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
         l_rr += (double)rk.x * rk.x + (double)rk.y * rk.y;
         l_rhr += (double)rhk.x * rk.x + (double)rhk.y * rk.y;
       }
-      block_store2(l_rhr, l_rr, sh, part, 0, nb);
+      block_store2(l_rhr, l_rr, sh, part, 0, nb, nw);
       grid.sync();
       double rr;
       rho_old = rho;
@@ -393,7 +403,7 @@ __global__ void __launch_bounds__(kKryBlk) k_bicgstab(Dev d, double rtol, int ma
     }
     if (it > maxit) it = maxit;
   } else {
-    for (int k = tid; k < nA; k += nth) x[k] = mk<T>(0, 0);
+    for (int k = kbeg; k < r1; k += kstep) x[k] = mk<T>(0, 0);
   }
   if (tid == 0) {
     d.ctr->krylov_iters = it;
@@ -419,13 +429,13 @@ int krylov_grid(int fp32, int sms) {
   return a < b ? a : b;
 }
 
-cudaError_t launch_bicgstab(const Dev& d, int fp32, double rtol, int maxit, int grid, LaunchCfg c) {
+cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, LaunchCfg c) {
   Dev dd = d;
   void* args[] = {&dd, &rtol, &maxit};
-  // Lines are always handled (n_lines may be zero: the line loop is then empty).
-  if (fp32)
-    return cudaLaunchCooperativeKernel((void*)k_bicgstab<float, true>, grid, kKryBlk, args, 0, c.stream);
-  return cudaLaunchCooperativeKernel((void*)k_bicgstab<double, true>, grid, kKryBlk, args, 0, c.stream);
+  count_launches(1);
+  void* fn = fp32 ? (lines ? (void*)k_bicgstab<float, true> : (void*)k_bicgstab<float, false>)
+                  : (lines ? (void*)k_bicgstab<double, true> : (void*)k_bicgstab<double, false>);
+  return cudaLaunchCooperativeKernel(fn, grid, kKryBlk, args, 0, c.stream);
 }
 
 }  // namespace lns

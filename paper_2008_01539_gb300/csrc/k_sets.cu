@@ -334,13 +334,16 @@ inline int words_grid(int W) { return (W + kBlk - 1) / kBlk; }
 cudaError_t launch_compact(const Dev& d, const uint32_t* bits, int* list, int* inv, int* count_out, LaunchCfg c) {
   int nb = words_grid(d.W);
   if (nb == 0) return cudaMemsetAsync(count_out, 0, sizeof(int), c.stream);
+  count_launches(1);
   k_compact_count<<<nb, kBlk, 0, c.stream>>>(bits, d.W, d.blk_sums);
+  count_launches(1);
   k_compact_write<<<nb, kBlk, 0, c.stream>>>(bits, d.W, d.blk_sums, list, inv, count_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_boundary(const Dev& d, const uint32_t* set, uint32_t* out, LaunchCfg c) {
   if (d.W == 0) return cudaSuccess;
+  count_launches(1);
   k_boundary<<<words_grid(d.W), kBlk, 0, c.stream>>>(d.row_ptr, d.nbr, set, d.W, out);
   return cudaGetLastError();
 }
@@ -349,6 +352,7 @@ cudaError_t launch_outer_halo(const Dev& d, const uint32_t* set, const int* list
                               LaunchCfg c) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t) * (size_t)d.W, c.stream);
   if (e != cudaSuccess) return e;
+  count_launches(1);
   k_outer_halo<<<4 * c.sms, kBlk, 0, c.stream>>>(d.row_ptr, d.nbr, set, list, count, out);
   return cudaGetLastError();
 }
@@ -356,6 +360,7 @@ cudaError_t launch_outer_halo(const Dev& d, const uint32_t* set, const int* list
 cudaError_t launch_flag(const Dev& d, const uint32_t* vb, int apply, int record_stamp, int solve_id, double eps_p,
                         double eps_sw, double p_scale, double sat_chop, int fp32, const void* x, double fail_rtol,
                         LaunchCfg c) {
+  count_launches(1);
   if (fp32)
     k_flag<float><<<4 * c.sms, kBlk, 0, c.stream>>>(d, vb, apply, record_stamp, solve_id, eps_p, eps_sw, p_scale,
                                                     sat_chop, (const float*)x, fail_rtol);
@@ -374,6 +379,7 @@ cudaError_t launch_dilate(const Dev& d, uint32_t* reach, int layers, LaunchCfg c
     int* cout = &d.ctr->n_frontier[(h + 1) & 1];
     cudaError_t e = cudaMemsetAsync(cout, 0, sizeof(int), c.stream);
     if (e != cudaSuccess) return e;
+    count_launches(1);
     k_dilate_round<<<4 * c.sms, kBlk, 0, c.stream>>>(d.row_ptr, d.nbr, fin, cin, fout, cout, reach);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -382,29 +388,34 @@ cudaError_t launch_dilate(const Dev& d, uint32_t* reach, int layers, LaunchCfg c
 }
 
 cudaError_t launch_seed_frontier(const Dev& d, const int* list, int count_host, uint32_t* reach, LaunchCfg c) {
+  count_launches(1);
   k_seed<<<4 * c.sms, kBlk, 0, c.stream>>>(list, count_host, reach, d.fr0, &d.ctr->n_frontier[0]);
   return cudaGetLastError();
 }
 
 cudaError_t launch_alg1_combine(const Dev& d, double tol_dp, double tol_cnv, int converged_override, LaunchCfg c) {
+  count_launches(1);
   k_alg1_combine<<<words_grid(d.W > 0 ? d.W : 1), kBlk, 0, c.stream>>>(d, tol_dp, tol_cnv, converged_override);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dd_combine(const Dev& d, const uint32_t* reach, uint32_t* vt, uint32_t* va_next, LaunchCfg c) {
   if (d.W == 0) return cudaSuccess;
+  count_launches(1);
   k_dd_combine<<<words_grid(d.W), kBlk, 0, c.stream>>>(d, reach, vt, va_next);
   return cudaGetLastError();
 }
 
 cudaError_t launch_words_op(const Dev& d, int op, uint32_t* out, const uint32_t* a, const uint32_t* b, LaunchCfg c) {
   if (d.W == 0) return cudaSuccess;
+  count_launches(1);
   k_words<<<words_grid(d.W), kBlk, 0, c.stream>>>(d.W, d.n, op, out, a, b);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_support(const Dev& d, double eps_p, double eps_sw, LaunchCfg c) {
   if (d.W == 0) return cudaSuccess;
+  count_launches(1);
   k_step_support<<<words_grid(d.W), kBlk, 0, c.stream>>>(d, eps_p, eps_sw);
   return cudaGetLastError();
 }
@@ -413,6 +424,7 @@ cudaError_t launch_halo_check(const Dev& d, const uint32_t* vdb, int since, Laun
   cudaError_t e = cudaMemsetAsync(&d.ctr->halo_flag, 0, sizeof(int), c.stream);
   if (e != cudaSuccess) return e;
   if (d.W == 0) return cudaSuccess;
+  count_launches(1);
   k_halo_check<<<words_grid(d.W), kBlk, 0, c.stream>>>(d, vdb, since);
   return cudaGetLastError();
 }

@@ -13,7 +13,14 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+
 #include "lns_internal.cuh"
+
+namespace lns {
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace lns
 
 using lns::Dev;
 using lns::IterCounters;
@@ -186,6 +193,7 @@ lns_status reset_iter(lns_model* m) {
   CK(cudaMemsetAsync(d.ctr, 0, sizeof(IterCounters), m->stream));
   CK(cudaMemsetAsync(d.supp, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
   CK(cudaMemsetAsync(d.reach, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+  CK(cudaMemsetAsync(d.vb, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));  // V_B is written by the assembly
   return LNS_OK;
 }
 
@@ -216,14 +224,18 @@ lns_status local_solve(lns_model* m, int debug) {
   TRY(ev_begin(m, KC_COMPACT, &pe));
   CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, c));
   TRY(ev_end(m, &pe, d.W * 4.0 * 2 + 0.0, 0.0));
+  if (fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
   TRY(ev_begin(m, KC_ASSEMBLE, &pe));
   CK(lns::launch_assemble(d, m->dt, eff_p_scale(m), fp32, debug, c));
   TRY(ev_end(m, &pe, 0.0, 0.0));
-  TRY(ev_begin(m, KC_LINES, &pe));
-  CK(lns::launch_line_setup(d, fp32, c));
-  TRY(ev_end(m, &pe, 0.0, 0.0));
+  const int lines = m->o.precond == LNS_PRECOND_BJAC;
+  if (lines) {
+    TRY(ev_begin(m, KC_LINES, &pe));
+    CK(lns::launch_line_setup(d, fp32, c));
+    TRY(ev_end(m, &pe, 0.0, 0.0));
+  }
   TRY(ev_begin(m, KC_KRYLOV, &pe));
-  CK(lns::launch_bicgstab(d, fp32, m->o.krylov_rtol, m->o.krylov_maxit, m->kgrid[fp32 ? 1 : 0], c));
+  CK(lns::launch_bicgstab(d, fp32, lines, m->o.krylov_rtol, m->o.krylov_maxit, m->kgrid[fp32 ? 1 : 0], c));
   TRY(ev_end(m, &pe, 0.0, 0.0));
   return LNS_OK;
 }
@@ -333,13 +345,7 @@ lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
   LaunchCfg c = cfg(m);
   const bool local = m->o.mode == LNS_MODE_LOCAL;
   TRY(reset_iter(m));
-  if (local) {
-    PendingEvent pe;
-    TRY(ev_begin(m, KC_SETS, &pe));
-    CK(lns::launch_boundary(d, d.va, d.vb, c));  // V_B of the set being solved
-    TRY(ev_end(m, &pe, 0.0, 0.0));
-  }
-  TRY(local_solve(m, 0));
+  TRY(local_solve(m, 0));  // the assembly also writes V_B of the set being solved
   PendingEvent pe;
   TRY(ev_begin(m, KC_UPDATE, &pe));
   // u^{nu+1} = u^nu + R_A^T du_A, and the flags of Algorithm 1 lines 8-14
@@ -528,7 +534,8 @@ lns_status validate_options(const lns_options* o) {
   if (o->max_newton < 1 || o->max_dd_outer < 1) return fail(LNS_EINVAL, "max_newton and max_dd_outer must be >= 1");
   if (o->krylov_maxit < 1) return fail(LNS_EINVAL, "krylov_maxit must be >= 1");
   if (!(o->krylov_rtol > 0.0) || !(o->eps_p >= 0.0)) return fail(LNS_EINVAL, "krylov_rtol > 0 and eps_p >= 0 required");
-  if (o->precond != LNS_PRECOND_BJAC) return fail(LNS_EINVAL, "unknown preconditioner");
+  if (o->precond != LNS_PRECOND_BJAC && o->precond != LNS_PRECOND_BJAC_CELL)
+    return fail(LNS_EINVAL, "unknown preconditioner");
   return LNS_OK;
 }
 
@@ -537,6 +544,8 @@ lns_status validate_options(const lns_options* o) {
 extern "C" {
 
 const char* lns_last_error(void) { return g_err.c_str(); }
+
+int64_t lns_launch_count(void) { return (int64_t)lns::g_launches.load(std::memory_order_relaxed); }
 
 lns_status lns_options_default(lns_options* o) {
   if (!o) return fail(LNS_EINVAL, "options is NULL");
@@ -793,8 +802,14 @@ lns_status lns_set_state(lns_model* m, const double* p, const double* sw, const 
   if (d.n > 0) {
     CK(cudaMemcpyAsync(d.p, p, nb, cudaMemcpyHostToDevice, m->stream));
     CK(cudaMemcpyAsync(d.sw, sw, nb, cudaMemcpyHostToDevice, m->stream));
-    CK(cudaMemcpyAsync(d.pn, pn ? pn : p, nb, cudaMemcpyHostToDevice, m->stream));
-    CK(cudaMemcpyAsync(d.swn, swn ? swn : sw, nb, cudaMemcpyHostToDevice, m->stream));
+    if (pn)
+      CK(cudaMemcpyAsync(d.pn, pn, nb, cudaMemcpyHostToDevice, m->stream));
+    else
+      CK(cudaMemcpyAsync(d.pn, d.p, nb, cudaMemcpyDeviceToDevice, m->stream));
+    if (swn)
+      CK(cudaMemcpyAsync(d.swn, swn, nb, cudaMemcpyHostToDevice, m->stream));
+    else
+      CK(cudaMemcpyAsync(d.swn, d.sw, nb, cudaMemcpyDeviceToDevice, m->stream));
     CK(cudaMemsetAsync(d.prev, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
   }
   m->has_prev = 0;
@@ -1005,6 +1020,7 @@ lns_status lns_assemble(lns_model* m, double dt, const uint32_t* va_bits, double
   TRY(bits_to_device(m, d.va, va_bits));
   TRY(reset_iter(m));
   CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, c));
+  if (m->o.krylov_fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
   CK(lns::launch_assemble(d, dt, eff_p_scale(m), m->o.krylov_fp32, 1, c));
   if (F) CK(cudaMemcpyAsync(F, d.resid, sizeof(double) * 2 * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));
   if (Jd) CK(cudaMemcpyAsync(Jd, d.dbg_diag, sizeof(double) * 4 * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));

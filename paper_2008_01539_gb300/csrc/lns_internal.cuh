@@ -63,6 +63,7 @@ struct Dev {
   int *act, *inv, *fr0, *fr1, *blk_sums;
   // system
   void* blocks;  // E2 * 4 * sizeof(T)
+  double* raw;   // E2 * 4: unscaled FP64 blocks (FP32 path only; the FP64 path scales in place)
   int* colA;
   void* rhs;     // 2n * sizeof(T)
   double* resid; // 2n (diagnostics), f64
@@ -77,6 +78,9 @@ struct Dev {
   IterCounters* ctr;   // device
   IterCounters* ctr_h; // pinned host mirror
 };
+
+// Process-wide count of kernels launched by the library (lns_launch_count).
+void count_launches(int k);
 
 // ---- launchers (defined in the .cu files) ----
 struct LaunchCfg {
@@ -112,7 +116,7 @@ cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, i
 cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c);
 
 // k_krylov.cu
-cudaError_t launch_bicgstab(const Dev& d, int fp32, double rtol, int maxit, int grid, LaunchCfg c);
+cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, LaunchCfg c);
 int krylov_grid(int fp32, int sms);
 
 }  // namespace lns

@@ -20,7 +20,7 @@ PSI = 6894.757293168
 
 LNS_OK, LNS_EINVAL, LNS_ENOMEM, LNS_ECUDA, LNS_ENOCONV, LNS_EKRYLOV, LNS_ETIMEOUT, LNS_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 LNS_MODE_FULL, LNS_MODE_LOCAL, LNS_MODE_DD = 0, 1, 2
-LNS_PRECOND_BJAC = 0
+LNS_PRECOND_BJAC, LNS_PRECOND_BJAC_CELL = 0, 1
 _STATUS = {0: "LNS_OK", -1: "LNS_EINVAL", -2: "LNS_ENOMEM", -3: "LNS_ECUDA", -4: "LNS_ENOCONV",
            -5: "LNS_EKRYLOV", -6: "LNS_ETIMEOUT", -7: "LNS_ESTATE"}
 
@@ -86,7 +86,7 @@ _lib = None
 EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_set_options", "lns_timestep",
            "lns_newton_iter", "lns_active_set", "lns_dd_expand", "lns_solve_local", "lns_assemble",
            "lns_get_state", "lns_set_state", "lns_get_state_device", "lns_reset", "lns_get_support",
-           "lns_kernel_times", "lns_reset_kernel_times", "lns_last_error"]
+           "lns_kernel_times", "lns_reset_kernel_times", "lns_launch_count", "lns_last_error"]
 
 
 def library_path() -> str:
@@ -131,8 +131,15 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         fn.restype = C.c_int
     L.lns_last_error.argtypes = []
     L.lns_last_error.restype = C.c_char_p
+    L.lns_launch_count.argtypes = []
+    L.lns_launch_count.restype = C.c_int64
     _lib = L
     return L
+
+
+def lns_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().lns_launch_count())
 
 
 def _check(rc: int, allow=()) -> int:
