@@ -221,6 +221,34 @@ lns_status lns_get_support(const lns_model* model, uint32_t* bits);
 lns_status lns_kernel_times(const lns_model* model, lns_kernel_time* out, int32_t cap, int32_t* count);
 lns_status lns_reset_kernel_times(lns_model* model);
 
+/* Allocation-free variant of lns_active_set.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- their memory is owned by a host
+ * framework's pool or a fixed budget, or they run where cudaMalloc (which may synchronize the
+ * whole device) would stall other work -- and therefore cannot create a model.
+ *
+ * Computes exactly what lns_active_set computes (Algorithm 1, lines 8-20), on the caller's arrays:
+ *   row_ptr [n_cells+1], nbr [row_ptr[n_cells]]: the connection graph as in lns_model_desc;
+ *   always_bits: bitset of always-active cells, or NULL for none;
+ *   dp, dsw [n_cells]: the update (dsw may be NULL: zero); entries outside V_A are ignored;
+ *   va_bits (in/out): V_A, replaced by the new V_A;  vb_bits (out): the new V_B.
+ * All of these are DEVICE pointers owned by the caller; is_expand is a host pointer.  Work runs
+ * on cuda_stream (NULL: legacy default stream) and the call returns after it has finished.
+ *
+ * The call allocates nothing: its working storage (frontier lists, bitsets, counters; about
+ * 8.4 MB for the limit below) is one file-scope __device__ array that every GPU loading the
+ * library keeps until the process exits.  Limits: n_cells <= LNS_NOALLOC_MAX_CELLS and
+ * m_layers <= LNS_NOALLOC_MAX_LAYERS; larger values return LNS_EINVAL.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the array and each clears
+ * what it needs, so calls that overlap on the GPU (two streams or two threads on one device)
+ * race: serialize them. */
+#define LNS_NOALLOC_MAX_CELLS (1 << 20)
+#define LNS_NOALLOC_MAX_LAYERS 1024
+lns_status lns_active_set_noalloc(int32_t n_cells, const int32_t* row_ptr, const int32_t* nbr,
+                                  const uint32_t* always_bits, const double* dp, const double* dsw, double eps_p,
+                                  double eps_sw, int32_t m_layers, int32_t converged, uint32_t* va_bits,
+                                  uint32_t* vb_bits, int32_t* is_expand, void* cuda_stream);
+
 /* Number of CUDA kernels the library has launched in this process (all models). */
 int64_t lns_launch_count(void);
 

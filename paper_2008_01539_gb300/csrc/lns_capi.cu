@@ -17,9 +17,14 @@
 
 #include "lns_internal.cuh"
 
+namespace {
+thread_local std::string g_err;
+}  // namespace
+
 namespace lns {
 static std::atomic<long long> g_launches{0};
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 }  // namespace lns
 
 using lns::Dev;
@@ -27,7 +32,6 @@ using lns::IterCounters;
 using lns::LaunchCfg;
 
 namespace {
-thread_local std::string g_err;
 
 lns_status fail(lns_status s, const std::string& msg) {
   g_err = msg;

@@ -81,6 +81,8 @@ struct Dev {
 
 // Process-wide count of kernels launched by the library (lns_launch_count).
 void count_launches(int k);
+// Message returned by lns_last_error() on the calling thread.
+void set_last_error(const char* msg);
 
 // ---- launchers (defined in the .cu files) ----
 struct LaunchCfg {

@@ -86,7 +86,8 @@ _lib = None
 EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_set_options", "lns_timestep",
            "lns_newton_iter", "lns_active_set", "lns_dd_expand", "lns_solve_local", "lns_assemble",
            "lns_get_state", "lns_set_state", "lns_get_state_device", "lns_reset", "lns_get_support",
-           "lns_kernel_times", "lns_reset_kernel_times", "lns_launch_count", "lns_last_error"]
+           "lns_kernel_times", "lns_reset_kernel_times", "lns_launch_count", "lns_last_error",
+           "lns_active_set_noalloc"]
 
 
 def library_path() -> str:
@@ -133,6 +134,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     L.lns_last_error.restype = C.c_char_p
     L.lns_launch_count.argtypes = []
     L.lns_launch_count.restype = C.c_int64
+    L.lns_active_set_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, f64, f64, i32, i32, vp, vp, P(i32), vp]
+    L.lns_active_set_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -140,6 +143,19 @@ def load(build_if_missing: bool = False) -> C.CDLL:
 def lns_launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().lns_launch_count())
+
+
+def lns_active_set_noalloc(n_cells: int, row_ptr: int, nbr: int, always_bits: int, dp: int, dsw: int,
+                           eps_p: float, eps_sw: float, m_layers: int, converged: bool, va_bits: int, vb_bits: int,
+                           stream: int = 0) -> int:
+    """Allocation-free active-set update on caller-owned DEVICE arrays (integer device
+    addresses, 0 for an optional NULL), for callers that cannot allocate device memory.
+    Returns is_expand; va_bits is updated in place and vb_bits written."""
+    ie = C.c_int32(0)
+    _check(load().lns_active_set_noalloc(int(n_cells), row_ptr or None, nbr or None, always_bits or None, dp or None,
+                                         dsw or None, float(eps_p), float(eps_sw), int(m_layers), int(bool(converged)),
+                                         va_bits or None, vb_bits or None, C.byref(ie), stream or None))
+    return int(ie.value)
 
 
 def _check(rc: int, allow=()) -> int:
