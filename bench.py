@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="run only the headline case (for profiler launch lists)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--krylov-rtol", type=float, default=None,
+                    help="BiCGStab relative tolerance (default: the library's)")
     return ap.parse_args()
 
 
@@ -277,8 +279,8 @@ def main():
     lns.load(build_if_missing=True)
     case = make_case(args.case)
     mode_id = {"local": lns.LNS_MODE_LOCAL, "full": lns.LNS_MODE_FULL, "dd": lns.LNS_MODE_DD}[args.mode]
-    opts = lns.Options(mode=mode_id, krylov_fp32=int(args.fp32_krylov),
-                       krylov_rtol=1e-5 if args.fp32_krylov else 1e-8,
+    rtol = args.krylov_rtol if args.krylov_rtol is not None else (1e-5 if args.fp32_krylov else lns.Options().krylov_rtol)
+    opts = lns.Options(mode=mode_id, krylov_fp32=int(args.fp32_krylov), krylov_rtol=rtol,
                        precond=lns.LNS_PRECOND_BJAC if args.precond == "lines" else lns.LNS_PRECOND_BJAC_CELL)
     stream = torch.cuda.current_stream()
     model = lns.Model(case, opts)

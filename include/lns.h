@@ -151,7 +151,8 @@ typedef struct {
   double flops;          /* algorithmic FP64/FP32 flops, summed over launches */
 } lns_kernel_time;
 
-/* Default options: Algorithm 1, eps_p = tol_dp = 0.3 psi, m = 2, tol_cnv = 1e-6, FP64. */
+/* Default options: Algorithm 1, eps_p = tol_dp = 0.3 psi, m = 2, tol_cnv = 1e-6, FP64, BiCGStab to
+ * krylov_rtol = 1e-6 (an inexact Newton step; the Newton loop reaches the same FP64 tolerance). */
 lns_status lns_options_default(lns_options* out);
 
 /* Copy the model to the device, set u = (p0, sw0).  cuda_stream: a cudaStream_t to run

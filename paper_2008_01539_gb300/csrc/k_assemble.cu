@@ -85,9 +85,9 @@ struct alignas(4 * sizeof(T)) Blk4 {
 // FP64, writes the raw off-diagonal blocks and marks the row as a boundary cell (V_B: an
 // inactive neighbour); pass 2 scales the row by S D^{-1} in place.
 template <typename T>
-__global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt, double p_scale, int debug) {
+__global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt, double inv_dt, double p_scale,
+                                                     double inv_p_scale, int debug) {
   const int nA = d.ctr->n_active;
-  const double inv_dt = 1.0 / dt;
   const double g = F.f.gravity;
   T* blocks = (T*)d.blocks;
   double* raw = sizeof(T) == sizeof(double) ? (double*)d.blocks : d.raw;
@@ -181,7 +181,10 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt
     const double I00 = D11 * id, I01 = -D01 * id, I10 = -D10 * id, I11 = D00 * id;
     rhs[2 * (size_t)k] = (T)(-p_scale * (I00 * R0 + I01 * R1));
     rhs[2 * (size_t)k + 1] = (T)(-(I10 * R0 + I11 * R1));
-    cnv_max = fmax(cnv_max, fmax(fabs(R0) * dt / (qi.pv * qi.b[0]), fabs(R1) * dt / (qi.pv * qi.b[1])));
+    {  // CNV with one FP64 division: 1/(PV b_l) = b_other / (PV b_o b_w)
+      const double ipbb = dt / (qi.pv * qi.b[0] * qi.b[1]);
+      cnv_max = fmax(cnv_max, fmax(fabs(R0) * qi.b[1] * ipbb, fabs(R1) * qi.b[0] * ipbb));
+    }
     if (debug) {
       d.resid[2 * (size_t)i] = R0;
       d.resid[2 * (size_t)i + 1] = R1;
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt
       d.dbg_diag[4 * (size_t)i + 3] = D11;
     }
     // pass 2: S D^{-1} O S^{-1} on the blocks of active columns
-    const double sp = p_scale, isp = 1.0 / p_scale;
+    const double sp = p_scale, isp = inv_p_scale;
     for (int e = e0; e < e1; e++) {
       if (d.colA[e] < 0) continue;
       const Blk4<double> bk = *(const Blk4<double>*)&raw[4 * (size_t)e];
@@ -367,9 +370,9 @@ cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, i
   const int grid = 4 * c.sms;
   count_launches(1);
   if (fp32)
-    k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, p_scale, debug);
+    k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, 1.0 / dt, p_scale, 1.0 / p_scale, debug);
   else
-    k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, p_scale, debug);
+    k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, 1.0 / dt, p_scale, 1.0 / p_scale, debug);
   return cudaGetLastError();
 }
 

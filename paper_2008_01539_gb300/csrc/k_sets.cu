@@ -156,6 +156,7 @@ __global__ void k_flag(Dev d, const uint32_t* __restrict__ vb, int apply, int re
                        double eps_p, double eps_sw, double p_scale, double sat_chop, const T* __restrict__ x,
                        double fail_rtol) {
   __shared__ double sh[32];
+  const double inv_p_scale = 1.0 / p_scale;  // once per thread, outside the row loop
   int nA = d.ctr->n_active;
   // a failed Krylov solve (breakdown, or stopped far from the tolerance) is not scattered
   if (x && apply && (d.ctr->krylov_status == 2 || (d.ctr->krylov_status == 1 && !(d.ctr->krylov_relres <= fail_rtol))))
@@ -166,7 +167,7 @@ __global__ void k_flag(Dev d, const uint32_t* __restrict__ vb, int apply, int re
     int i = d.act[k];
     double dp, dsw;
     if (x) {
-      dp = (double)x[2 * k] / p_scale;
+      dp = (double)x[2 * k] * inv_p_scale;
       dsw = (double)x[2 * k + 1];
       if (sat_chop > 0.0) dsw = fmin(fmax(dsw, -sat_chop), sat_chop);
       d.dp[i] = dp;

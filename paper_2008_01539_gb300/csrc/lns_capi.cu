@@ -566,7 +566,7 @@ lns_status lns_options_default(lns_options* o) {
   o->sat_chop = 0.2;
   o->krylov_fp32 = 0;
   o->precond = LNS_PRECOND_BJAC;
-  o->krylov_rtol = 1e-8;
+  o->krylov_rtol = 1e-6;
   o->krylov_maxit = 2000;
   o->krylov_fail_rtol = 1e-3;
   o->p_scale = 0.0;

@@ -179,7 +179,7 @@ class Options:
     sat_chop: float = 0.2
     krylov_fp32: int = 0
     precond: int = LNS_PRECOND_BJAC
-    krylov_rtol: float = 1e-8
+    krylov_rtol: float = 1e-6
     krylov_maxit: int = 2000
     krylov_fail_rtol: float = 1e-3
     p_scale: float = 0.0
