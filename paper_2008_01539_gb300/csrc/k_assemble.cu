@@ -246,8 +246,9 @@ __global__ void k_line_mark(Dev d) {
     }
     d.line_row_flag[k] = cont ? 2 : (next ? 1 : 0);
     if (next && !cont) {
-      int pos = atomicAdd(&d.ctr->n_lines, 1);
+      int pos = atomicAdd(&d.ctr->n_line_starts, 1);
       d.line_start[pos] = k;
+      atomicAdd(&d.ctr->n_lines, 1);
     }
   }
 }
@@ -256,6 +257,7 @@ __global__ void k_line_mark(Dev d) {
 // L_t: row t -> t-1) 32 rows at a time into shared memory, in FP32; lane 0 runs the block
 // Thomas recurrence over the staged rows; the warp stores D'^{-1}, A and G (FP32) per row.
 constexpr int kLineWarps = 4;
+constexpr int kMaxLineRows = 128;  // one warp holds a line block in registers (4 chunks of 32)
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int nl = d.ctr->n_lines;
+  const int nl = d.ctr->n_line_starts;  // the factor pass appends cut blocks after these
   const int nA = d.ctr->n_active;
   const T* blocks = (const T*)d.blocks;
   float* ldinv = (float*)d.line_dinv;
@@ -291,11 +293,11 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
       float U[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
       if (t < len) {
         const int i = d.act[k0 + t];
-        if (t + 1 < len) {
+        if (t + 1 < len && (t + 1) % kMaxLineRows != 0) {
           const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)find_entry(d.row_ptr, d.nbr, i, i + 1)];
           U[0] = (float)b.a, U[1] = (float)b.b, U[2] = (float)b.c, U[3] = (float)b.d;
         }
-        if (t >= 1) {
+        if (t >= 1 && t % kMaxLineRows != 0) {
           const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)find_entry(d.row_ptr, d.nbr, i, i - 1)];
           L[0] = (float)b.a, L[1] = (float)b.b, L[2] = (float)b.c, L[3] = (float)b.d;
         }
@@ -355,7 +357,16 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
       }
       __syncwarp();
     }
-    if (lane == 0) d.line_len[l] = len;
+    // lines longer than kMaxLineRows are cut into blocks of kMaxLineRows rows (the couplings at the
+    // cuts were left out of the factors above); the extra blocks are appended to the line list
+    if (lane == 0) {
+      d.line_len[l] = min(len, kMaxLineRows);
+      for (int q = kMaxLineRows; q < len; q += kMaxLineRows) {
+        const int pos = atomicAdd(&d.ctr->n_lines, 1);
+        d.line_start[pos] = k0 + q;
+        d.line_len[pos] = min(kMaxLineRows, len - q);
+      }
+    }
   }
 }
 
@@ -377,7 +388,7 @@ cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, i
 }
 
 cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c) {
-  cudaError_t e = cudaMemsetAsync(&d.ctr->n_lines, 0, sizeof(int), c.stream);
+  cudaError_t e = cudaMemsetAsync(&d.ctr->n_lines, 0, 2 * sizeof(int), c.stream);  // n_lines, n_line_starts
   if (e != cudaSuccess) return e;
   count_launches(1);
   k_line_mark<<<4 * c.sms, 256, 0, c.stream>>>(d);

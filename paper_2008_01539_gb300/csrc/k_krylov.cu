@@ -1,22 +1,35 @@
 // k_krylov.cu -- BiCGStab on the compacted local system J_A du_A = -F_A (Section 4.3),
 // right-preconditioned by block Jacobi whose blocks are single cells (already the identity
-// after the assembly's row scaling) and whole fracture segments (block tridiagonal).
+// after the assembly's row scaling) and fracture segments (block tridiagonal, cut into blocks of
+// at most 128 rows when factored).
 //
-// One persistent cooperative launch runs the whole Krylov loop; grid-wide barriers separate
-// the five phases of an iteration.  Dot products are reduced per block into fixed slots and
-// every block sums the slots in the same order, so all blocks hold identical scalars, take
-// the same branches, and the result does not depend on scheduling.
+// One persistent cooperative launch runs the whole Krylov loop with TWO grid-wide barriers per
+// iteration.  The local systems are small (thousands of rows), so an iteration is bound by
+// latency: barriers, L2 round trips and dependent FP64 chains, not bandwidth.
 //
-// The local systems of the localized method are small (thousands of rows), so an iteration
-// is bound by latency, not bandwidth.  Each phase is kept to one level of L2 round trips:
-//  - rows are contiguous chunks spread over all SMs; the columns and blocks of a block's rows,
-//    and the factors of its fracture lines (line l lives in block l mod gridDim), are staged
-//    in shared memory once per solve (read-only data does not survive in L1 across grid
-//    barriers); the partial sums of a reduction are loaded all at once;
-//  - the product's gathers of the preconditioned vector are issued several at a time;
-//  - a fracture line (one warp) loads all of its rows at once, runs the forward and backward
-//    block-Thomas recurrences as FP32 scans of 2x2 affine maps in registers, and stores once.
-// Vectors written by other blocks between barriers are read through L2 (__ldcg).
+// Preconditioned vectors are carried through the recurrence by linearity of M^{-1}
+// (y = M^{-1} p, z = M^{-1} s, v~ = M^{-1} v, t~ = M^{-1} t, z^ = M^{-1} s applied directly):
+//   r~_{i-1} = z^_{i-1} - omega_{i-1} t~_{i-1}                 (= M^{-1} r_{i-1})
+//   y_i      = r~_{i-1} + beta_i (y_{i-1} - omega_{i-1} v~_{i-1})
+//   z_i      = r~_{i-1} - alpha_i v~_i
+// so the preconditioner is applied only right after a product, by the owner of the rows (a
+// fracture line's warp), and the products' neighbour values are formed on the fly from vectors
+// written before the last barrier:
+//   phase 1: x_{i-1}, r_{i-1}, r~_{i-1}, y_i, v = A y_i, v~ = M^{-1} v;  reduce (r^,v), (r,r)
+//   phase 2: s = r - alpha v, z_i, t = A z_i, [z^, t~] = M^{-1} [s, t];
+//            reduce (t,s), (t,t), (r^,s), (r^,t)   ->  omega, rho_{i+1} = (r^,s) - omega (r^,t), beta
+// The owner and every neighbour evaluate y and z with the same fused operations on the same
+// stored values, so each row of v (and t) is the product of one consistent vector with A, and the
+// recurrence residual stays the true residual of x up to FP64 rounding.  r~ is rebuilt each
+// iteration from the directly preconditioned s, so the FP32 rounding of M^{-1} does not accumulate.
+//
+// Ownership: non-line rows go to threads in contiguous chunks spread over all SMs; the rows of a
+// fracture line block go to one warp (line l lives in block l mod gridDim), lane t holding rows
+// t, t+32, t+64, t+96.  Matrix rows (columns and blocks) and line factors are staged in shared
+// memory once per solve.  Reductions: per-row products in FP64; across lanes, warps and blocks in
+// double-float (two FP32 words, Knuth's TwoSum), after scaling by an exact power of two near
+// 1/||b||^2.  Every block sums the block partials in the same order, so all blocks hold identical
+// scalars (computed once per block by thread 0: FP64 division is a long sequence here).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -29,8 +42,13 @@ namespace lns {
 namespace {
 
 constexpr int kKryBlk = 512;
-constexpr int kRowsCached = 2;   // rows per thread whose CSR bounds stay in registers
-constexpr int kLineChunks = 4;   // 32-row chunks a line warp holds in registers (longer lines: chunked path)
+constexpr int kWarps = kKryBlk / 32;
+constexpr int kRowsCached = 2;   // non-line rows per thread whose matrix row is staged
+constexpr int kLineChunks = 4;   // 32-row chunks of a line block
+constexpr int kLineSlots = 4;    // line blocks per block whose factors are staged in shared memory
+constexpr size_t kLineSmem = (size_t)kLineSlots * kLineChunks * 32 * 3 * sizeof(float4);
+constexpr size_t kKrySmem = 200 * 1024;
+constexpr int kSlotS1 = 0, kSlotS2 = 2, kSlotInit = 6;  // partial-sum slots (nb entries each)
 
 template <typename T>
 struct V2;
@@ -51,14 +69,25 @@ struct alignas(4 * sizeof(T)) B4 {
 __device__ __forceinline__ float2 ldv(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldv(const double2* p) { return __ldcg(p); }
 
-__device__ __forceinline__ float4 ldf4(const float* p) { return __ldg((const float4*)p); }
-
 template <typename T>
 __device__ __forceinline__ typename V2<T>::t mk(T x, T y) {
   typename V2<T>::t v;
   v.x = x;
   v.y = y;
   return v;
+}
+
+// a * b + c, one rounding (explicit, so that every evaluation of a shared formula is identical)
+__device__ __forceinline__ double fm(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fm(float a, float b, float c) { return fmaf(a, b, c); }
+
+// u + a w, componentwise, fused
+template <typename V, typename T>
+__device__ __forceinline__ V axpy(T a, V w, V u) {
+  V o;
+  o.x = fm(a, w.x, u.x);
+  o.y = fm(a, w.y, u.y);
+  return o;
 }
 
 template <typename T>
@@ -70,70 +99,7 @@ __device__ __forceinline__ M2<T> mm(const M2<T>& x, const M2<T>& y) {
   return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
 }
 
-// Block-reduce up to two doubles into partial slots (slot, slot+1) of this block.  Only the
-// first `nw` warps hold values; the others skip the FP64 shuffles (FP64 issues slowly here).
-__device__ __forceinline__ void block_store2(double a, double b, double* sh, double* part, int slot, int nb, int nw) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (w < nw) {
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) {
-      sh[2 * w] = a;
-      sh[2 * w + 1] = b;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double sa = 0.0, sb = 0.0;
-    for (int k = 0; k < nw; k++) {
-      sa += sh[2 * k];
-      sb += sh[2 * k + 1];
-    }
-    part[(size_t)slot * nb + blockIdx.x] = sa;
-    part[(size_t)(slot + 1) * nb + blockIdx.x] = sb;
-  }
-  __syncthreads();
-}
-
-// Sum partial slots (slot, slot+1) over all blocks in a fixed order (warp 0; the sums are
-// valid in thread 0).  Every block computes the same two numbers.  All of a lane's partial
-// loads are issued before any is used.
-__device__ __forceinline__ void grid_sum2(const double* part, int slot, int nb, double& ra, double& rb) {
-  ra = rb = 0.0;
-  if (threadIdx.x < 32) {
-    constexpr int kU = 8;
-    double a = 0.0, b = 0.0;
-    for (int base = 0; base < nb; base += 32 * kU) {
-      double va[kU], vb[kU];
-#pragma unroll
-      for (int u = 0; u < kU; u++) {
-        const int k = base + u * 32 + (int)threadIdx.x;
-        va[u] = k < nb ? __ldcg(&part[(size_t)slot * nb + k]) : 0.0;
-        vb[u] = k < nb ? __ldcg(&part[(size_t)(slot + 1) * nb + k]) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < kU; u++) {
-        a += va[u];
-        b += vb[u];
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    ra = a;
-    rb = b;
-  }
-}
-
-// Reductions inside the iteration are carried in double-float: an unevaluated sum hi + lo of
-// two FP32 words, added with Knuth's TwoSum and renormalized (about 48 significant bits).
-// Dependent FP64 operations have a long latency on this GPU; the FP32 pipe does the same tree
-// several times faster.  Values are first multiplied by an exact power of two near 1/||b||^2 so
-// that no partial sum leaves the FP32 range.  Per-row products, vectors and the recurrence
-// scalars stay FP64; the summation order is fixed (deterministic).
+// ---- reductions --------------------------------------------------------------------------
 struct DF {
   float hi, lo;
 };
@@ -157,619 +123,602 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
-// Block partials of two scaled values into slots (slot, slot+1), as (hi, lo) pairs.
-__device__ __forceinline__ void block_store_df(double a, double b, double scale, float4* sh4, double* part, int slot,
-                                               int nb, int nw) {
+// Block partials of NV scaled values into slots [slot, slot+NV) as (hi, lo) pairs.  Warps
+// w >= nw hold nothing and skip the conversions.  Contains one block barrier.
+template <int NV>
+__device__ __forceinline__ void block_store(const double (&vals)[NV], double scale, DF* sdf, double* part, int slot,
+                                            int nb, int nw) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (w < nw) {
-    DF da = df_from(a * scale), db = df_from(b * scale);
+    DF a[NV];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      da = df_add(da, df_shfl_xor(da, o));
-      db = df_add(db, df_shfl_xor(db, o));
-    }
-    if (lane == 0) sh4[w] = make_float4(da.hi, da.lo, db.hi, db.lo);
+    for (int q = 0; q < NV; q++) a[q] = df_from(vals[q] * scale);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < NV; q++) a[q] = df_add(a[q], df_shfl_xor(a[q], o));
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NV; q++) sdf[q * kWarps + w] = a[q];
   }
   __syncthreads();
   if (w == 0) {
-    const float4 v = lane < nw ? sh4[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    DF da = {v.x, v.y}, db = {v.z, v.w};
+    DF a[NV];
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {  // nw <= 16 warps per block
-      da = df_add(da, df_shfl_xor(da, o));
-      db = df_add(db, df_shfl_xor(db, o));
-    }
-    if (lane == 0) {
-      ((float2*)part)[(size_t)slot * nb + blockIdx.x] = make_float2(da.hi, da.lo);
-      ((float2*)part)[(size_t)(slot + 1) * nb + blockIdx.x] = make_float2(db.hi, db.lo);
-    }
+    for (int q = 0; q < NV; q++) a[q] = lane < nw ? sdf[q * kWarps + lane] : DF{0.f, 0.f};
+#pragma unroll
+    for (int o = kWarps / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < NV; q++) a[q] = df_add(a[q], df_shfl_xor(a[q], o));
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NV; q++)
+        ((float2*)part)[(size_t)(slot + q) * nb + blockIdx.x] = make_float2(a[q].hi, a[q].lo);
   }
 }
 
-// Sum of the block partials of slots (slot, slot+1), unscaled, valid in warp 0.
-__device__ __forceinline__ void grid_sum_df(const double* part, int slot, int nb, double inv_scale, double& ra,
-                                            double& rb) {
-  ra = rb = 0.0;
+// Sum over all blocks of slots [slot, slot+NV), unscaled, in a fixed order; valid in warp 0.
+// All of a lane's partial loads of one pass are issued before any is used.
+template <int NV>
+__device__ __forceinline__ void grid_sum(const double* part, int slot, int nb, double inv_scale, double (&out)[NV]) {
+#pragma unroll
+  for (int q = 0; q < NV; q++) out[q] = 0.0;
+  if (threadIdx.x >= 32) return;
+  constexpr int kU = 5;
+  DF a[NV];
+#pragma unroll
+  for (int q = 0; q < NV; q++) a[q] = {0.f, 0.f};
+  for (int base = 0; base < nb; base += 32 * kU) {
+    DF v[NV][kU];
+#pragma unroll
+    for (int u = 0; u < kU; u++) {
+      const int k = base + u * 32 + (int)threadIdx.x;
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        const float2 x = k < nb ? __ldcg(&((const float2*)part)[(size_t)(slot + q) * nb + k]) : make_float2(0.f, 0.f);
+        v[q][u] = {x.x, x.y};
+      }
+    }
+#pragma unroll
+    for (int h = 1; h < kU; h <<= 1)
+#pragma unroll
+      for (int u = 0; u + h < kU; u += 2 * h)
+#pragma unroll
+        for (int q = 0; q < NV; q++) v[q][u] = df_add(v[q][u], v[q][u + h]);
+#pragma unroll
+    for (int q = 0; q < NV; q++) a[q] = df_add(a[q], v[q][0]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < NV; q++) a[q] = df_add(a[q], df_shfl_xor(a[q], o));
+#pragma unroll
+  for (int q = 0; q < NV; q++) out[q] = ((double)a[q].hi + (double)a[q].lo) * inv_scale;
+}
+
+// ||b||^2 (once per solve, before the scale is known): FP64 block partial and grid sum.
+__device__ __forceinline__ void block_store_f64(double a, double* sh, double* part, int nb) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) sh[w] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kWarps; k++) s += sh[k];
+    part[(size_t)kSlotInit * nb + blockIdx.x] = s;
+  }
+}
+
+__device__ __forceinline__ double grid_sum_f64(const double* part, int nb) {
+  double a = 0.0;
   if (threadIdx.x < 32) {
-    constexpr int kU = 8;
-    DF a = {0.f, 0.f}, b = {0.f, 0.f};
-    for (int base = 0; base < nb; base += 32 * kU) {
-      DF va[kU], vb[kU];
-#pragma unroll
-      for (int u = 0; u < kU; u++) {
-        const int k = base + u * 32 + (int)threadIdx.x;
-        const float2 x = k < nb ? __ldcg(&((const float2*)part)[(size_t)slot * nb + k]) : make_float2(0.f, 0.f);
-        const float2 y = k < nb ? __ldcg(&((const float2*)part)[(size_t)(slot + 1) * nb + k]) : make_float2(0.f, 0.f);
-        va[u] = {x.x, x.y};
-        vb[u] = {y.x, y.y};
-      }
-#pragma unroll
-      for (int h = 1; h < kU; h <<= 1)
-#pragma unroll
-        for (int u = 0; u + h < kU; u += 2 * h) {
-          va[u] = df_add(va[u], va[u + h]);
-          vb[u] = df_add(vb[u], vb[u + h]);
-        }
-      a = df_add(a, va[0]);
-      b = df_add(b, vb[0]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a = df_add(a, df_shfl_xor(a, o));
-      b = df_add(b, df_shfl_xor(b, o));
-    }
-    ra = ((double)a.hi + (double)a.lo) * inv_scale;
-    rb = ((double)b.hi + (double)b.lo) * inv_scale;
+    for (int k = threadIdx.x; k < nb; k += 32) a += __ldcg(&part[(size_t)kSlotInit * nb + k]);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   }
+  return a;
 }
 
-// y_k = x_k + sum over active columns of the row's scaled blocks (identity diagonal).  The
-// row's columns and blocks come from shared memory (staged once per solve) or from global
-// memory.  The gathers are issued U at a time (U = 4 for FP32 blocks, 2 for FP64 to stay within
-// registers).
-template <typename T>
-__device__ __forceinline__ typename V2<T>::t spmv_row(const int* col, const B4<T>* blk, int deg, int k,
-                                                      const typename V2<T>::t* xv) {
+// ---- product of one row ------------------------------------------------------------------
+// own + sum over the row's active columns j of B_kj nbv(j); `nbv` forms the neighbour's value
+// from vectors written before the last barrier.  Two entries are gathered at a time and summed in
+// separate accumulators (a shorter dependent FP64 chain).
+template <typename T, typename NbF>
+__device__ __forceinline__ typename V2<T>::t row_product(const int* col, const B4<T>* blk, int deg,
+                                                         typename V2<T>::t own, NbF nbv) {
   using V = typename V2<T>::t;
-  constexpr int U = sizeof(T) == 8 ? 2 : 4;
-  V y = ldv(&xv[k]);
-  for (int j = 0; j < deg; j += U) {
-    int c[U];
-#pragma unroll
-    for (int q = 0; q < U; q++) c[q] = (j + q < deg) ? col[j + q] : -1;
-    V xc[U];
-    B4<T> b[U];
-#pragma unroll
-    for (int q = 0; q < U; q++)
-      if (c[q] >= 0) {
-        xc[q] = ldv(&xv[c[q]]);
-        b[q] = blk[j + q];
-      }
-#pragma unroll
-    for (int q = 0; q < U; q++)
-      if (c[q] >= 0) {
-        y.x += b[q].a * xc[q].x + b[q].b * xc[q].y;
-        y.y += b[q].c * xc[q].x + b[q].d * xc[q].y;
-      }
+  V acc0 = own, acc1 = mk<T>(0, 0);
+  for (int j = 0; j < deg; j += 2) {
+    const int c0 = col[j];
+    const int c1 = j + 1 < deg ? col[j + 1] : -1;
+    V x0 = mk<T>(0, 0), x1 = mk<T>(0, 0);
+    B4<T> b0 = {0, 0, 0, 0}, b1 = {0, 0, 0, 0};
+    if (c0 >= 0) {
+      x0 = nbv(c0);
+      b0 = blk[j];
+    }
+    if (c1 >= 0) {
+      x1 = nbv(c1);
+      b1 = blk[j + 1];
+    }
+    acc0.x += b0.a * x0.x + b0.b * x0.y;
+    acc0.y += b0.c * x0.x + b0.d * x0.y;
+    acc1.x += b1.a * x1.x + b1.b * x1.y;
+    acc1.y += b1.c * x1.x + b1.d * x1.y;
   }
-  return y;
+  return mk<T>(acc0.x + acc1.x, acc0.y + acc1.y);
 }
 
-// Forward and backward block-Thomas recurrences of one 32-row chunk as FP32 inclusive scans of
-// 2x2 affine maps.  fwd: w_t = Dinv_t src_t + A_t w_{t-1};  bwd: z_t = w_t - G_t z_{t+1}.
-__device__ __forceinline__ float2 scan_fwd(float2 c, M2<float> A, float2 carry, int lane) {
+// ---- fracture-line solve -----------------------------------------------------------------
+// FP32 block-Thomas recurrences of one 32-row chunk for NR right-hand sides, as inclusive warp
+// scans of 2x2 affine maps.  fwd: w_t = Dinv_t src_t + A_t w_{t-1};  bwd: z_t = w_t - G_t z_{t+1}.
+template <int NR>
+__device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float> A, const float2 (&carry)[NR], int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     M2<float> Ap;
-    float2 cp;
     Ap.a = __shfl_up_sync(0xffffffffu, A.a, o);
     Ap.b = __shfl_up_sync(0xffffffffu, A.b, o);
     Ap.c = __shfl_up_sync(0xffffffffu, A.c, o);
     Ap.d = __shfl_up_sync(0xffffffffu, A.d, o);
-    cp.x = __shfl_up_sync(0xffffffffu, c.x, o);
-    cp.y = __shfl_up_sync(0xffffffffu, c.y, o);
+    float2 cp[NR];
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+      cp[q].x = __shfl_up_sync(0xffffffffu, c[q].x, o);
+      cp[q].y = __shfl_up_sync(0xffffffffu, c[q].y, o);
+    }
     if (lane >= o) {
-      c.x += A.a * cp.x + A.b * cp.y;
-      c.y += A.c * cp.x + A.d * cp.y;
+#pragma unroll
+      for (int q = 0; q < NR; q++) {
+        c[q].x += A.a * cp[q].x + A.b * cp[q].y;
+        c[q].y += A.c * cp[q].x + A.d * cp[q].y;
+      }
       A = mm(A, Ap);
     }
   }
-  return make_float2(c.x + A.a * carry.x + A.b * carry.y, c.y + A.c * carry.x + A.d * carry.y);
+#pragma unroll
+  for (int q = 0; q < NR; q++)
+    c[q] = make_float2(c[q].x + A.a * carry[q].x + A.b * carry[q].y, c[q].y + A.c * carry[q].x + A.d * carry[q].y);
 }
 
-__device__ __forceinline__ float2 scan_bwd(float2 c, M2<float> B, float2 carry, int lane) {
+template <int NR>
+__device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float> B, const float2 (&carry)[NR], int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     M2<float> Bp;
-    float2 cp;
     Bp.a = __shfl_down_sync(0xffffffffu, B.a, o);
     Bp.b = __shfl_down_sync(0xffffffffu, B.b, o);
     Bp.c = __shfl_down_sync(0xffffffffu, B.c, o);
     Bp.d = __shfl_down_sync(0xffffffffu, B.d, o);
-    cp.x = __shfl_down_sync(0xffffffffu, c.x, o);
-    cp.y = __shfl_down_sync(0xffffffffu, c.y, o);
+    float2 cp[NR];
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+      cp[q].x = __shfl_down_sync(0xffffffffu, c[q].x, o);
+      cp[q].y = __shfl_down_sync(0xffffffffu, c[q].y, o);
+    }
     if (lane + o < 32) {
-      c.x += B.a * cp.x + B.b * cp.y;
-      c.y += B.c * cp.x + B.d * cp.y;
+#pragma unroll
+      for (int q = 0; q < NR; q++) {
+        c[q].x += B.a * cp[q].x + B.b * cp[q].y;
+        c[q].y += B.c * cp[q].x + B.d * cp[q].y;
+      }
       B = mm(B, Bp);
     }
   }
-  return make_float2(c.x + B.a * carry.x + B.b * carry.y, c.y + B.c * carry.x + B.d * carry.y);
+#pragma unroll
+  for (int q = 0; q < NR; q++)
+    c[q] = make_float2(c[q].x + B.a * carry[q].x + B.b * carry[q].y, c[q].y + B.c * carry[q].x + B.d * carry[q].y);
 }
 
-// M^{-1} on one fracture line of at most kLineChunks*32 rows, all in registers.  `src[c]` holds
-// the input of row k0 + 32c + lane; the result is stored to dst.  Row t's factors are
-// fac[t*fs] (D'^{-1}), fac[t*fs + fa] (A) and fac[t*fs + fg] (G): shared memory when staged.
-template <typename T>
-__device__ __forceinline__ void line_solve_reg(int k0, int len, const float4* fac, int fs, int fa, int fg,
-                                               const float2* src, typename V2<T>::t* dst) {
+// Factors of one line block: row t's D'^{-1}, A and G at fd[t*fs], fa[t*fs], fg[t*fs].
+struct LineFac {
+  const float4 *fd, *fa, *fg;
+  int fs;
+};
+
+// M^{-1} on one line block (len <= 128 rows) for NR right-hand sides held in registers
+// (src[c][q] = input q of row k0 + 32c + lane); results stored to dst[q][k0 + t].
+template <typename T, int NR>
+__device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, const float2 (&src)[kLineChunks][NR],
+                                           typename V2<T>::t* const (&dst)[NR]) {
   const int lane = threadIdx.x & 31;
-  float2 w[kLineChunks];
-  float2 carry = make_float2(0.f, 0.f);
+  float2 w[kLineChunks][NR];
+  float2 carry[NR];
+#pragma unroll
+  for (int q = 0; q < NR; q++) carry[q] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int c = 0; c < kLineChunks; c++) {
-    w[c] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NR; q++) w[c][q] = make_float2(0.f, 0.f);
     if (c * 32 < len) {
       const int t = c * 32 + lane;
       M2<float> A = {0.f, 0.f, 0.f, 0.f};
-      float2 cc = make_float2(0.f, 0.f);
       if (t < len) {
-        const float4 Di = fac[(size_t)t * fs];
-        cc = make_float2(Di.x * src[c].x + Di.y * src[c].y, Di.z * src[c].x + Di.w * src[c].y);
-        const float4 a4 = fac[(size_t)t * fs + fa];
+        const float4 Di = f.fd[(size_t)t * f.fs];
+#pragma unroll
+        for (int q = 0; q < NR; q++)
+          w[c][q] = make_float2(Di.x * src[c][q].x + Di.y * src[c][q].y, Di.z * src[c][q].x + Di.w * src[c][q].y);
+        const float4 a4 = f.fa[(size_t)t * f.fs];
         A = {a4.x, a4.y, a4.z, a4.w};
       }
-      w[c] = scan_fwd(cc, A, carry, lane);
+      scan_fwd<NR>(w[c], A, carry, lane);
       const int last = min(31, len - 1 - c * 32);
-      carry.x = __shfl_sync(0xffffffffu, w[c].x, last);
-      carry.y = __shfl_sync(0xffffffffu, w[c].y, last);
+#pragma unroll
+      for (int q = 0; q < NR; q++) {
+        carry[q].x = __shfl_sync(0xffffffffu, w[c][q].x, last);
+        carry[q].y = __shfl_sync(0xffffffffu, w[c][q].y, last);
+      }
     }
   }
-  carry = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < NR; q++) carry[q] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int c = kLineChunks - 1; c >= 0; c--) {
     if (c * 32 < len) {
       const int t = c * 32 + lane;
       M2<float> B = {0.f, 0.f, 0.f, 0.f};
-      float2 cc = make_float2(0.f, 0.f);
+      float2 z[NR];
+#pragma unroll
+      for (int q = 0; q < NR; q++) z[q] = make_float2(0.f, 0.f);
       if (t < len) {
-        const float4 g4 = fac[(size_t)t * fs + fg];
+        const float4 g4 = f.fg[(size_t)t * f.fs];
         B = {-g4.x, -g4.y, -g4.z, -g4.w};
-        cc = w[c];
+#pragma unroll
+        for (int q = 0; q < NR; q++) z[q] = w[c][q];
       }
-      const float2 z = scan_bwd(cc, B, carry, lane);
-      if (t < len) dst[k0 + t] = mk<T>((T)z.x, (T)z.y);
-      carry.x = __shfl_sync(0xffffffffu, z.x, 0);
-      carry.y = __shfl_sync(0xffffffffu, z.y, 0);
+      scan_bwd<NR>(z, B, carry, lane);
+#pragma unroll
+      for (int q = 0; q < NR; q++) {
+        if (t < len) dst[q][k0 + t] = mk<T>((T)z[q].x, (T)z[q].y);
+        carry[q].x = __shfl_sync(0xffffffffu, z[q].x, 0);
+        carry[q].y = __shfl_sync(0xffffffffu, z[q].y, 0);
+      }
     }
   }
 }
 
-// M^{-1} on a line longer than kLineChunks*32 rows: chunk by chunk through memory.  `make(k)`
-// produces (and stores) the row's input.
-template <typename T, typename MakeF>
-__device__ __forceinline__ void line_solve_long(const Dev& d, int k0, int len, typename V2<T>::t* dst, MakeF make) {
-  using V = typename V2<T>::t;
-  const int lane = threadIdx.x & 31;
-  const float* ldinv = (const float*)d.line_dinv;
-  const float* la = (const float*)d.line_a;
-  const float* lg = (const float*)d.line_g;
-  float2 carry = make_float2(0.f, 0.f);
-  for (int base = 0; base < len; base += 32) {
-    const int t = base + lane;
-    M2<float> A = {0.f, 0.f, 0.f, 0.f};
-    float2 cc = make_float2(0.f, 0.f);
-    if (t < len) {
-      const size_t k = (size_t)(k0 + t);
-      const V s = make((int)k);
-      const float4 Di = ldf4(&ldinv[4 * k]);
-      cc = make_float2(Di.x * (float)s.x + Di.y * (float)s.y, Di.z * (float)s.x + Di.w * (float)s.y);
-      const float4 a4 = ldf4(&la[4 * k]);
-      A = {a4.x, a4.y, a4.z, a4.w};
-    }
-    const float2 w = scan_fwd(cc, A, carry, lane);
-    if (t < len) dst[k0 + t] = mk<T>((T)w.x, (T)w.y);
-    const int last = min(31, len - 1 - base);
-    carry.x = __shfl_sync(0xffffffffu, w.x, last);
-    carry.y = __shfl_sync(0xffffffffu, w.y, last);
-  }
-  __syncwarp();
-  carry = make_float2(0.f, 0.f);
-  for (int ch = (len + 31) / 32 - 1; ch >= 0; ch--) {
-    const int t = ch * 32 + lane;
-    M2<float> B = {0.f, 0.f, 0.f, 0.f};
-    float2 cc = make_float2(0.f, 0.f);
-    if (t < len) {
-      const V wv = ldv(&dst[k0 + t]);
-      cc = make_float2((float)wv.x, (float)wv.y);
-      const float4 g4 = ldf4(&lg[4 * (size_t)(k0 + t)]);
-      B = {-g4.x, -g4.y, -g4.z, -g4.w};
-    }
-    const float2 z = scan_bwd(cc, B, carry, lane);
-    if (t < len) dst[k0 + t] = mk<T>((T)z.x, (T)z.y);
-    carry.x = __shfl_sync(0xffffffffu, z.x, 0);
-    carry.y = __shfl_sync(0xffffffffu, z.y, 0);
-  }
-  __syncwarp();
-}
-
-// Shared memory of one block: the factors of up to kLineSlots of its lines (3 float4 per row),
-// then the columns and blocks of its rows, packed in row order.
-constexpr int kLineSlots = 4;
-constexpr size_t kLineSmem = (size_t)kLineSlots * kLineChunks * 32 * 3 * sizeof(float4);
-constexpr size_t kKrySmem = 200 * 1024;
+// ---- the solver --------------------------------------------------------------------------
+// A matrix row: off >= 0 is its first entry in the shared-memory pool, off < 0 encodes its first
+// CSR entry e0 as -(e0 + 1) (global memory); deg entries.
+struct RowRef {
+  int off, deg;
+};
 
 template <typename T, bool LINES>
 __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int maxit) {
   using V = typename V2<T>::t;
+  using B = B4<T>;
+  using Ref = RowRef;
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ double sh[72];
-  __shared__ int s_scan[kKryBlk / 32 + 1];
+  __shared__ double sh[kWarps];
+  __shared__ DF s_df[4 * kWarps];
+  __shared__ double s_bc[6];  // beta, alpha_prev, omega_prev, alpha, scale, 1/scale
+  __shared__ int s_ctl;       // 0 continue, 1 stop
+  __shared__ int s_epool;     // next free entry of the shared-memory pool
   const int nA = d.ctr->n_active;
   const int nb = gridDim.x;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // rows: a contiguous chunk per block, spread over all SMs (FP64 throughput is per SM)
   const int rpb = (nA + nb - 1) / nb;
-  const int r0 = min(nA, blockIdx.x * rpb), r1 = min(nA, r0 + rpb);
+  const int r0 = min(nA, (int)blockIdx.x * rpb), r1 = min(nA, r0 + rpb);
   const int kbeg = r0 + (int)threadIdx.x, kstep = blockDim.x;
-  const int nw = min((int)(blockDim.x >> 5), (r1 - r0 + 31) / 32);
   const int nlines = LINES ? d.ctr->n_lines : 0;
-  // (s, s) also collects the line rows' contributions from the line warps
-  const int nw_ss = LINES ? (int)(blockDim.x >> 5) : nw;
-  V* __restrict__ x = (V*)d.kx;
-  V* __restrict__ r = (V*)d.kr;
-  V* __restrict__ rh = (V*)d.krh;
-  V* __restrict__ p = (V*)d.kp;
-  V* __restrict__ v = (V*)d.kv;
-  V* __restrict__ s = (V*)d.ks;
-  V* __restrict__ t = (V*)d.kt;
-  V* ph = LINES ? (V*)d.kph : p;
-  V* shv = LINES ? (V*)d.ksh : s;
+  const int nw = LINES ? kWarps : min(kWarps, (r1 - r0 + 31) / 32);  // warps holding values
+  V* const x = (V*)d.kx;
+  V* const r = (V*)d.kr;
+  V* const rh = (V*)d.krh;
+  V* const v = (V*)d.kv;
+  V* const s = (V*)d.ks;
+  V* const t = (V*)d.kt;
+  V* const z = (V*)d.kz;
+  V* const rt = LINES ? (V*)d.krt : r;    // M = I without lines: r~ = r, z^ = s, t~ = t
+  V* const zf = LINES ? (V*)d.kzf : s;
+  V* const tt = LINES ? (V*)d.ktt : t;
+  V* const yb[2] = {(V*)d.ky0, (V*)d.ky1};
+  V* const vtb[2] = {(V*)d.kvt0, (V*)d.kvt1};
   const V* b = (const V*)d.rhs;
   const T* blocks = (const T*)d.blocks;
   const int* lflag = d.line_row_flag;
   double* part = d.partials;
   float4* s_fac = (float4*)dsm;
-  const int ecap = (int)((kKrySmem - kLineSmem) / (sizeof(int) + sizeof(B4<T>)));
-  B4<T>* s_blk = (B4<T>*)(dsm + kLineSmem);
-  int* s_col = (int*)(dsm + kLineSmem + (size_t)ecap * sizeof(B4<T>));
+  const int ecap = (int)((kKrySmem - kLineSmem) / (sizeof(int) + sizeof(B)));
+  B* s_blk = (B*)(dsm + kLineSmem);
+  int* s_col = (int*)(dsm + kLineSmem + (size_t)ecap * sizeof(B));
+  if (threadIdx.x == 0) s_epool = 0;
+  __syncthreads();
 
-  // Stage the columns and blocks of this thread's first rows in shared memory (packed in row
-  // order by a block scan of the row degrees); rows that do not fit read global memory.
-  const int* rcol[kRowsCached];
-  const B4<T>* rblk[kRowsCached];
-  int rdeg[kRowsCached], rfl[kRowsCached];
-  int ebase = 0;
+  auto global_ref = [&](int k) -> Ref {
+    const int i = __ldg(&d.act[k]);
+    const int e0 = __ldg(&d.row_ptr[i]);
+    return {-(e0 + 1), __ldg(&d.row_ptr[i + 1]) - e0};
+  };
+  // stage a row's columns and blocks in the shared pool (placement does not affect the result)
+  auto stage = [&](int k) -> Ref {
+    const Ref g = global_ref(k);
+    const int off = atomicAdd(&s_epool, g.deg);
+    if (off + g.deg > ecap) return g;
+    const int e0 = -(g.off + 1);
+    for (int j = 0; j < g.deg; j++) {
+      s_col[off + j] = __ldg(&d.colA[e0 + j]);
+      s_blk[off + j] = *(const B*)&blocks[4 * (size_t)(e0 + j)];
+    }
+    return {off, g.deg};
+  };
+  // product of a row with a vector whose own value is `own` and whose neighbour values come from nbv
+  auto product = [&](const Ref& ref, const V& own, auto nbv) -> V {
+    if (ref.off >= 0) return row_product<T>(s_col + ref.off, s_blk + ref.off, ref.deg, own, nbv);
+    const size_t e0 = (size_t)(-(ref.off + 1));
+    return row_product<T>(d.colA + e0, (const B*)&blocks[4 * e0], ref.deg, own, nbv);
+  };
+  // this thread's first non-line rows
+  Ref rr_[kRowsCached];
+  int rk_[kRowsCached];
 #pragma unroll
   for (int q = 0; q < kRowsCached; q++) {
     const int k = kbeg + q * kstep;
-    int e0 = 0, deg = 0;
-    rfl[q] = 1;
-    if (k < r1) {
-      const int i = __ldg(&d.act[k]);
-      e0 = __ldg(&d.row_ptr[i]);
-      deg = __ldg(&d.row_ptr[i + 1]) - e0;
-      rfl[q] = LINES ? __ldg(&lflag[k]) : 0;
-    }
-    // exclusive block scan of deg
-    int inc = deg;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_scan[wib] = inc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int acc = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-        const int c = s_scan[w];
-        s_scan[w] = acc;
-        acc += c;
-      }
-      s_scan[kKryBlk / 32] = acc;
-    }
-    __syncthreads();
-    const int off = ebase + s_scan[wib] + inc - deg;
-    ebase += s_scan[kKryBlk / 32];
-    __syncthreads();
-    rdeg[q] = deg;
-    if (off + deg <= ecap) {
-      for (int j = 0; j < deg; j++) {
-        s_col[off + j] = __ldg(&d.colA[e0 + j]);
-        s_blk[off + j] = *(const B4<T>*)&blocks[4 * (size_t)(e0 + j)];
-      }
-      rcol[q] = s_col + off;
-      rblk[q] = s_blk + off;
-    } else {
-      rcol[q] = d.colA + e0;
-      rblk[q] = (const B4<T>*)&blocks[4 * (size_t)e0];
+    rk_[q] = -1;
+    rr_[q] = {0, 0};
+    if (k < r1 && !(LINES && __ldg(&lflag[k]))) {
+      rk_[q] = k;
+      rr_[q] = stage(k);
     }
   }
-  // Stage the factors of this block's first kLineSlots lines (line l lives in block l % nb).
-  if (LINES)
-    for (int j = wib; j < kLineSlots; j += (int)(blockDim.x >> 5)) {
-      const int l = (int)blockIdx.x + nb * j;
-      if (l >= nlines) continue;
-      const int k0 = __ldg(&d.line_start[l]), len = __ldg(&d.line_len[l]);
-      if (len > kLineChunks * 32) continue;
-      for (int tt = lane; tt < len; tt += 32) {
-        const size_t k = (size_t)(k0 + tt);
-        float4* dst = &s_fac[((size_t)j * kLineChunks * 32 + tt) * 3];
-        dst[0] = ldf4(&((const float*)d.line_dinv)[4 * k]);
-        dst[1] = ldf4(&((const float*)d.line_a)[4 * k]);
-        dst[2] = ldf4(&((const float*)d.line_g)[4 * k]);
+  // this warp's first line block (l = blockIdx + nb * wib): rows staged, factors staged if a slot is free
+  Ref lr_[kLineChunks];
+  int lk0 = 0, llen = 0;
+  auto gfac = [&](int k0) -> LineFac {
+    return {(const float4*)d.line_dinv + k0, (const float4*)d.line_a + k0, (const float4*)d.line_g + k0, 1};
+  };
+  auto sfac = [&]() -> LineFac {
+    const float4* base = &s_fac[(size_t)wib * kLineChunks * 32 * 3];
+    return {base, base + 1, base + 2, 3};
+  };
+  if (LINES) {
+    const int l = (int)blockIdx.x + nb * wib;
+    if (l < nlines) {
+      lk0 = __ldg(&d.line_start[l]);
+      llen = __ldg(&d.line_len[l]);
+      if (wib < kLineSlots) {
+        const LineFac g = gfac(lk0);
+        float4* base = &s_fac[(size_t)wib * kLineChunks * 32 * 3];
+        for (int q = lane; q < llen; q += 32) {
+          base[3 * q] = g.fd[q];
+          base[3 * q + 1] = g.fa[q];
+          base[3 * q + 2] = g.fg[q];
+        }
       }
     }
+#pragma unroll
+    for (int c = 0; c < kLineChunks; c++) {
+      lr_[c] = {0, 0};
+      if (c * 32 + lane < llen) lr_[c] = stage(lk0 + c * 32 + lane);
+    }
+  }
   __syncthreads();
-  // visit this thread's rows: fn(k, col, blk, deg, line_flag)
+
+  // fn(k, ref) over this thread's non-line rows
   auto rows = [&](auto fn) {
 #pragma unroll
-    for (int q = 0; q < kRowsCached; q++) {
-      const int k = kbeg + q * kstep;
-      if (k < r1) fn(k, rcol[q], rblk[q], rdeg[q], rfl[q]);
-    }
+    for (int q = 0; q < kRowsCached; q++)
+      if (rk_[q] >= 0) fn(rk_[q], rr_[q]);
     for (int k = kbeg + kRowsCached * kstep; k < r1; k += kstep) {
-      const int i = __ldg(&d.act[k]);
-      const int e0 = __ldg(&d.row_ptr[i]);
-      fn(k, d.colA + e0, (const B4<T>*)&blocks[4 * (size_t)e0], __ldg(&d.row_ptr[i + 1]) - e0,
-         LINES ? __ldg(&lflag[k]) : 0);
+      if (LINES && __ldg(&lflag[k])) continue;
+      fn(k, global_ref(k));
     }
   };
-  // visit this block's lines: fn(k0, len, factors, stride, offA, offG); line l lives in block l % nb
+  // fn(k0, len, factors, refs) over this warp's line blocks (warp-uniform)
   auto lines = [&](auto fn) {
-    for (int j = wib;; j += (int)(blockDim.x >> 5)) {
-      const int l = (int)blockIdx.x + nb * j;
-      if (l >= nlines) break;
-      const int k0 = __ldg(&d.line_start[l]), len = __ldg(&d.line_len[l]);
-      if (j < kLineSlots && len <= kLineChunks * 32)
-        fn(k0, len, (const float4*)&s_fac[(size_t)j * kLineChunks * 32 * 3], 3, 1, 2);
-      else
-        fn(k0, len, (const float4*)nullptr, 0, 0, 0);
+    if constexpr (LINES) {
+      for (int j = wib;; j += kWarps) {
+        const int l = (int)blockIdx.x + nb * j;
+        if (l >= nlines) break;
+        if (j == wib) {
+          fn(lk0, llen, wib < kLineSlots ? sfac() : gfac(lk0), lr_);
+        } else {
+          const int k0 = __ldg(&d.line_start[l]), len = __ldg(&d.line_len[l]);
+          Ref refs[kLineChunks];
+#pragma unroll
+          for (int c = 0; c < kLineChunks; c++) {
+            refs[c] = {0, 0};
+            if (c * 32 + lane < len) refs[c] = global_ref(k0 + c * 32 + lane);
+          }
+          fn(k0, len, gfac(k0), refs);
+        }
+      }
     }
   };
 
-  // Scalars of the recurrence live in thread 0 (FP64 division and square root are long FP64
-  // sequences here: computed once per block, broadcast through shared memory).
-  __shared__ double s_bc[6];  // broadcast: beta, omega (phase A), alpha (C..E), omega (E), scale, 1/scale
-  __shared__ int s_ctl;       // 0 continue, 1 converged, 2 breakdown
-  __shared__ float4 s_df[kKryBlk / 32];
+  // ---- initialisation: x = z = t = t~ = y_0 = v~_0 = 0, s = r^ = b, z^ = M^{-1} b -------------
   double l_bb = 0.0;
-  rows([&](int k, const int*, const B4<T>*, int, int) {
+  auto init_row = [&](int k) -> V {
     const V bk = b[k];
-    x[k] = mk<T>(0, 0);
-    r[k] = bk;
+    const V o = mk<T>(0, 0);
+    x[k] = o;
+    z[k] = o;
+    t[k] = o;
+    tt[k] = o;
+    yb[0][k] = o;
+    vtb[0][k] = o;
+    s[k] = bk;
     rh[k] = bk;
-    p[k] = mk<T>(0, 0);
-    v[k] = mk<T>(0, 0);
     l_bb += (double)bk.x * bk.x + (double)bk.y * bk.y;
+    return bk;
+  };
+  rows([&](int k, const Ref&) { zf[k] = init_row(k); });
+  lines([&](int k0, int len, const LineFac& f, const Ref*) {
+    float2 src[kLineChunks][1];
+#pragma unroll
+    for (int c = 0; c < kLineChunks; c++) {
+      src[c][0] = make_float2(0.f, 0.f);
+      if (c * 32 + lane < len) {
+        const V bk = init_row(k0 + c * 32 + lane);
+        src[c][0] = make_float2((float)bk.x, (float)bk.y);
+      }
+    }
+    V* const dst[1] = {zf};
+    line_solve<T, 1>(k0, len, f, src, dst);
   });
-  block_store2(l_bb, 0.0, sh, part, 0, nb, nw);
+  block_store_f64(l_bb, sh, part, nb);
   grid.sync();
-  double bb = 0.0, dummy, rho = 0.0, rho_old = 1.0, alpha = 1.0, omega = 1.0, stop2 = 0.0, relres = 0.0;
-  grid_sum2(part, 0, nb, bb, dummy);
+  const double bb = grid_sum_f64(part, nb);
+  double rho = 0.0, alpha = 0.0, stop2 = 0.0, rr_last = 0.0;
   if (threadIdx.x == 0) {
-    s_ctl = bb > 0.0 ? 0 : 1;
     rho = bb;
     stop2 = rtol * rtol * bb;
-    // exact power of two near 1/bb (biased exponent 2046 - E of bb, clamped to normal range)
+    // exact power of two near 1/bb (biased exponent 2046 - E of bb, clamped to the normal range)
     long long e = bb > 0.0 ? ((__double_as_longlong(bb) >> 52) & 0x7ff) : 1023;
     e = e < 1 ? 1 : (e > 2045 ? 2045 : e);
     s_bc[4] = __longlong_as_double((2046 - e) << 52);
     s_bc[5] = __longlong_as_double(e << 52);
+    s_bc[0] = 0.0;  // beta_1
+    s_bc[1] = 0.0;  // alpha_0
+    s_bc[2] = 0.0;  // omega_0
+    s_ctl = 0;
   }
   __syncthreads();
   const double dscale = s_bc[4], dinv = s_bc[5];
-  int status = 0, it = 0;
-  if (s_ctl == 0) {
-    status = 1;
-    for (it = 1; it <= maxit; it++) {
+  int status = 1, it;
+  for (it = 1;; it++) {
+    // ---- phase 1 -------------------------------------------------------------------------
+    const T beta = (T)s_bc[0], alp = (T)s_bc[1], omp = (T)s_bc[2], nom = -omp;
+    const V* yo = yb[(it + 1) & 1];
+    V* yn = yb[it & 1];
+    const V* vto = vtb[(it + 1) & 1];
+    V* vtn = vtb[it & 1];
+    // r~_{i-1} and y_i of a row from stored vectors (the owner evaluates the same expressions)
+    auto rt_of = [&](int c) { return axpy(nom, ldv(&tt[c]), ldv(&zf[c])); };
+    auto y_of = [&](const V& rtc, int c) { return axpy(beta, axpy(nom, ldv(&vto[c]), ldv(&yo[c])), rtc); };
+    auto ynb = [&](int c) { return y_of(rt_of(c), c); };
+    double l_rv = 0.0, l_rr = 0.0;
+    auto p1_row = [&](int k, const Ref& ref) -> V {
+      const V xk = ldv(&x[k]), yk = ldv(&yo[k]), zk = ldv(&z[k]), sk = ldv(&s[k]), tk = ldv(&t[k]),
+              rhk = ldv(&rh[k]);
+      x[k] = mk<T>(xk.x + alp * yk.x + omp * zk.x, xk.y + alp * yk.y + omp * zk.y);
+      const V rk = axpy(nom, tk, sk);
+      r[k] = rk;
+      l_rr += (double)rk.x * rk.x + (double)rk.y * rk.y;
+      const V rtk = rt_of(k);
+      if (LINES) rt[k] = rtk;
+      const V ynk = y_of(rtk, k);
+      yn[k] = ynk;
+      const V vv = product(ref, ynk, ynb);
+      v[k] = vv;
+      l_rv += (double)rhk.x * vv.x + (double)rhk.y * vv.y;
+      return vv;
+    };
+    rows([&](int k, const Ref& ref) { vtn[k] = p1_row(k, ref); });
+    lines([&](int k0, int len, const LineFac& f, const Ref* refs) {
+      float2 src[kLineChunks][1];
+#pragma unroll
+      for (int c = 0; c < kLineChunks; c++) {
+        src[c][0] = make_float2(0.f, 0.f);
+        if (c * 32 + lane < len) {
+          const V vv = p1_row(k0 + c * 32 + lane, refs[c]);
+          src[c][0] = make_float2((float)vv.x, (float)vv.y);
+        }
+      }
+      V* const dst[1] = {vtn};
+      line_solve<T, 1>(k0, len, f, src, dst);
+    });
+    {
+      const double vals[2] = {l_rv, l_rr};
+      block_store<2>(vals, dscale, s_df, part, kSlotS1, nb, nw);
+    }
+    grid.sync();
+    {
+      double o[2];
+      grid_sum<2>(part, kSlotS1, nb, dinv, o);
       if (threadIdx.x == 0) {
-        s_bc[0] = it == 1 ? 0.0 : (rho / rho_old) * (alpha / omega);
-        s_bc[1] = omega;
-      }
-      __syncthreads();
-      const T beta = (T)s_bc[0];
-      const T om = (T)s_bc[1];
-      // Phase A: p = r + beta (p - omega v);  ph = M^{-1} p
-      rows([&](int k, const int*, const B4<T>*, int, int fl) {
-        if (LINES && fl) return;
-        const V rk = ldv(&r[k]), pk = ldv(&p[k]), vk = ldv(&v[k]);
-        const V np = mk<T>(rk.x + beta * (pk.x - om * vk.x), rk.y + beta * (pk.y - om * vk.y));
-        p[k] = np;
-        if (LINES) ph[k] = np;
-      });
-      if (LINES)
-        lines([&](int k0, int len, const float4* fac, int fs, int fa, int fg) {
-          if (fac) {
-            // all of the line's loads first (p, then r and v), then the updates: one L2 round trip
-            V pk[kLineChunks];
-            float2 src[kLineChunks];
-#pragma unroll
-            for (int c = 0; c < kLineChunks; c++)
-              if (c * 32 + lane < len) pk[c] = ldv(&p[k0 + c * 32 + lane]);
-#pragma unroll
-            for (int c = 0; c < kLineChunks; c++) {
-              src[c] = make_float2(0.f, 0.f);
-              if (c * 32 + lane < len) {
-                const int k = k0 + c * 32 + lane;
-                const V rk = ldv(&r[k]), vk = ldv(&v[k]);
-                const V np = mk<T>(rk.x + beta * (pk[c].x - om * vk.x), rk.y + beta * (pk[c].y - om * vk.y));
-                p[k] = np;
-                src[c] = make_float2((float)np.x, (float)np.y);
-              }
-            }
-            line_solve_reg<T>(k0, len, fac, fs, fa, fg, src, ph);
-          } else {
-            line_solve_long<T>(d, k0, len, ph, [&](int k) {
-              const V rk = ldv(&r[k]), pk = ldv(&p[k]), vk = ldv(&v[k]);
-              const V np = mk<T>(rk.x + beta * (pk.x - om * vk.x), rk.y + beta * (pk.y - om * vk.y));
-              p[k] = np;
-              return np;
-            });
-          }
-        });
-      grid.sync();
-      // Phase B: v = A ph, (rh, v)
-      double l_rv = 0.0;
-      rows([&](int k, const int* col, const B4<T>* blk, int deg, int) {
-        const V rhk = ldv(&rh[k]);
-        const V vk = spmv_row<T>(col, blk, deg, k, ph);
-        v[k] = vk;
-        l_rv += (double)rhk.x * vk.x + (double)rhk.y * vk.y;
-      });
-      block_store_df(l_rv, 0.0, dscale, s_df, part, 2, nb, nw);
-      grid.sync();
-      {
-        double rv;
-        grid_sum_df(part, 2, nb, dinv, rv, dummy);
-        if (threadIdx.x == 0) {
-          if (rv == 0.0 || !isfinite(rv)) {
-            s_ctl = 2;
-          } else {
-            alpha = rho / rv;
-            s_bc[2] = alpha;
-          }
-        }
-      }
-      __syncthreads();
-      if (s_ctl == 2) {
-        status = 2;
-        break;
-      }
-      const T al = (T)s_bc[2];
-      // Phase C: s = r - alpha v; shv = M^{-1} s; (s, s)
-      double l_ss = 0.0;
-      rows([&](int k, const int*, const B4<T>*, int, int fl) {
-        if (LINES && fl) return;
-        const V rk = ldv(&r[k]), vk = ldv(&v[k]);
-        const V sk = mk<T>(rk.x - al * vk.x, rk.y - al * vk.y);
-        s[k] = sk;
-        if (LINES) shv[k] = sk;
-        l_ss += (double)sk.x * sk.x + (double)sk.y * sk.y;
-      });
-      if (LINES)
-        lines([&](int k0, int len, const float4* fac, int fs, int fa, int fg) {
-          if (fac) {
-            float2 src[kLineChunks];
-#pragma unroll
-            for (int c = 0; c < kLineChunks; c++) {
-              src[c] = make_float2(0.f, 0.f);
-              if (c * 32 + lane < len) {
-                const int k = k0 + c * 32 + lane;
-                const V rk = ldv(&r[k]), vk = ldv(&v[k]);
-                const V sk = mk<T>(rk.x - al * vk.x, rk.y - al * vk.y);
-                s[k] = sk;
-                l_ss += (double)sk.x * sk.x + (double)sk.y * sk.y;
-                src[c] = make_float2((float)sk.x, (float)sk.y);
-              }
-            }
-            line_solve_reg<T>(k0, len, fac, fs, fa, fg, src, shv);
-          } else {
-            double acc = 0.0;
-            line_solve_long<T>(d, k0, len, shv, [&](int k) {
-              const V rk = ldv(&r[k]), vk = ldv(&v[k]);
-              const V sk = mk<T>(rk.x - al * vk.x, rk.y - al * vk.y);
-              s[k] = sk;
-              acc += (double)sk.x * sk.x + (double)sk.y * sk.y;
-              return sk;
-            });
-            l_ss += acc;
-          }
-        });
-      block_store_df(l_ss, 0.0, dscale, s_df, part, 4, nb, nw_ss);
-      grid.sync();
-      {
-        double ss;
-        grid_sum_df(part, 4, nb, dinv, ss, dummy);
-        if (threadIdx.x == 0 && ss <= stop2) {
+        rr_last = o[1];
+        if (o[1] <= stop2) {
           s_ctl = 1;
-          relres = sqrt(ss / bb);
+          status = 0;
+        } else if (it > maxit) {
+          s_ctl = 1;
+          status = 1;
+        } else if (o[0] == 0.0 || !isfinite(o[0]) || rho == 0.0 || !isfinite(rho)) {
+          s_ctl = 1;
+          status = 2;
+        } else {
+          alpha = rho / o[0];
+          s_bc[3] = alpha;
         }
-      }
-      __syncthreads();
-      if (s_ctl == 1) {
-        rows([&](int k, const int*, const B4<T>*, int, int) {
-          const V xk = ldv(&x[k]), pk = ldv(&ph[k]);
-          x[k] = mk<T>(xk.x + al * pk.x, xk.y + al * pk.y);
-        });
-        status = 0;
-        break;
-      }
-      // Phase D: t = A shv; (t, s), (t, t)
-      double l_ts = 0.0, l_tt = 0.0;
-      rows([&](int k, const int* col, const B4<T>* blk, int deg, int) {
-        const V sk = ldv(&s[k]);
-        const V tk = spmv_row<T>(col, blk, deg, k, shv);
-        t[k] = tk;
-        l_ts += (double)tk.x * sk.x + (double)tk.y * sk.y;
-        l_tt += (double)tk.x * tk.x + (double)tk.y * tk.y;
-      });
-      block_store_df(l_ts, l_tt, dscale, s_df, part, 6, nb, nw);
-      grid.sync();
-      {
-        double ts, tt;
-        grid_sum_df(part, 6, nb, dinv, ts, tt);
-        if (threadIdx.x == 0) {
-          if (tt == 0.0 || !isfinite(tt)) {
-            s_ctl = 2;
-          } else {
-            omega = ts / tt;
-            s_bc[3] = omega;
-          }
-        }
-      }
-      __syncthreads();
-      if (s_ctl == 2) {
-        status = 2;
-        break;
-      }
-      const T omg = (T)s_bc[3];
-      // Phase E: x += alpha ph + omega shv; r = s - omega t; (rh, r), (r, r)
-      double l_rr = 0.0, l_rhr = 0.0;
-      rows([&](int k, const int*, const B4<T>*, int, int) {
-        const V xk = ldv(&x[k]), pk = ldv(&ph[k]), sk2 = ldv(&shv[k]), sk = ldv(&s[k]), tk = ldv(&t[k]),
-                rhk = ldv(&rh[k]);
-        x[k] = mk<T>(xk.x + al * pk.x + omg * sk2.x, xk.y + al * pk.y + omg * sk2.y);
-        const V rk = mk<T>(sk.x - omg * tk.x, sk.y - omg * tk.y);
-        r[k] = rk;
-        l_rr += (double)rk.x * rk.x + (double)rk.y * rk.y;
-        l_rhr += (double)rhk.x * rk.x + (double)rhk.y * rk.y;
-      });
-      block_store_df(l_rhr, l_rr, dscale, s_df, part, 0, nb, nw);
-      grid.sync();
-      {
-        double rr, rhr;
-        grid_sum_df(part, 0, nb, dinv, rhr, rr);
-        if (threadIdx.x == 0) {
-          rho_old = rho;
-          rho = rhr;
-          relres = sqrt(rr / bb);
-          if (rr <= stop2)
-            s_ctl = 1;
-          else if (rho == 0.0 || omega == 0.0 || !isfinite(rho))
-            s_ctl = 2;
-        }
-      }
-      __syncthreads();
-      if (s_ctl == 1) {
-        status = 0;
-        break;
-      }
-      if (s_ctl == 2) {
-        status = 2;
-        break;
       }
     }
-    if (it > maxit) it = maxit;
-  } else {
-    rows([&](int k, const int*, const B4<T>*, int, int) { x[k] = mk<T>(0, 0); });
+    __syncthreads();
+    if (s_ctl) break;
+    // ---- phase 2 -------------------------------------------------------------------------
+    const T nal = -(T)s_bc[3];
+    auto znb = [&](int c) { return axpy(nal, ldv(&vtn[c]), ldv(&rt[c])); };
+    double l_ts = 0.0, l_tt = 0.0, l_rs = 0.0, l_rt = 0.0;
+    V sk_, tk_;
+    auto p2_row = [&](int k, const Ref& ref) {
+      const V rk = ldv(&r[k]), vk = ldv(&v[k]), rhk = ldv(&rh[k]);
+      const V sk = axpy(nal, vk, rk);
+      s[k] = sk;
+      const V zk = znb(k);
+      z[k] = zk;
+      const V tk = product(ref, zk, znb);
+      t[k] = tk;
+      l_ts += (double)tk.x * sk.x + (double)tk.y * sk.y;
+      l_tt += (double)tk.x * tk.x + (double)tk.y * tk.y;
+      l_rs += (double)rhk.x * sk.x + (double)rhk.y * sk.y;
+      l_rt += (double)rhk.x * tk.x + (double)rhk.y * tk.y;
+      sk_ = sk;
+      tk_ = tk;
+    };
+    rows([&](int k, const Ref& ref) {
+      p2_row(k, ref);
+      if (LINES) {
+        zf[k] = sk_;
+        tt[k] = tk_;
+      }
+    });
+    lines([&](int k0, int len, const LineFac& f, const Ref* refs) {
+      float2 src[kLineChunks][2];
+#pragma unroll
+      for (int c = 0; c < kLineChunks; c++) {
+        src[c][0] = src[c][1] = make_float2(0.f, 0.f);
+        if (c * 32 + lane < len) {
+          p2_row(k0 + c * 32 + lane, refs[c]);
+          src[c][0] = make_float2((float)sk_.x, (float)sk_.y);
+          src[c][1] = make_float2((float)tk_.x, (float)tk_.y);
+        }
+      }
+      V* const dst[2] = {zf, tt};
+      line_solve<T, 2>(k0, len, f, src, dst);
+    });
+    {
+      const double vals[4] = {l_ts, l_tt, l_rs, l_rt};
+      block_store<4>(vals, dscale, s_df, part, kSlotS2, nb, nw);
+    }
+    grid.sync();
+    {
+      double o[4];
+      grid_sum<4>(part, kSlotS2, nb, dinv, o);
+      if (threadIdx.x == 0) {
+        const double ts = o[0], t2 = o[1], rs = o[2], rtv = o[3];
+        if (!isfinite(ts) || !isfinite(t2) || !isfinite(rs) || !isfinite(rtv)) {
+          s_ctl = 1;
+          status = 2;
+        } else {
+          // t = 0 means A z = 0: omega = 0 leaves r = s and restarts the direction (beta = 0)
+          const double omega = t2 > 0.0 ? ts / t2 : 0.0;
+          const double rho_new = rs - omega * rtv;
+          s_bc[0] = omega != 0.0 ? (rho_new / rho) * (alpha / omega) : 0.0;
+          s_bc[1] = alpha;
+          s_bc[2] = omega;
+          rho = rho_new;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_ctl) break;
   }
-  if (tid == 0) {  // thread 0 of block 0 holds the scalars
-    d.ctr->krylov_iters = it;
+  // x holds x_{it-1} at every exit; thread 0 of block 0 reports
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.ctr->krylov_iters = it - 1;
     d.ctr->krylov_status = status;
-    d.ctr->krylov_relres = relres;
+    d.ctr->krylov_relres = bb > 0.0 ? sqrt(rr_last / bb) : 0.0;
   }
 }
 

@@ -700,8 +700,9 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
     AL(d.line_start, N);
     AL(d.line_len, N);
     AL(d.line_row_flag, N);
-    double** vecs[9] = {(double**)&d.kx, (double**)&d.kr, (double**)&d.krh, (double**)&d.kp, (double**)&d.kv,
-                        (double**)&d.ks, (double**)&d.kt, (double**)&d.kph, (double**)&d.ksh};
+    double** vecs[14] = {(double**)&d.kx,  (double**)&d.kr,   (double**)&d.krh,  (double**)&d.ky0, (double**)&d.ky1,
+                         (double**)&d.kv,  (double**)&d.ks,   (double**)&d.kt,   (double**)&d.kz,  (double**)&d.kvt0,
+                         (double**)&d.kvt1, (double**)&d.krt, (double**)&d.kzf, (double**)&d.ktt};
     for (auto v : vecs) AL(*v, N * 2);
     AL(d.partials, (size_t)8 * 4 * m->sms + 64);
   }

@@ -10,7 +10,7 @@
 //   system       : blocks[E2] 2x2 off-diagonal blocks stored at the CSR entry of their
 //                  row (f64 or f32), colA[E2] compact column or -1, rhs[2n]; the diagonal
 //                  blocks are scaled to the identity and not stored
-//   Krylov       : x, r, rhat, p, v, s, t, phat, shat [2n] (f64 or f32), partial sums
+//   Krylov       : x, r, rhat, y[2], v, s, t, z, v~[2], r~, z~, t~ [2n] (f64 or f32), partial sums
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -34,7 +34,8 @@ struct IterCounters {
   int any_e;           // some boundary cell had a non-negligible update
   int any_s;           // the support of du_A is non-empty
   int any_new;         // Algorithm 2: the next subdomain is non-empty
-  int n_lines;         // fracture line blocks in the compacted system
+  int n_lines;         // fracture line blocks in the compacted system (after cutting long lines)
+  int n_line_starts;   // line starts found by the marking pass (fixed while the factor pass appends)
   int krylov_iters;
   int krylov_status;   // 0 ok, 1 maxit, 2 breakdown
   int converged;
@@ -73,7 +74,7 @@ struct Dev {
   void *line_dinv, *line_a, *line_g;
   int *line_start, *line_len, *line_row_flag;
   // Krylov vectors
-  void *kx, *kr, *krh, *kp, *kv, *ks, *kt, *kph, *ksh;
+  void *kx, *kr, *krh, *ky0, *ky1, *kv, *ks, *kt, *kz, *kvt0, *kvt1, *krt, *kzf, *ktt;
   double* partials;
   IterCounters* ctr;   // device
   IterCounters* ctr_h; // pinned host mirror
