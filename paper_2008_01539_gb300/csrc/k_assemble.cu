@@ -257,7 +257,7 @@ __global__ void k_line_mark(Dev d) {
 // L_t: row t -> t-1) 32 rows at a time into shared memory, in FP32; lane 0 runs the block
 // Thomas recurrence over the staged rows; the warp stores D'^{-1}, A and G (FP32) per row.
 constexpr int kLineWarps = 4;
-constexpr int kMaxLineRows = 128;  // one warp holds a line block in registers (4 chunks of 32)
+constexpr int kMaxLineRows = kLineBlockRows;
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {

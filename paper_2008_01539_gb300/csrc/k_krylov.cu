@@ -41,10 +41,10 @@ namespace lns {
 
 namespace {
 
-constexpr int kKryBlk = 512;
+constexpr int kKryBlk = 256;
 constexpr int kWarps = kKryBlk / 32;
-constexpr int kRowsCached = 2;   // non-line rows per thread whose matrix row is staged
-constexpr int kLineChunks = 4;   // 32-row chunks of a line block
+constexpr int kRowsCached = 4;   // non-line rows per thread whose matrix row is staged
+constexpr int kLineChunks = kLineBlockRows / 32;  // 32-row chunks of a line block
 constexpr int kLineSlots = 4;    // line blocks per block whose factors are staged in shared memory
 constexpr size_t kLineSmem = (size_t)kLineSlots * kLineChunks * 32 * 3 * sizeof(float4);
 constexpr size_t kKrySmem = 200 * 1024;
@@ -123,29 +123,48 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
-// Block partials of NV scaled values into slots [slot, slot+NV) as (hi, lo) pairs.  Warps
-// w >= nw hold nothing and skip the conversions.  Contains one block barrier.
+// Dot products of one thread's rows.  FP64 vectors: fused FP64 products, converted to double-float
+// (after scaling) once per phase.  FP32 vectors: exact FP32 products (p + e, e = fma(a, b, -p))
+// summed in double-float, so the FP32 path issues no FP64 instruction per row.
+template <typename T>
+struct DotAcc {
+  using t = double;
+};
+template <>
+struct DotAcc<float> {
+  using t = DF;
+};
+__device__ __forceinline__ void dot_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void dot_zero(DF& a) { a = DF{0.f, 0.f}; }
+__device__ __forceinline__ void dot_acc(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void dot_acc(DF& acc, float a, float b) {
+  const float p = a * b;
+  acc = df_add(acc, DF{p, fmaf(a, b, -p)});
+}
+__device__ __forceinline__ DF dot_df(double acc, double scale) { return df_from(acc * scale); }
+__device__ __forceinline__ DF dot_df(DF acc, double) { return acc; }
+
+// Block partials of NV values into slots [slot, slot+NV) as (hi, lo) pairs.  Warps with nothing
+// to add (busy == false) contribute zeros without converting.  Contains one block barrier.
 template <int NV>
-__device__ __forceinline__ void block_store(const double (&vals)[NV], double scale, DF* sdf, double* part, int slot,
-                                            int nb, int nw) {
+__device__ __forceinline__ void block_store(const DF (&vals)[NV], bool busy, DF* sdf, double* part, int slot, int nb) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (w < nw) {
-    DF a[NV];
+  DF a[NV];
 #pragma unroll
-    for (int q = 0; q < NV; q++) a[q] = df_from(vals[q] * scale);
+  for (int q = 0; q < NV; q++) a[q] = busy ? vals[q] : DF{0.f, 0.f};
+  if (busy) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
       for (int q = 0; q < NV; q++) a[q] = df_add(a[q], df_shfl_xor(a[q], o));
-    if (lane == 0)
-#pragma unroll
-      for (int q = 0; q < NV; q++) sdf[q * kWarps + w] = a[q];
   }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; q++) sdf[q * kWarps + w] = a[q];
   __syncthreads();
   if (w == 0) {
-    DF a[NV];
 #pragma unroll
-    for (int q = 0; q < NV; q++) a[q] = lane < nw ? sdf[q * kWarps + lane] : DF{0.f, 0.f};
+    for (int q = 0; q < NV; q++) a[q] = lane < kWarps ? sdf[q * kWarps + lane] : DF{0.f, 0.f};
 #pragma unroll
     for (int o = kWarps / 2; o > 0; o >>= 1)
 #pragma unroll
@@ -157,13 +176,15 @@ __device__ __forceinline__ void block_store(const double (&vals)[NV], double sca
   }
 }
 
-// Sum over all blocks of slots [slot, slot+NV), unscaled, in a fixed order; valid in warp 0.
-// All of a lane's partial loads of one pass are issued before any is used.
+// Sum over all blocks of slots [slot, slot+NV), unscaled, in a fixed order; valid in warps 0 and
+// 1 (both compute it, so that two threads can share the scalar work).  All of a lane's partial
+// loads of one pass are issued before any is used.
 template <int NV>
 __device__ __forceinline__ void grid_sum(const double* part, int slot, int nb, double inv_scale, double (&out)[NV]) {
 #pragma unroll
   for (int q = 0; q < NV; q++) out[q] = 0.0;
-  if (threadIdx.x >= 32) return;
+  if (threadIdx.x >= 64) return;
+  const int ln = threadIdx.x & 31;
   constexpr int kU = 5;
   DF a[NV];
 #pragma unroll
@@ -172,7 +193,7 @@ __device__ __forceinline__ void grid_sum(const double* part, int slot, int nb, d
     DF v[NV][kU];
 #pragma unroll
     for (int u = 0; u < kU; u++) {
-      const int k = base + u * 32 + (int)threadIdx.x;
+      const int k = base + u * 32 + ln;
 #pragma unroll
       for (int q = 0; q < NV; q++) {
         const float2 x = k < nb ? __ldcg(&((const float2*)part)[(size_t)(slot + q) * nb + k]) : make_float2(0.f, 0.f);
@@ -388,11 +409,12 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   using V = typename V2<T>::t;
   using B = B4<T>;
   using Ref = RowRef;
+  using Acc = typename DotAcc<T>::t;
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double sh[kWarps];
   __shared__ DF s_df[4 * kWarps];
-  __shared__ double s_bc[6];  // beta, alpha_prev, omega_prev, alpha, scale, 1/scale
+  __shared__ double s_bc[8];  // beta, alpha_prev, omega_prev, alpha, scale, 1/scale, rho
   __shared__ int s_ctl;       // 0 continue, 1 stop
   __shared__ int s_epool;     // next free entry of the shared-memory pool
   const int nA = d.ctr->n_active;
@@ -402,7 +424,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   const int r0 = min(nA, (int)blockIdx.x * rpb), r1 = min(nA, r0 + rpb);
   const int kbeg = r0 + (int)threadIdx.x, kstep = blockDim.x;
   const int nlines = LINES ? d.ctr->n_lines : 0;
-  const int nw = LINES ? kWarps : min(kWarps, (r1 - r0 + 31) / 32);  // warps holding values
+  const bool has_line = LINES && (int)blockIdx.x + nb * wib < nlines;
+  const bool busy = __any_sync(0xffffffffu, kbeg < r1) || has_line;  // this warp adds to the dots
   V* const x = (V*)d.kx;
   V* const r = (V*)d.kr;
   V* const rh = (V*)d.krh;
@@ -410,11 +433,13 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   V* const s = (V*)d.ks;
   V* const t = (V*)d.kt;
   V* const z = (V*)d.kz;
-  V* const rt = LINES ? (V*)d.krt : r;    // M = I without lines: r~ = r, z^ = s, t~ = t
+  V* const rt = LINES ? (V*)d.krt : r;  // M = I without lines: r~ = r, z^ = s, t~ = t
   V* const zf = LINES ? (V*)d.kzf : s;
   V* const tt = LINES ? (V*)d.ktt : t;
-  V* const yb[2] = {(V*)d.ky0, (V*)d.ky1};
-  V* const vtb[2] = {(V*)d.kvt0, (V*)d.kvt1};
+  V* const y0 = (V*)d.ky0;
+  V* const y1 = (V*)d.ky1;
+  V* const vt0 = (V*)d.kvt0;
+  V* const vt1 = (V*)d.kvt1;
   const V* b = (const V*)d.rhs;
   const T* blocks = (const T*)d.blocks;
   const int* lflag = d.line_row_flag;
@@ -473,8 +498,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     return {base, base + 1, base + 2, 3};
   };
   if (LINES) {
-    const int l = (int)blockIdx.x + nb * wib;
-    if (l < nlines) {
+    if (has_line) {
+      const int l = (int)blockIdx.x + nb * wib;
       lk0 = __ldg(&d.line_start[l]);
       llen = __ldg(&d.line_len[l]);
       if (wib < kLineSlots) {
@@ -508,21 +533,19 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   // fn(k0, len, factors, refs) over this warp's line blocks (warp-uniform)
   auto lines = [&](auto fn) {
     if constexpr (LINES) {
-      for (int j = wib;; j += kWarps) {
+      if (!has_line) return;
+      fn(lk0, llen, wib < kLineSlots ? sfac() : gfac(lk0), lr_);
+      for (int j = wib + kWarps;; j += kWarps) {
         const int l = (int)blockIdx.x + nb * j;
         if (l >= nlines) break;
-        if (j == wib) {
-          fn(lk0, llen, wib < kLineSlots ? sfac() : gfac(lk0), lr_);
-        } else {
-          const int k0 = __ldg(&d.line_start[l]), len = __ldg(&d.line_len[l]);
-          Ref refs[kLineChunks];
+        const int k0 = __ldg(&d.line_start[l]), len = __ldg(&d.line_len[l]);
+        Ref refs[kLineChunks];
 #pragma unroll
-          for (int c = 0; c < kLineChunks; c++) {
-            refs[c] = {0, 0};
-            if (c * 32 + lane < len) refs[c] = global_ref(k0 + c * 32 + lane);
-          }
-          fn(k0, len, gfac(k0), refs);
+        for (int c = 0; c < kLineChunks; c++) {
+          refs[c] = {0, 0};
+          if (c * 32 + lane < len) refs[c] = global_ref(k0 + c * 32 + lane);
         }
+        fn(k0, len, gfac(k0), refs);
       }
     }
   };
@@ -536,15 +559,15 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     z[k] = o;
     t[k] = o;
     tt[k] = o;
-    yb[0][k] = o;
-    vtb[0][k] = o;
+    y0[k] = o;
+    vt0[k] = o;
     s[k] = bk;
     rh[k] = bk;
     l_bb += (double)bk.x * bk.x + (double)bk.y * bk.y;
     return bk;
   };
   rows([&](int k, const Ref&) { zf[k] = init_row(k); });
-  lines([&](int k0, int len, const LineFac& f, const Ref*) {
+  lines([&](int k0, int len, const LineFac& f, const Ref(&)[kLineChunks]) {
     float2 src[kLineChunks][1];
 #pragma unroll
     for (int c = 0; c < kLineChunks; c++) {
@@ -564,14 +587,17 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   if (threadIdx.x == 0) {
     rho = bb;
     stop2 = rtol * rtol * bb;
-    // exact power of two near 1/bb (biased exponent 2046 - E of bb, clamped to the normal range)
+    // FP64 dots are scaled by an exact power of two near 1/bb (biased exponent 2046 - E of bb,
+    // clamped to the normal range) before they are carried in double-float; FP32 dots need none
     long long e = bb > 0.0 ? ((__double_as_longlong(bb) >> 52) & 0x7ff) : 1023;
     e = e < 1 ? 1 : (e > 2045 ? 2045 : e);
-    s_bc[4] = __longlong_as_double((2046 - e) << 52);
-    s_bc[5] = __longlong_as_double(e << 52);
+    const bool f64 = sizeof(T) == 8;
+    s_bc[4] = f64 ? __longlong_as_double((2046 - e) << 52) : 1.0;
+    s_bc[5] = f64 ? __longlong_as_double(e << 52) : 1.0;
     s_bc[0] = 0.0;  // beta_1
     s_bc[1] = 0.0;  // alpha_0
     s_bc[2] = 0.0;  // omega_0
+    s_bc[6] = bb;   // rho_1
     s_ctl = 0;
   }
   __syncthreads();
@@ -580,33 +606,38 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   for (it = 1;; it++) {
     // ---- phase 1 -------------------------------------------------------------------------
     const T beta = (T)s_bc[0], alp = (T)s_bc[1], omp = (T)s_bc[2], nom = -omp;
-    const V* yo = yb[(it + 1) & 1];
-    V* yn = yb[it & 1];
-    const V* vto = vtb[(it + 1) & 1];
-    V* vtn = vtb[it & 1];
+    const bool odd = it & 1;
+    const V* yo = odd ? y0 : y1;
+    V* yn = odd ? y1 : y0;
+    const V* vto = odd ? vt0 : vt1;
+    V* vtn = odd ? vt1 : vt0;
     // r~_{i-1} and y_i of a row from stored vectors (the owner evaluates the same expressions)
     auto rt_of = [&](int c) { return axpy(nom, ldv(&tt[c]), ldv(&zf[c])); };
     auto y_of = [&](const V& rtc, int c) { return axpy(beta, axpy(nom, ldv(&vto[c]), ldv(&yo[c])), rtc); };
     auto ynb = [&](int c) { return y_of(rt_of(c), c); };
-    double l_rv = 0.0, l_rr = 0.0;
+    Acc l_rv, l_rr;
+    dot_zero(l_rv);
+    dot_zero(l_rr);
     auto p1_row = [&](int k, const Ref& ref) -> V {
       const V xk = ldv(&x[k]), yk = ldv(&yo[k]), zk = ldv(&z[k]), sk = ldv(&s[k]), tk = ldv(&t[k]),
               rhk = ldv(&rh[k]);
       x[k] = mk<T>(xk.x + alp * yk.x + omp * zk.x, xk.y + alp * yk.y + omp * zk.y);
       const V rk = axpy(nom, tk, sk);
       r[k] = rk;
-      l_rr += (double)rk.x * rk.x + (double)rk.y * rk.y;
+      dot_acc(l_rr, rk.x, rk.x);
+      dot_acc(l_rr, rk.y, rk.y);
       const V rtk = rt_of(k);
       if (LINES) rt[k] = rtk;
       const V ynk = y_of(rtk, k);
       yn[k] = ynk;
       const V vv = product(ref, ynk, ynb);
       v[k] = vv;
-      l_rv += (double)rhk.x * vv.x + (double)rhk.y * vv.y;
+      dot_acc(l_rv, rhk.x, vv.x);
+      dot_acc(l_rv, rhk.y, vv.y);
       return vv;
     };
     rows([&](int k, const Ref& ref) { vtn[k] = p1_row(k, ref); });
-    lines([&](int k0, int len, const LineFac& f, const Ref* refs) {
+    lines([&](int k0, int len, const LineFac& f, const Ref(&refs)[kLineChunks]) {
       float2 src[kLineChunks][1];
 #pragma unroll
       for (int c = 0; c < kLineChunks; c++) {
@@ -620,8 +651,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       line_solve<T, 1>(k0, len, f, src, dst);
     });
     {
-      const double vals[2] = {l_rv, l_rr};
-      block_store<2>(vals, dscale, s_df, part, kSlotS1, nb, nw);
+      const DF vals[2] = {dot_df(l_rv, dscale), dot_df(l_rr, dscale)};
+      block_store<2>(vals, busy, s_df, part, kSlotS1, nb);
     }
     grid.sync();
     {
@@ -648,8 +679,13 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     if (s_ctl) break;
     // ---- phase 2 -------------------------------------------------------------------------
     const T nal = -(T)s_bc[3];
+    const double rho_i = s_bc[6], alpha_i = s_bc[3];  // read before thread 0 overwrites rho below
     auto znb = [&](int c) { return axpy(nal, ldv(&vtn[c]), ldv(&rt[c])); };
-    double l_ts = 0.0, l_tt = 0.0, l_rs = 0.0, l_rt = 0.0;
+    Acc l_ts, l_tt, l_rs, l_rt;
+    dot_zero(l_ts);
+    dot_zero(l_tt);
+    dot_zero(l_rs);
+    dot_zero(l_rt);
     V sk_, tk_;
     auto p2_row = [&](int k, const Ref& ref) {
       const V rk = ldv(&r[k]), vk = ldv(&v[k]), rhk = ldv(&rh[k]);
@@ -659,10 +695,14 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       z[k] = zk;
       const V tk = product(ref, zk, znb);
       t[k] = tk;
-      l_ts += (double)tk.x * sk.x + (double)tk.y * sk.y;
-      l_tt += (double)tk.x * tk.x + (double)tk.y * tk.y;
-      l_rs += (double)rhk.x * sk.x + (double)rhk.y * sk.y;
-      l_rt += (double)rhk.x * tk.x + (double)rhk.y * tk.y;
+      dot_acc(l_ts, tk.x, sk.x);
+      dot_acc(l_ts, tk.y, sk.y);
+      dot_acc(l_tt, tk.x, tk.x);
+      dot_acc(l_tt, tk.y, tk.y);
+      dot_acc(l_rs, rhk.x, sk.x);
+      dot_acc(l_rs, rhk.y, sk.y);
+      dot_acc(l_rt, rhk.x, tk.x);
+      dot_acc(l_rt, rhk.y, tk.y);
       sk_ = sk;
       tk_ = tk;
     };
@@ -673,7 +713,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
         tt[k] = tk_;
       }
     });
-    lines([&](int k0, int len, const LineFac& f, const Ref* refs) {
+    lines([&](int k0, int len, const LineFac& f, const Ref(&refs)[kLineChunks]) {
       float2 src[kLineChunks][2];
 #pragma unroll
       for (int c = 0; c < kLineChunks; c++) {
@@ -688,27 +728,30 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       line_solve<T, 2>(k0, len, f, src, dst);
     });
     {
-      const double vals[4] = {l_ts, l_tt, l_rs, l_rt};
-      block_store<4>(vals, dscale, s_df, part, kSlotS2, nb, nw);
+      const DF vals[4] = {dot_df(l_ts, dscale), dot_df(l_tt, dscale), dot_df(l_rs, dscale), dot_df(l_rt, dscale)};
+      block_store<4>(vals, busy, s_df, part, kSlotS2, nb);
     }
     grid.sync();
     {
       double o[4];
       grid_sum<4>(part, kSlotS2, nb, dinv, o);
+      const double ts = o[0], t2 = o[1], rs = o[2], rtv = o[3];
+      // the two divisions run in two warps: thread 0 omega and rho_{i+1}, thread 32 beta_{i+1}
+      //   beta = (rho_{i+1} / rho_i) (alpha / omega) = alpha (rs t2 - ts rt) / (rho_i ts)
       if (threadIdx.x == 0) {
-        const double ts = o[0], t2 = o[1], rs = o[2], rtv = o[3];
         if (!isfinite(ts) || !isfinite(t2) || !isfinite(rs) || !isfinite(rtv)) {
           s_ctl = 1;
           status = 2;
         } else {
           // t = 0 means A z = 0: omega = 0 leaves r = s and restarts the direction (beta = 0)
           const double omega = t2 > 0.0 ? ts / t2 : 0.0;
-          const double rho_new = rs - omega * rtv;
-          s_bc[0] = omega != 0.0 ? (rho_new / rho) * (alpha / omega) : 0.0;
+          rho = fma(-omega, rtv, rs);
           s_bc[1] = alpha;
           s_bc[2] = omega;
-          rho = rho_new;
+          s_bc[6] = rho;
         }
+      } else if (threadIdx.x == 32) {
+        s_bc[0] = (t2 > 0.0 && ts != 0.0) ? alpha_i * fma(rs, t2, -ts * rtv) / (rho_i * ts) : 0.0;
       }
     }
     __syncthreads();

@@ -20,6 +20,13 @@
 namespace lns {
 
 constexpr int kMaxLinesPerRow = 1;
+// Fracture lines are cut into preconditioner blocks of at most this many rows (a multiple of 32:
+// one warp holds a block in registers, 32 rows per chunk).
+#ifndef LNS_LINE_BLOCK_ROWS
+#define LNS_LINE_BLOCK_ROWS 128
+#endif
+constexpr int kLineBlockRows = LNS_LINE_BLOCK_ROWS;
+static_assert(kLineBlockRows % 32 == 0 && kLineBlockRows >= 32, "line blocks are whole 32-row chunks");
 
 struct Fluid {
   double p_ref, c_r, b_o_ref, c_o, b_w_ref, c_w, rho_o_ref, rho_w_ref, mu_o, mu_w, swc, sor;
