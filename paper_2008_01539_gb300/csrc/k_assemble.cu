@@ -248,7 +248,6 @@ __global__ void k_line_mark(Dev d) {
     if (next && !cont) {
       int pos = atomicAdd(&d.ctr->n_line_starts, 1);
       d.line_start[pos] = k;
-      atomicAdd(&d.ctr->n_lines, 1);
     }
   }
 }
@@ -266,7 +265,7 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int nl = d.ctr->n_line_starts;  // the factor pass appends cut blocks after these
+  const int nl = d.ctr->n_line_starts;
   const int nA = d.ctr->n_active;
   const T* blocks = (const T*)d.blocks;
   float* ldinv = (float*)d.line_dinv;
@@ -358,15 +357,15 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
       __syncwarp();
     }
     // lines longer than kMaxLineRows are cut into blocks of kMaxLineRows rows (the couplings at the
-    // cuts were left out of the factors above); the extra blocks are appended to the line list
-    if (lane == 0) {
-      d.line_len[l] = min(len, kMaxLineRows);
-      for (int q = kMaxLineRows; q < len; q += kMaxLineRows) {
-        const int pos = atomicAdd(&d.ctr->n_lines, 1);
-        d.line_start[pos] = k0 + q;
-        d.line_len[pos] = min(kMaxLineRows, len - q);
+    // cuts were left out of the factors above); each block start is marked in lblk with its length
+    // at line_len[start], and the ascending list of block starts is compacted afterwards, so that
+    // the blocks are numbered the same way in every run
+    if (lane == 0)
+      for (int q = 0; q < len; q += kMaxLineRows) {
+        const int k = k0 + q;
+        atomicOr(&d.lblk[k >> 5], 1u << (k & 31));
+        d.line_len[k] = min(kMaxLineRows, len - q);
       }
-    }
   }
 }
 
@@ -389,6 +388,7 @@ cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, i
 
 cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c) {
   cudaError_t e = cudaMemsetAsync(&d.ctr->n_lines, 0, 2 * sizeof(int), c.stream);  // n_lines, n_line_starts
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.lblk, 0, sizeof(uint32_t) * (size_t)d.W, c.stream);
   if (e != cudaSuccess) return e;
   count_launches(1);
   k_line_mark<<<4 * c.sms, 256, 0, c.stream>>>(d);
@@ -397,7 +397,10 @@ cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c) {
     k_line_factor<float><<<c.sms, 32 * kLineWarps, 0, c.stream>>>(d);
   else
     k_line_factor<double><<<c.sms, 32 * kLineWarps, 0, c.stream>>>(d);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // ascending line-block starts (compact rows < n_active <= n, so the n-bit bitset covers them)
+  return launch_compact(d, d.lblk, d.line_start, d.lscratch, &d.ctr->n_lines, c);
 }
 
 }  // namespace lns

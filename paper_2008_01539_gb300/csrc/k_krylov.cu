@@ -33,6 +33,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lns_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -44,9 +46,6 @@ namespace {
 constexpr int kKryBlk = 256;
 constexpr int kWarps = kKryBlk / 32;
 constexpr int kRowsCached = 4;   // non-line rows per thread whose matrix row is staged
-constexpr int kLineChunks = kLineBlockRows / 32;  // 32-row chunks of a line block
-constexpr int kLineSlots = 4;    // line blocks per block whose factors are staged in shared memory
-constexpr size_t kLineSmem = (size_t)kLineSlots * kLineChunks * 32 * 3 * sizeof(float4);
 constexpr size_t kKrySmem = 200 * 1024;
 constexpr int kSlotS1 = 0, kSlotS2 = 2, kSlotInit = 6;  // partial-sum slots (nb entries each)
 
@@ -90,6 +89,11 @@ __device__ __forceinline__ V axpy(T a, V w, V u) {
   return o;
 }
 
+template <typename V>
+struct V2pair {
+  V a, b;
+};
+
 template <typename T>
 struct M2 {
   T a, b, c, d;
@@ -123,6 +127,55 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
 }
 
+// Scalar arithmetic of the recurrence in double-float (FP32 instructions only; about 44
+// significant bits, ample for the BiCGStab coefficients).
+__device__ __forceinline__ DF df_fast(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  return df_fast(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const DF r = df_add(a, df_neg(df_mul(DF{q1, 0.f}, b)));
+  return df_fast(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ bool df_le(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+__device__ __forceinline__ bool df_finite(DF a) { return isfinite(a.hi) && isfinite(a.lo); }
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+// Recurrence scalars: FP64 for FP64 vectors, double-float for FP32 vectors.
+__device__ __forceinline__ double sc_from(DF a, double) { return df_to_double(a); }
+__device__ __forceinline__ DF sc_from(DF a, DF) { return a; }
+__device__ __forceinline__ double sc_div(double a, double b) { return a / b; }
+__device__ __forceinline__ DF sc_div(DF a, DF b) { return df_div(a, b); }
+__device__ __forceinline__ double sc_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ DF sc_mul(DF a, DF b) { return df_mul(a, b); }
+__device__ __forceinline__ double sc_fnma(double a, double b, double c) { return fma(-a, b, c); }  // c - a b
+__device__ __forceinline__ DF sc_fnma(DF a, DF b, DF c) { return df_add(c, df_neg(df_mul(a, b))); }
+__device__ __forceinline__ bool sc_le(double a, double b) { return a <= b; }
+__device__ __forceinline__ bool sc_le(DF a, DF b) { return df_le(a, b); }
+__device__ __forceinline__ bool sc_ok(double a) { return a != 0.0 && isfinite(a); }  // usable divisor
+__device__ __forceinline__ bool sc_ok(DF a) { return a.hi != 0.f && df_finite(a); }
+__device__ __forceinline__ bool sc_finite(double a) { return isfinite(a); }
+__device__ __forceinline__ bool sc_finite(DF a) { return df_finite(a); }
+__device__ __forceinline__ bool sc_pos(double a) { return a > 0.0; }
+__device__ __forceinline__ bool sc_pos(DF a) { return a.hi > 0.f; }
+__device__ __forceinline__ bool sc_nonzero(double a) { return a != 0.0; }
+__device__ __forceinline__ bool sc_nonzero(DF a) { return a.hi != 0.f; }
+__device__ __forceinline__ void sc_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void sc_zero(DF& a) { a = DF{0.f, 0.f}; }
+__device__ __forceinline__ double sc_double(double a) { return a; }
+__device__ __forceinline__ double sc_double(DF a) { return df_to_double(a); }
+template <typename T>
+__device__ __forceinline__ T sc_t(double a) { return (T)a; }
+template <typename T>
+__device__ __forceinline__ T sc_t(DF a) { return (T)a.hi; }
+
 // Dot products of one thread's rows.  FP64 vectors: fused FP64 products, converted to double-float
 // (after scaling) once per phase.  FP32 vectors: exact FP32 products (p + e, e = fma(a, b, -p))
 // summed in double-float, so the FP32 path issues no FP64 instruction per row.
@@ -142,7 +195,7 @@ __device__ __forceinline__ void dot_acc(DF& acc, float a, float b) {
   acc = df_add(acc, DF{p, fmaf(a, b, -p)});
 }
 __device__ __forceinline__ DF dot_df(double acc, double scale) { return df_from(acc * scale); }
-__device__ __forceinline__ DF dot_df(DF acc, double) { return acc; }
+__device__ __forceinline__ DF dot_df(DF acc, float scale) { return {acc.hi * scale, acc.lo * scale}; }
 
 // Block partials of NV values into slots [slot, slot+NV) as (hi, lo) pairs.  Warps with nothing
 // to add (busy == false) contribute zeros without converting.  Contains one block barrier.
@@ -176,19 +229,16 @@ __device__ __forceinline__ void block_store(const DF (&vals)[NV], bool busy, DF*
   }
 }
 
-// Sum over all blocks of slots [slot, slot+NV), unscaled, in a fixed order; valid in warps 0 and
-// 1 (both compute it, so that two threads can share the scalar work).  All of a lane's partial
+// Sum over all blocks of slots [slot, slot+NV) in a fixed order, in double-float; valid in warps 0
+// and 1 (both compute it, so that two threads can share the scalar work).  All of a lane's partial
 // loads of one pass are issued before any is used.
 template <int NV>
-__device__ __forceinline__ void grid_sum(const double* part, int slot, int nb, double inv_scale, double (&out)[NV]) {
+__device__ __forceinline__ void grid_sum(const double* part, int slot, int nb, DF (&out)[NV]) {
 #pragma unroll
-  for (int q = 0; q < NV; q++) out[q] = 0.0;
+  for (int q = 0; q < NV; q++) out[q] = {0.f, 0.f};
   if (threadIdx.x >= 64) return;
   const int ln = threadIdx.x & 31;
   constexpr int kU = 5;
-  DF a[NV];
-#pragma unroll
-  for (int q = 0; q < NV; q++) a[q] = {0.f, 0.f};
   for (int base = 0; base < nb; base += 32 * kU) {
     DF v[NV][kU];
 #pragma unroll
@@ -207,14 +257,12 @@ __device__ __forceinline__ void grid_sum(const double* part, int slot, int nb, d
 #pragma unroll
         for (int q = 0; q < NV; q++) v[q][u] = df_add(v[q][u], v[q][u + h]);
 #pragma unroll
-    for (int q = 0; q < NV; q++) a[q] = df_add(a[q], v[q][0]);
+    for (int q = 0; q < NV; q++) out[q] = df_add(out[q], v[q][0]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int q = 0; q < NV; q++) a[q] = df_add(a[q], df_shfl_xor(a[q], o));
-#pragma unroll
-  for (int q = 0; q < NV; q++) out[q] = ((double)a[q].hi + (double)a[q].lo) * inv_scale;
+    for (int q = 0; q < NV; q++) out[q] = df_add(out[q], df_shfl_xor(out[q], o));
 }
 
 // ||b||^2 (once per solve, before the scale is known): FP64 block partial and grid sum.
@@ -240,31 +288,34 @@ __device__ __forceinline__ double grid_sum_f64(const double* part, int nb) {
 }
 
 // ---- product of one row ------------------------------------------------------------------
-// own + sum over the row's active columns j of B_kj nbv(j); `nbv` forms the neighbour's value
-// from vectors written before the last barrier.  Two entries are gathered at a time and summed in
-// separate accumulators (a shorter dependent FP64 chain).
-template <typename T, typename NbF>
+// own + sum over the row's active columns j of B_kj x_j, where x_j = comb(load(j)) is formed from
+// vectors written before the last barrier.  The loads of up to kBatch neighbours are issued before
+// any is used, so a row of degree <= kBatch costs one L2 round trip (4 neighbours at a time in
+// FP32; 2 in FP64, whose gathered values take twice the registers).
+template <typename T, typename LoadF, typename CombF>
 __device__ __forceinline__ typename V2<T>::t row_product(const int* col, const B4<T>* blk, int deg,
-                                                         typename V2<T>::t own, NbF nbv) {
+                                                         typename V2<T>::t own, LoadF load, CombF comb) {
   using V = typename V2<T>::t;
+  using Raw = decltype(load(0));
+  constexpr int kBatch = sizeof(T) == 8 ? 2 : 4;
   V acc0 = own, acc1 = mk<T>(0, 0);
-  for (int j = 0; j < deg; j += 2) {
-    const int c0 = col[j];
-    const int c1 = j + 1 < deg ? col[j + 1] : -1;
-    V x0 = mk<T>(0, 0), x1 = mk<T>(0, 0);
-    B4<T> b0 = {0, 0, 0, 0}, b1 = {0, 0, 0, 0};
-    if (c0 >= 0) {
-      x0 = nbv(c0);
-      b0 = blk[j];
-    }
-    if (c1 >= 0) {
-      x1 = nbv(c1);
-      b1 = blk[j + 1];
-    }
-    acc0.x += b0.a * x0.x + b0.b * x0.y;
-    acc0.y += b0.c * x0.x + b0.d * x0.y;
-    acc1.x += b1.a * x1.x + b1.b * x1.y;
-    acc1.y += b1.c * x1.x + b1.d * x1.y;
+  for (int j = 0; j < deg; j += kBatch) {
+    int c[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; q++) c[q] = j + q < deg ? col[j + q] : -1;
+    Raw raw[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; q++)
+      if (c[q] >= 0) raw[q] = load(c[q]);
+#pragma unroll
+    for (int q = 0; q < kBatch; q++)
+      if (c[q] >= 0) {
+        const V xv = comb(raw[q]);
+        const B4<T> bq = blk[j + q];
+        V& acc = (q & 1) ? acc1 : acc0;
+        acc.x += bq.a * xv.x + bq.b * xv.y;
+        acc.y += bq.c * xv.x + bq.d * xv.y;
+      }
   }
   return mk<T>(acc0.x + acc1.x, acc0.y + acc1.y);
 }
@@ -336,73 +387,125 @@ struct LineFac {
   int fs;
 };
 
-// M^{-1} on one line block (len <= 128 rows) for NR right-hand sides held in registers
-// (src[c][q] = input q of row k0 + 32c + lane); results stored to dst[q][k0 + t].
+// M^{-1} on one line block (len <= kLineBlockRows rows) for NR right-hand sides.  Input q of row
+// k0 + t is buf[q * bstride + t] (overwritten by the forward sweep); results are stored to
+// dst[q][k0 + t].  Chunks of 32 rows are swept one after
+// another with the carry passed between them; each lane touches only its own buffer entries.
 template <typename T, int NR>
-__device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, const float2 (&src)[kLineChunks][NR],
+__device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, float2* buf, int bstride,
                                            typename V2<T>::t* const (&dst)[NR]) {
   const int lane = threadIdx.x & 31;
-  float2 w[kLineChunks][NR];
   float2 carry[NR];
 #pragma unroll
   for (int q = 0; q < NR; q++) carry[q] = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int c0 = 0; c0 < len; c0 += 32) {
+    const int t = c0 + lane;
+    M2<float> A = {0.f, 0.f, 0.f, 0.f};
+    float2 w[NR];
 #pragma unroll
-  for (int c = 0; c < kLineChunks; c++) {
-#pragma unroll
-    for (int q = 0; q < NR; q++) w[c][q] = make_float2(0.f, 0.f);
-    if (c * 32 < len) {
-      const int t = c * 32 + lane;
-      M2<float> A = {0.f, 0.f, 0.f, 0.f};
-      if (t < len) {
-        const float4 Di = f.fd[(size_t)t * f.fs];
-#pragma unroll
-        for (int q = 0; q < NR; q++)
-          w[c][q] = make_float2(Di.x * src[c][q].x + Di.y * src[c][q].y, Di.z * src[c][q].x + Di.w * src[c][q].y);
-        const float4 a4 = f.fa[(size_t)t * f.fs];
-        A = {a4.x, a4.y, a4.z, a4.w};
-      }
-      scan_fwd<NR>(w[c], A, carry, lane);
-      const int last = min(31, len - 1 - c * 32);
+    for (int q = 0; q < NR; q++) w[q] = make_float2(0.f, 0.f);
+    if (t < len) {
+      const float4 Di = f.fd[(size_t)t * f.fs];
 #pragma unroll
       for (int q = 0; q < NR; q++) {
-        carry[q].x = __shfl_sync(0xffffffffu, w[c][q].x, last);
-        carry[q].y = __shfl_sync(0xffffffffu, w[c][q].y, last);
+        const float2 u = buf[q * bstride + t];
+        w[q] = make_float2(Di.x * u.x + Di.y * u.y, Di.z * u.x + Di.w * u.y);
       }
+      const float4 a4 = f.fa[(size_t)t * f.fs];
+      A = {a4.x, a4.y, a4.z, a4.w};
+    }
+    scan_fwd<NR>(w, A, carry, lane);
+    const int last = min(31, len - 1 - c0);
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+      if (t < len) buf[q * bstride + t] = w[q];
+      carry[q].x = __shfl_sync(0xffffffffu, w[q].x, last);
+      carry[q].y = __shfl_sync(0xffffffffu, w[q].y, last);
     }
   }
+  __syncwarp();
 #pragma unroll
   for (int q = 0; q < NR; q++) carry[q] = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int c0 = ((len - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
+    const int t = c0 + lane;
+    M2<float> B = {0.f, 0.f, 0.f, 0.f};
+    float2 z[NR];
 #pragma unroll
-  for (int c = kLineChunks - 1; c >= 0; c--) {
-    if (c * 32 < len) {
-      const int t = c * 32 + lane;
-      M2<float> B = {0.f, 0.f, 0.f, 0.f};
-      float2 z[NR];
+    for (int q = 0; q < NR; q++) z[q] = make_float2(0.f, 0.f);
+    if (t < len) {
+      const float4 g4 = f.fg[(size_t)t * f.fs];
+      B = {-g4.x, -g4.y, -g4.z, -g4.w};
 #pragma unroll
-      for (int q = 0; q < NR; q++) z[q] = make_float2(0.f, 0.f);
-      if (t < len) {
-        const float4 g4 = f.fg[(size_t)t * f.fs];
-        B = {-g4.x, -g4.y, -g4.z, -g4.w};
+      for (int q = 0; q < NR; q++) z[q] = buf[q * bstride + t];
+    }
+    scan_bwd<NR>(z, B, carry, lane);
 #pragma unroll
-        for (int q = 0; q < NR; q++) z[q] = w[c][q];
-      }
-      scan_bwd<NR>(z, B, carry, lane);
-#pragma unroll
-      for (int q = 0; q < NR; q++) {
-        if (t < len) dst[q][k0 + t] = mk<T>((T)z[q].x, (T)z[q].y);
-        carry[q].x = __shfl_sync(0xffffffffu, z[q].x, 0);
-        carry[q].y = __shfl_sync(0xffffffffu, z[q].y, 0);
-      }
+    for (int q = 0; q < NR; q++) {
+      if (t < len) dst[q][k0 + t] = mk<T>((T)z[q].x, (T)z[q].y);
+      carry[q].x = __shfl_sync(0xffffffffu, z[q].x, 0);
+      carry[q].y = __shfl_sync(0xffffffffu, z[q].y, 0);
     }
   }
 }
 
 // ---- the solver --------------------------------------------------------------------------
 // A matrix row: off >= 0 is its first entry in the shared-memory pool, off < 0 encodes its first
-// CSR entry e0 as -(e0 + 1) (global memory); deg entries.
+// CSR entry e0 as -(e0 + 1) (global memory); deg entries; line: a fracture-line row.
 struct RowRef {
-  int off, deg;
+  int off, deg, line;
 };
+
+// Rows are split into one contiguous chunk per block, whose ends are moved forward so that no
+// fracture-line block straddles two chunks: a block solves its own line blocks after a block
+// barrier, from inputs its threads left in a block buffer.  Dynamic shared memory of a block:
+// the references of its first kRowsCached rows per thread, the line input buffer (two float2
+// per row), the line factors of its first kFacRows rows, the line-block table, and the pool of
+// staged matrix rows (columns and blocks).
+constexpr int kBufRows = 2048;   // chunk rows whose line inputs fit the shared buffer
+constexpr int kFacRows = 512;    // chunk rows whose line factors are staged
+constexpr int kLineCache = 64;   // line blocks of a chunk whose (start, length) are staged
+constexpr size_t kSmRref = (size_t)kRowsCached * kKryBlk * sizeof(RowRef);
+constexpr size_t kSmBuf = (size_t)2 * kBufRows * sizeof(float2);
+constexpr size_t kSmFac = (size_t)kFacRows * 3 * sizeof(float4);
+constexpr size_t kSmLines = (size_t)kLineCache * sizeof(int2);
+constexpr size_t kSmPool = kKrySmem - kSmRref - kSmBuf - kSmFac - kSmLines;
+
+// First row >= k that does not continue a line block (the end of a chunk starting or ending at
+// k), found 32 rows at a time by one warp; valid in all lanes.
+__device__ __forceinline__ int chunk_edge(const Dev& d, int k, int nA) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    const int q = k + lane;
+    bool inside = false;
+    if (q < nA) inside = __ldg(&d.line_row_flag[q]) == 2 && !((__ldg(&d.lblk[q >> 5]) >> (q & 31)) & 1u);
+    const unsigned m = __ballot_sync(0xffffffffu, !inside);
+    if (m) return min(nA, k + __ffs(m) - 1);
+    k += 32;
+  }
+}
+
+// First index l with line_start[l] >= k (line_start ascending, n entries), by one warp in steps
+// that narrow the range 32-fold; valid in all lanes.
+__device__ __forceinline__ int line_lower_bound(const int* ls, int n, int k) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) / 32;
+    const int q = lo + lane * step;
+    // samples at or beyond hi count as ">= k" (the answer is at most hi)
+    const bool ge = q >= hi || __ldg(&ls[q]) >= k;
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    const int f = m ? __ffs(m) - 1 : 32;  // first sample with ls >= k
+    const int nhi = f < 32 ? min(hi, lo + f * step) : hi;
+    if (f > 0) lo += (f - 1) * step;      // sample f-1 has ls < k
+    hi = nhi;
+  }
+  const int q = lo + lane;
+  const unsigned m = __ballot_sync(0xffffffffu, q < hi && __ldg(&ls[q]) >= k);
+  return m ? lo + __ffs(m) - 1 : hi;
+}
 
 template <typename T, bool LINES>
 __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int maxit) {
@@ -410,22 +513,20 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   using B = B4<T>;
   using Ref = RowRef;
   using Acc = typename DotAcc<T>::t;
+  constexpr bool kF64 = sizeof(T) == 8;
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double sh[kWarps];
   __shared__ DF s_df[4 * kWarps];
-  __shared__ double s_bc[8];  // beta, alpha_prev, omega_prev, alpha, scale, 1/scale, rho
+  using S = std::conditional_t<kF64, double, DF>;  // recurrence scalars
+  __shared__ S s_sc[4];       // beta, alpha_prev, omega_prev, alpha
   __shared__ int s_ctl;       // 0 continue, 1 stop
   __shared__ int s_epool;     // next free entry of the shared-memory pool
+  __shared__ int s_rng[4];    // chunk start, chunk end, first line block, line-block count
   const int nA = d.ctr->n_active;
   const int nb = gridDim.x;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int rpb = (nA + nb - 1) / nb;
-  const int r0 = min(nA, (int)blockIdx.x * rpb), r1 = min(nA, r0 + rpb);
-  const int kbeg = r0 + (int)threadIdx.x, kstep = blockDim.x;
   const int nlines = LINES ? d.ctr->n_lines : 0;
-  const bool has_line = LINES && (int)blockIdx.x + nb * wib < nlines;
-  const bool busy = __any_sync(0xffffffffu, kbeg < r1) || has_line;  // this warp adds to the dots
   V* const x = (V*)d.kx;
   V* const r = (V*)d.kr;
   V* const rh = (V*)d.krh;
@@ -442,19 +543,49 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   V* const vt1 = (V*)d.kvt1;
   const V* b = (const V*)d.rhs;
   const T* blocks = (const T*)d.blocks;
-  const int* lflag = d.line_row_flag;
   double* part = d.partials;
-  float4* s_fac = (float4*)dsm;
-  const int ecap = (int)((kKrySmem - kLineSmem) / (sizeof(int) + sizeof(B)));
-  B* s_blk = (B*)(dsm + kLineSmem);
-  int* s_col = (int*)(dsm + kLineSmem + (size_t)ecap * sizeof(B));
-  if (threadIdx.x == 0) s_epool = 0;
+  Ref* s_rref = (Ref*)dsm;
+  float2* s_buf = (float2*)(dsm + kSmRref);
+  float4* s_fac = (float4*)(dsm + kSmRref + kSmBuf);
+  int2* s_lines = (int2*)(dsm + kSmRref + kSmBuf + kSmFac);
+  const int ecap = (int)(kSmPool / (sizeof(int) + sizeof(B)));
+  B* s_blk = (B*)(dsm + kKrySmem - kSmPool);
+  int* s_col = (int*)(dsm + kKrySmem - kSmPool + (size_t)ecap * sizeof(B));
+
+  // ---- this block's rows and line blocks ------------------------------------------------
+  if (wib == 0) {
+    const int rpb = (nA + nb - 1) / nb;
+    int c0 = min(nA, (int)blockIdx.x * rpb), c1 = min(nA, c0 + rpb);
+    if (LINES) {
+      c0 = chunk_edge(d, c0, nA);
+      c1 = chunk_edge(d, c1, nA);
+    }
+    int l0 = 0, l1 = 0;
+    if (LINES && nlines > 0) {
+      l0 = line_lower_bound(d.line_start, nlines, c0);
+      l1 = line_lower_bound(d.line_start, nlines, c1);
+    }
+    if (lane == 0) {
+      s_rng[0] = c0;
+      s_rng[1] = max(c0, c1);
+      s_rng[2] = l0;
+      s_rng[3] = max(0, l1 - l0);
+      s_epool = 0;
+    }
+  }
   __syncthreads();
+  const int r0 = s_rng[0], r1 = s_rng[1], l0 = s_rng[2], nlb = s_rng[3];
+  const int kbeg = r0 + (int)threadIdx.x, kstep = blockDim.x;
+  const bool busy = __any_sync(0xffffffffu, kbeg < r1) || (LINES && wib < nlb);  // adds to the dots
+  // line inputs: the shared buffer, or (a chunk too long for it) global scratch, two float2 per row
+  const bool buf_sm = r1 - r0 <= kBufRows;
+  float2* const lbuf = buf_sm ? s_buf : (float2*)d.kls + 2 * (size_t)r0;
+  const int bstride = buf_sm ? kBufRows : r1 - r0;
 
   auto global_ref = [&](int k) -> Ref {
     const int i = __ldg(&d.act[k]);
     const int e0 = __ldg(&d.row_ptr[i]);
-    return {-(e0 + 1), __ldg(&d.row_ptr[i + 1]) - e0};
+    return {-(e0 + 1), __ldg(&d.row_ptr[i + 1]) - e0, LINES ? __ldg(&d.line_row_flag[k]) : 0};
   };
   // stage a row's columns and blocks in the shared pool (placement does not affect the result)
   auto stage = [&](int k) -> Ref {
@@ -466,93 +597,66 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       s_col[off + j] = __ldg(&d.colA[e0 + j]);
       s_blk[off + j] = *(const B*)&blocks[4 * (size_t)(e0 + j)];
     }
-    return {off, g.deg};
+    return {off, g.deg, g.line};
   };
-  // product of a row with a vector whose own value is `own` and whose neighbour values come from nbv
-  auto product = [&](const Ref& ref, const V& own, auto nbv) -> V {
-    if (ref.off >= 0) return row_product<T>(s_col + ref.off, s_blk + ref.off, ref.deg, own, nbv);
+  // product of a row with a vector whose own value is `own` and whose neighbour values are
+  // comb(load(j))
+  auto product = [&](const Ref& ref, const V& own, auto load, auto comb) -> V {
+    if (ref.off >= 0) return row_product<T>(s_col + ref.off, s_blk + ref.off, ref.deg, own, load, comb);
     const size_t e0 = (size_t)(-(ref.off + 1));
-    return row_product<T>(d.colA + e0, (const B*)&blocks[4 * e0], ref.deg, own, nbv);
+    return row_product<T>(d.colA + e0, (const B*)&blocks[4 * e0], ref.deg, own, load, comb);
   };
-  // this thread's first non-line rows
-  Ref rr_[kRowsCached];
-  int rk_[kRowsCached];
-#pragma unroll
   for (int q = 0; q < kRowsCached; q++) {
     const int k = kbeg + q * kstep;
-    rk_[q] = -1;
-    rr_[q] = {0, 0};
-    if (k < r1 && !(LINES && __ldg(&lflag[k]))) {
-      rk_[q] = k;
-      rr_[q] = stage(k);
-    }
+    if (k < r1) s_rref[q * kKryBlk + threadIdx.x] = stage(k);
   }
-  // this warp's first line block (l = blockIdx + nb * wib): rows staged, factors staged if a slot is free
-  Ref lr_[kLineChunks];
-  int lk0 = 0, llen = 0;
-  auto gfac = [&](int k0) -> LineFac {
-    return {(const float4*)d.line_dinv + k0, (const float4*)d.line_a + k0, (const float4*)d.line_g + k0, 1};
-  };
-  auto sfac = [&]() -> LineFac {
-    const float4* base = &s_fac[(size_t)wib * kLineChunks * 32 * 3];
-    return {base, base + 1, base + 2, 3};
-  };
   if (LINES) {
-    if (has_line) {
-      const int l = (int)blockIdx.x + nb * wib;
-      lk0 = __ldg(&d.line_start[l]);
-      llen = __ldg(&d.line_len[l]);
-      if (wib < kLineSlots) {
-        const LineFac g = gfac(lk0);
-        float4* base = &s_fac[(size_t)wib * kLineChunks * 32 * 3];
-        for (int q = lane; q < llen; q += 32) {
-          base[3 * q] = g.fd[q];
-          base[3 * q + 1] = g.fa[q];
-          base[3 * q + 2] = g.fg[q];
-        }
+    for (int k = kbeg; k < min(r1, r0 + kFacRows); k += kstep)
+      if (__ldg(&d.line_row_flag[k])) {
+        float4* f = &s_fac[3 * (size_t)(k - r0)];
+        f[0] = __ldg((const float4*)d.line_dinv + k);
+        f[1] = __ldg((const float4*)d.line_a + k);
+        f[2] = __ldg((const float4*)d.line_g + k);
       }
-    }
-#pragma unroll
-    for (int c = 0; c < kLineChunks; c++) {
-      lr_[c] = {0, 0};
-      if (c * 32 + lane < llen) lr_[c] = stage(lk0 + c * 32 + lane);
+    for (int j = threadIdx.x; j < min(nlb, kLineCache); j += kstep) {
+      const int k0 = __ldg(&d.line_start[l0 + j]);
+      s_lines[j] = make_int2(k0, __ldg(&d.line_len[k0]));
     }
   }
   __syncthreads();
 
-  // fn(k, ref) over this thread's non-line rows
+  // fn(k, ref) over this thread's rows of the chunk (one call site: one copy of the row code)
   auto rows = [&](auto fn) {
-#pragma unroll
-    for (int q = 0; q < kRowsCached; q++)
-      if (rk_[q] >= 0) fn(rk_[q], rr_[q]);
-    for (int k = kbeg + kRowsCached * kstep; k < r1; k += kstep) {
-      if (LINES && __ldg(&lflag[k])) continue;
-      fn(k, global_ref(k));
-    }
+#pragma unroll 1
+    for (int k = kbeg, q = 0; k < r1; k += kstep, q++) fn(k, q < kRowsCached ? s_rref[q * kKryBlk + threadIdx.x] : global_ref(k));
   };
-  // fn(k0, len, factors, refs) over this warp's line blocks (warp-uniform)
-  auto lines = [&](auto fn) {
+  // after a block barrier: M^{-1} on this block's line blocks, one warp per line block
+  auto lines = [&](auto solvefn) {
     if constexpr (LINES) {
-      if (!has_line) return;
-      fn(lk0, llen, wib < kLineSlots ? sfac() : gfac(lk0), lr_);
-      for (int j = wib + kWarps;; j += kWarps) {
-        const int l = (int)blockIdx.x + nb * j;
-        if (l >= nlines) break;
-        const int k0 = __ldg(&d.line_start[l]), len = __ldg(&d.line_len[l]);
-        Ref refs[kLineChunks];
-#pragma unroll
-        for (int c = 0; c < kLineChunks; c++) {
-          refs[c] = {0, 0};
-          if (c * 32 + lane < len) refs[c] = global_ref(k0 + c * 32 + lane);
+      __syncthreads();
+#pragma unroll 1
+      for (int j = wib; j < nlb; j += kWarps) {
+        int2 kl;
+        if (j < kLineCache) {
+          kl = s_lines[j];
+        } else {
+          kl.x = __ldg(&d.line_start[l0 + j]);
+          kl.y = __ldg(&d.line_len[kl.x]);
         }
-        fn(k0, len, gfac(k0), refs);
+        const int o = kl.x - r0;
+        const float4* fb = &s_fac[3 * (size_t)o];
+        const LineFac f = o + kl.y <= kFacRows
+                              ? LineFac{fb, fb + 1, fb + 2, 3}
+                              : LineFac{(const float4*)d.line_dinv + kl.x, (const float4*)d.line_a + kl.x,
+                                        (const float4*)d.line_g + kl.x, 1};
+        solvefn(kl.x, kl.y, f, lbuf + o);
       }
     }
   };
 
   // ---- initialisation: x = z = t = t~ = y_0 = v~_0 = 0, s = r^ = b, z^ = M^{-1} b -------------
   double l_bb = 0.0;
-  auto init_row = [&](int k) -> V {
+  rows([&](int k, const Ref& ref) {
     const V bk = b[k];
     const V o = mk<T>(0, 0);
     x[k] = o;
@@ -564,137 +668,147 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     s[k] = bk;
     rh[k] = bk;
     l_bb += (double)bk.x * bk.x + (double)bk.y * bk.y;
-    return bk;
-  };
-  rows([&](int k, const Ref&) { zf[k] = init_row(k); });
-  lines([&](int k0, int len, const LineFac& f, const Ref(&)[kLineChunks]) {
-    float2 src[kLineChunks][1];
-#pragma unroll
-    for (int c = 0; c < kLineChunks; c++) {
-      src[c][0] = make_float2(0.f, 0.f);
-      if (c * 32 + lane < len) {
-        const V bk = init_row(k0 + c * 32 + lane);
-        src[c][0] = make_float2((float)bk.x, (float)bk.y);
-      }
-    }
+    if (LINES && ref.line)
+      lbuf[k - r0] = make_float2((float)bk.x, (float)bk.y);
+    else
+      zf[k] = bk;
+  });
+  lines([&](int k0, int len, const LineFac& f, float2* buf) {
     V* const dst[1] = {zf};
-    line_solve<T, 1>(k0, len, f, src, dst);
+    line_solve<T, 1>(k0, len, f, buf, bstride, dst);
   });
   block_store_f64(l_bb, sh, part, nb);
   grid.sync();
   const double bb = grid_sum_f64(part, nb);
-  double rho = 0.0, alpha = 0.0, stop2 = 0.0, rr_last = 0.0;
-  if (threadIdx.x == 0) {
-    rho = bb;
-    stop2 = rtol * rtol * bb;
-    // FP64 dots are scaled by an exact power of two near 1/bb (biased exponent 2046 - E of bb,
-    // clamped to the normal range) before they are carried in double-float; FP32 dots need none
-    long long e = bb > 0.0 ? ((__double_as_longlong(bb) >> 52) & 0x7ff) : 1023;
-    e = e < 1 ? 1 : (e > 2045 ? 2045 : e);
-    const bool f64 = sizeof(T) == 8;
-    s_bc[4] = f64 ? __longlong_as_double((2046 - e) << 52) : 1.0;
-    s_bc[5] = f64 ? __longlong_as_double(e << 52) : 1.0;
-    s_bc[0] = 0.0;  // beta_1
-    s_bc[1] = 0.0;  // alpha_0
-    s_bc[2] = 0.0;  // omega_0
-    s_bc[6] = bb;   // rho_1
+  // Dots are scaled by an exact power of two near 1/bb before they are carried in double-float,
+  // so that the reductions and the scalar arithmetic stay far from the FP32 range limits (the
+  // scalars are ratios of dots and do not depend on the scale).  2^(1023 - E) with E the unbiased
+  // exponent of bb, clamped to what FP32 represents exactly.
+  long long eb = bb > 0.0 ? ((__double_as_longlong(bb) >> 52) & 0x7ff) - 1023 : 0;
+  eb = eb < -126 ? -126 : (eb > 126 ? 126 : eb);
+  const double dscale = __longlong_as_double((1023 - eb) << 52);
+  const float fscale = (float)dscale;
+  auto to_df = [&](const Acc& a) -> DF {
+    if constexpr (kF64)
+      return dot_df(a, dscale);
+    else
+      return dot_df(a, fscale);
+  };
+  S rho, alpha, stop2, rr_last;
+  sc_zero(rho);
+  sc_zero(alpha);
+  sc_zero(stop2);
+  sc_zero(rr_last);
+  if (threadIdx.x == 0) {  // thread 0 tracks the scalars
+    rho = sc_from(df_from(bb * dscale), S{});
+    stop2 = sc_from(df_from(rtol * rtol * bb * dscale), S{});
+    sc_zero(s_sc[0]);  // beta_1
+    sc_zero(s_sc[1]);  // alpha_0
+    sc_zero(s_sc[2]);  // omega_0
     s_ctl = 0;
   }
   __syncthreads();
-  const double dscale = s_bc[4], dinv = s_bc[5];
   int status = 1, it;
   for (it = 1;; it++) {
     // ---- phase 1 -------------------------------------------------------------------------
-    const T beta = (T)s_bc[0], alp = (T)s_bc[1], omp = (T)s_bc[2], nom = -omp;
+    const T beta = sc_t<T>(s_sc[0]), alp = sc_t<T>(s_sc[1]), omp = sc_t<T>(s_sc[2]);
+    const T nom = -omp;
     const bool odd = it & 1;
     const V* yo = odd ? y0 : y1;
     V* yn = odd ? y1 : y0;
     const V* vto = odd ? vt0 : vt1;
     V* vtn = odd ? vt1 : vt0;
-    // r~_{i-1} and y_i of a row from stored vectors (the owner evaluates the same expressions)
-    auto rt_of = [&](int c) { return axpy(nom, ldv(&tt[c]), ldv(&zf[c])); };
-    auto y_of = [&](const V& rtc, int c) { return axpy(beta, axpy(nom, ldv(&vto[c]), ldv(&yo[c])), rtc); };
-    auto ynb = [&](int c) { return y_of(rt_of(c), c); };
+    // y_i of a row from stored vectors: r~_{i-1} = z^ - omega t~, y_i = r~ + beta (y_{i-1} - omega v~);
+    // the owner evaluates the same expressions on the same values
+    struct Raw1 {
+      V tt, zf, vt, y;
+    };
+    auto ld1 = [&](int c) { return Raw1{ldv(&tt[c]), ldv(&zf[c]), ldv(&vto[c]), ldv(&yo[c])}; };
+    auto rt_of = [&](const Raw1& a) { return axpy(nom, a.tt, a.zf); };
+    auto y_of = [&](const Raw1& a, const V& rtc) { return axpy(beta, axpy(nom, a.vt, a.y), rtc); };
+    auto cb1 = [&](const Raw1& a) { return y_of(a, rt_of(a)); };
     Acc l_rv, l_rr;
     dot_zero(l_rv);
     dot_zero(l_rr);
-    auto p1_row = [&](int k, const Ref& ref) -> V {
-      const V xk = ldv(&x[k]), yk = ldv(&yo[k]), zk = ldv(&z[k]), sk = ldv(&s[k]), tk = ldv(&t[k]),
-              rhk = ldv(&rh[k]);
-      x[k] = mk<T>(xk.x + alp * yk.x + omp * zk.x, xk.y + alp * yk.y + omp * zk.y);
+    // all loads of a row (own and neighbours) are issued before its stores
+    rows([&](int k, const Ref& ref) {
+      const V xk = ldv(&x[k]), zk = ldv(&z[k]), sk = ldv(&s[k]), tk = ldv(&t[k]), rhk = ldv(&rh[k]);
+      const Raw1 own = ld1(k);
+      const V rtk = rt_of(own);
+      const V ynk = y_of(own, rtk);
+      const V vv = product(ref, ynk, ld1, cb1);
       const V rk = axpy(nom, tk, sk);
+      x[k] = mk<T>(xk.x + alp * own.y.x + omp * zk.x, xk.y + alp * own.y.y + omp * zk.y);
       r[k] = rk;
+      if (LINES) rt[k] = rtk;
+      yn[k] = ynk;
+      v[k] = vv;
+      if (LINES && ref.line)
+        lbuf[k - r0] = make_float2((float)vv.x, (float)vv.y);
+      else
+        vtn[k] = vv;
       dot_acc(l_rr, rk.x, rk.x);
       dot_acc(l_rr, rk.y, rk.y);
-      const V rtk = rt_of(k);
-      if (LINES) rt[k] = rtk;
-      const V ynk = y_of(rtk, k);
-      yn[k] = ynk;
-      const V vv = product(ref, ynk, ynb);
-      v[k] = vv;
       dot_acc(l_rv, rhk.x, vv.x);
       dot_acc(l_rv, rhk.y, vv.y);
-      return vv;
-    };
-    rows([&](int k, const Ref& ref) { vtn[k] = p1_row(k, ref); });
-    lines([&](int k0, int len, const LineFac& f, const Ref(&refs)[kLineChunks]) {
-      float2 src[kLineChunks][1];
-#pragma unroll
-      for (int c = 0; c < kLineChunks; c++) {
-        src[c][0] = make_float2(0.f, 0.f);
-        if (c * 32 + lane < len) {
-          const V vv = p1_row(k0 + c * 32 + lane, refs[c]);
-          src[c][0] = make_float2((float)vv.x, (float)vv.y);
-        }
-      }
+    });
+    lines([&](int k0, int len, const LineFac& f, float2* buf) {
       V* const dst[1] = {vtn};
-      line_solve<T, 1>(k0, len, f, src, dst);
+      line_solve<T, 1>(k0, len, f, buf, bstride, dst);
     });
     {
-      const DF vals[2] = {dot_df(l_rv, dscale), dot_df(l_rr, dscale)};
+      const DF vals[2] = {to_df(l_rv), to_df(l_rr)};
       block_store<2>(vals, busy, s_df, part, kSlotS1, nb);
     }
     grid.sync();
     {
-      double o[2];
-      grid_sum<2>(part, kSlotS1, nb, dinv, o);
+      DF o[2];
+      grid_sum<2>(part, kSlotS1, nb, o);
       if (threadIdx.x == 0) {
-        rr_last = o[1];
-        if (o[1] <= stop2) {
+        const S rv = sc_from(o[0], S{});
+        rr_last = sc_from(o[1], S{});
+        if (sc_le(rr_last, stop2)) {
           s_ctl = 1;
           status = 0;
         } else if (it > maxit) {
           s_ctl = 1;
           status = 1;
-        } else if (o[0] == 0.0 || !isfinite(o[0]) || rho == 0.0 || !isfinite(rho)) {
+        } else if (!sc_ok(rv) || !sc_ok(rho)) {
           s_ctl = 1;
           status = 2;
         } else {
-          alpha = rho / o[0];
-          s_bc[3] = alpha;
+          alpha = sc_div(rho, rv);
+          s_sc[3] = alpha;
         }
       }
     }
     __syncthreads();
     if (s_ctl) break;
     // ---- phase 2 -------------------------------------------------------------------------
-    const T nal = -(T)s_bc[3];
-    const double rho_i = s_bc[6], alpha_i = s_bc[3];  // read before thread 0 overwrites rho below
-    auto znb = [&](int c) { return axpy(nal, ldv(&vtn[c]), ldv(&rt[c])); };
+    const T nal = -sc_t<T>(s_sc[3]);
+    // z_i of a row: r~_{i-1} - alpha v~_i (the owner evaluates the same expression)
+    auto ld2 = [&](int c) { return V2pair<V>{ldv(&vtn[c]), ldv(&rt[c])}; };
+    auto cb2 = [&](const V2pair<V>& a) { return axpy(nal, a.a, a.b); };
     Acc l_ts, l_tt, l_rs, l_rt;
     dot_zero(l_ts);
     dot_zero(l_tt);
     dot_zero(l_rs);
     dot_zero(l_rt);
-    V sk_, tk_;
-    auto p2_row = [&](int k, const Ref& ref) {
+    rows([&](int k, const Ref& ref) {
       const V rk = ldv(&r[k]), vk = ldv(&v[k]), rhk = ldv(&rh[k]);
+      const V zk = cb2(ld2(k));
+      const V tk = product(ref, zk, ld2, cb2);
       const V sk = axpy(nal, vk, rk);
       s[k] = sk;
-      const V zk = znb(k);
       z[k] = zk;
-      const V tk = product(ref, zk, znb);
       t[k] = tk;
+      if (LINES && ref.line) {
+        lbuf[k - r0] = make_float2((float)sk.x, (float)sk.y);
+        lbuf[bstride + k - r0] = make_float2((float)tk.x, (float)tk.y);
+      } else if (LINES) {
+        zf[k] = sk;
+        tt[k] = tk;
+      }
       dot_acc(l_ts, tk.x, sk.x);
       dot_acc(l_ts, tk.y, sk.y);
       dot_acc(l_tt, tk.x, tk.x);
@@ -703,55 +817,38 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       dot_acc(l_rs, rhk.y, sk.y);
       dot_acc(l_rt, rhk.x, tk.x);
       dot_acc(l_rt, rhk.y, tk.y);
-      sk_ = sk;
-      tk_ = tk;
-    };
-    rows([&](int k, const Ref& ref) {
-      p2_row(k, ref);
-      if (LINES) {
-        zf[k] = sk_;
-        tt[k] = tk_;
-      }
     });
-    lines([&](int k0, int len, const LineFac& f, const Ref(&refs)[kLineChunks]) {
-      float2 src[kLineChunks][2];
-#pragma unroll
-      for (int c = 0; c < kLineChunks; c++) {
-        src[c][0] = src[c][1] = make_float2(0.f, 0.f);
-        if (c * 32 + lane < len) {
-          p2_row(k0 + c * 32 + lane, refs[c]);
-          src[c][0] = make_float2((float)sk_.x, (float)sk_.y);
-          src[c][1] = make_float2((float)tk_.x, (float)tk_.y);
-        }
-      }
+    lines([&](int k0, int len, const LineFac& f, float2* buf) {
       V* const dst[2] = {zf, tt};
-      line_solve<T, 2>(k0, len, f, src, dst);
+      line_solve<T, 2>(k0, len, f, buf, bstride, dst);
     });
     {
-      const DF vals[4] = {dot_df(l_ts, dscale), dot_df(l_tt, dscale), dot_df(l_rs, dscale), dot_df(l_rt, dscale)};
+      const DF vals[4] = {to_df(l_ts), to_df(l_tt), to_df(l_rs), to_df(l_rt)};
       block_store<4>(vals, busy, s_df, part, kSlotS2, nb);
     }
     grid.sync();
     {
-      double o[4];
-      grid_sum<4>(part, kSlotS2, nb, dinv, o);
-      const double ts = o[0], t2 = o[1], rs = o[2], rtv = o[3];
-      // the two divisions run in two warps: thread 0 omega and rho_{i+1}, thread 32 beta_{i+1}
-      //   beta = (rho_{i+1} / rho_i) (alpha / omega) = alpha (rs t2 - ts rt) / (rho_i ts)
+      DF o[4];
+      grid_sum<4>(part, kSlotS2, nb, o);
       if (threadIdx.x == 0) {
-        if (!isfinite(ts) || !isfinite(t2) || !isfinite(rs) || !isfinite(rtv)) {
+        const S ts = sc_from(o[0], S{}), t2 = sc_from(o[1], S{}), rs = sc_from(o[2], S{}), rtv = sc_from(o[3], S{});
+        if (!sc_finite(ts) || !sc_finite(t2) || !sc_finite(rs) || !sc_finite(rtv)) {
           s_ctl = 1;
           status = 2;
         } else {
-          // t = 0 means A z = 0: omega = 0 leaves r = s and restarts the direction (beta = 0)
-          const double omega = t2 > 0.0 ? ts / t2 : 0.0;
-          rho = fma(-omega, rtv, rs);
-          s_bc[1] = alpha;
-          s_bc[2] = omega;
-          s_bc[6] = rho;
+          // t = 0 means A z = 0: omega = 0 leaves r = s and restarts the direction (beta = 0).
+          // Only ratios of dots are formed, so nothing underflows at tight tolerances.
+          S omega, beta;
+          sc_zero(omega);
+          sc_zero(beta);
+          if (sc_pos(t2)) omega = sc_div(ts, t2);
+          const S rho_new = sc_fnma(omega, rtv, rs);
+          if (sc_nonzero(omega)) beta = sc_mul(sc_div(rho_new, rho), sc_div(alpha, omega));
+          s_sc[0] = beta;
+          s_sc[1] = alpha;
+          s_sc[2] = omega;
+          rho = rho_new;
         }
-      } else if (threadIdx.x == 32) {
-        s_bc[0] = (t2 > 0.0 && ts != 0.0) ? alpha_i * fma(rs, t2, -ts * rtv) / (rho_i * ts) : 0.0;
       }
     }
     __syncthreads();
@@ -761,7 +858,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     d.ctr->krylov_iters = it - 1;
     d.ctr->krylov_status = status;
-    d.ctr->krylov_relres = bb > 0.0 ? sqrt(rr_last / bb) : 0.0;
+    d.ctr->krylov_relres = bb > 0.0 ? sqrt(sc_double(rr_last) / (bb * dscale)) : 0.0;
   }
 }
 

@@ -699,11 +699,14 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
     d.line_g = t;
     AL(d.line_start, N);
     AL(d.line_len, N);
+    AL(d.lscratch, N);
+    AL(d.lblk, W);
     AL(d.line_row_flag, N);
     double** vecs[14] = {(double**)&d.kx,  (double**)&d.kr,   (double**)&d.krh,  (double**)&d.ky0, (double**)&d.ky1,
                          (double**)&d.kv,  (double**)&d.ks,   (double**)&d.kt,   (double**)&d.kz,  (double**)&d.kvt0,
                          (double**)&d.kvt1, (double**)&d.krt, (double**)&d.kzf, (double**)&d.ktt};
     for (auto v : vecs) AL(*v, N * 2);
+    AL(d.kls, N * 2);
     AL(d.partials, (size_t)8 * 4 * m->sms + 64);
   }
   AL(d.ctr, 1);

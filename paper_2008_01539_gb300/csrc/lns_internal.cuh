@@ -42,7 +42,7 @@ struct IterCounters {
   int any_s;           // the support of du_A is non-empty
   int any_new;         // Algorithm 2: the next subdomain is non-empty
   int n_lines;         // fracture line blocks in the compacted system (after cutting long lines)
-  int n_line_starts;   // line starts found by the marking pass (fixed while the factor pass appends)
+  int n_line_starts;   // fracture lines found by the marking pass (before cutting)
   int krylov_iters;
   int krylov_status;   // 0 ok, 1 maxit, 2 breakdown
   int converged;
@@ -79,9 +79,14 @@ struct Dev {
   double* dbg_off;   // 4 E2 (diagnostics), f64
   // fracture-line blocks of the preconditioner (per compact row, T)
   void *line_dinv, *line_a, *line_g;
-  int *line_start, *line_len, *line_row_flag;
+  // line_start: the marking pass's line starts (any order), then the ascending list of line-block
+  // starts (after cutting); line_len[k]: rows of the line block starting at compact row k;
+  // lblk: bitset of line-block starts; lscratch: compaction scratch
+  int *line_start, *line_len, *line_row_flag, *lscratch;
+  uint32_t* lblk;
   // Krylov vectors
   void *kx, *kr, *krh, *ky0, *ky1, *kv, *ks, *kt, *kz, *kvt0, *kvt1, *krt, *kzf, *ktt;
+  double* kls;  // 2n: line-solve inputs of chunks too long for shared memory
   double* partials;
   IterCounters* ctr;   // device
   IterCounters* ctr_h; // pinned host mirror
