@@ -3,12 +3,15 @@
 
 One step = one whole simulation case: the 40 timesteps (0.01 d growing to 30 d, 365 d in
 total) of the 400x400-cell matrix with a 300-segment natural fracture network and four
-80-cell hydraulic fractures on a producer at 1500 psi (166,659 cells), FP64 throughout,
-started from the initial state.  The headline value is cell-Newton-updates per second
-(the sum over Newton iterations of the active-set size n_A, divided by the case time).
-The same case with standard (full-domain) Newton on the same GPU, the end-to-end figure
-through the C ABI with host buffers, the roofline of the dominant kernel, the CPU oracle
-on a bounded sample of the same workload, and the SM clocks are reported beside it.
+80-cell hydraulic fractures on a producer at 1500 psi (166,659 cells), started from the
+initial state.  Residual, Jacobian assembly, convergence checks and the Newton update are
+FP64; the BiCGStab solve and its preconditioner run in FP32 as an inexact Newton (the default,
+--krylov fp64 for FP64 throughout).  The headline value is cell-Newton-updates per second (the
+sum over Newton iterations of the active-set size n_A, divided by the case time).  Beside it:
+the same case with the other Krylov precision and with standard (full-domain) Newton on the
+same GPU, the final fields' error against the FP64 CPU oracle, the end-to-end figure through
+the C ABI with host buffers, the roofline of the dominant kernel, the CPU oracle on a bounded
+sample of the same workload, and the SM clocks.
 
 Multi-GPU: the path does not shard (one model per process), so N GPUs run N independent
 replicas ("weak" scaling); rank 0 prints the aggregate.
@@ -45,12 +48,17 @@ def parse():
     ap.add_argument("--mode", choices=["local", "full", "dd"], default="local",
                     help="solver whose case is the headline (default: Algorithm 1)")
     ap.add_argument("--case", choices=["config1", "config0"], default="config1")
-    ap.add_argument("--fp32-krylov", action="store_true", help="FP32 BiCGStab (inexact Newton)")
+    ap.add_argument("--krylov", choices=["fp32", "fp64"], default="fp32",
+                    help="BiCGStab and preconditioner precision: FP32 (inexact Newton, the default) or FP64; "
+                         "residual, Jacobian assembly, convergence checks and updates are FP64 in both")
+    ap.add_argument("--fp32-krylov", action="store_true", help="same as --krylov fp32")
     ap.add_argument("--precond", choices=["lines", "cells"], default="lines",
                     help="block Jacobi with fracture-segment blocks (default) or single-cell blocks")
     ap.add_argument("--headline-only", action="store_true",
                     help="run only the headline case (for profiler launch lists)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--ensemble", type=int, default=64,
+                    help="realizations in the batched-ensemble run (N ~ U{150..500} grids; 0 skips it)")
     ap.add_argument("--krylov-rtol", type=float, default=None,
                     help="BiCGStab relative tolerance (default: the library's)")
     return ap.parse_args()
@@ -68,7 +76,8 @@ def workload_name(case, args):
     meta = case.meta
     return (f"{meta['nx']}x{meta['ny']} matrix ({meta['dx']:.0f} m cells) + {meta['n_segments'] - meta['n_hf']}-segment "
             f"DFN + {meta['n_hf']} hydraulic fractures, n={case.n} cells, {len(case.dt_schedule)} timesteps to "
-            f"{case.dt_schedule.sum() / 86400:.0f} d, {mode}, {'FP32 Krylov' if args.fp32_krylov else 'FP64'}")
+            f"{case.dt_schedule.sum() / 86400:.0f} d, {mode}, "
+            f"{'FP64 residual/Jacobian + FP32 BiCGStab' if args.fp32_krylov else 'FP64 throughout'}")
 
 
 # ---------------------------------------------------------------------------------------
@@ -266,8 +275,51 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
+def time_case(model, case, steps, flush, stream):
+    """Run the case `steps` times from the initial state; CUDA-event times (s) and stats."""
+    import torch
+
+    ev, stats_all = [], []
+    for _ in range(steps):
+        flush.zero_()
+        model.lns_reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats_all.append(run_case(model, case))
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) / 1e3 for a, b in ev], stats_all
+
+
+def field_error(p, sw, p_ref, sw_ref):
+    """Difference of final fields from the FP64 oracle's."""
+    import numpy as np
+
+    from paper_2008_01539_gb300 import lns
+
+    dp = np.abs(p - p_ref)
+    return {"max_abs_dp_psi": float(dp.max()) / lns.PSI,
+            "max_rel_dp": float((dp / np.abs(p_ref)).max()),
+            "max_abs_dsw": float(np.abs(sw - sw_ref).max())}
+
+
+def oracle_case(case, mode):
+    """The FP64 oracle's final fields for the whole case (the accuracy reference)."""
+    import oracle as O
+
+    mode_id = {"local": 1, "full": 0, "dd": 2}[mode]
+    sim = O.Sim(case, O.Options(mode=mode_id))
+    t0 = time.perf_counter()
+    for dt in case.dt_schedule:
+        sim.timestep(float(dt))
+    return sim.p.copy(), sim.sw.copy(), time.perf_counter() - t0
+
+
 def main():
     args = parse()
+    args.fp32_krylov = args.fp32_krylov or args.krylov == "fp32"
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
@@ -346,7 +398,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(args.steps, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32-krylov/f64" if args.fp32_krylov else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if args.fp32_krylov else "f64",
             "data": "synthetic (seeded generator shaped like the paper's DFN models)",
             "config": {"workload": workload_name(case, args), "cells": case.n, "timesteps": len(case.dt_schedule),
                        "l2": "flushed (256 MB write) before every timed case", "parallelism": f"replicas x{world}"},
@@ -357,30 +409,33 @@ def main():
             "gpu_launches": launches, "kernels": kernels, "roofline": roof, "clocks": clk}
 
     if not args.headline_only:
-        # standard Newton on the same GPU, same case
+        # the other Krylov precision and standard Newton on the same GPU, same case
+        def variant(vopts):
+            vm = lns.Model(case, vopts)
+            vm.lns_reset()
+            run_case(vm, case)  # warm-up
+            vt, vst = time_case(vm, case, max(1, min(args.steps, 3)), flush, stream)
+            vp, vsw = vm.lns_get_state()
+            vm.close()
+            return vt, vst, vp, vsw
+
+        other = "fp64" if args.fp32_krylov else "fp32"
+        oopts = lns.Options(**{**opts.__dict__, "krylov_fp32": int(not args.fp32_krylov),
+                               "krylov_rtol": lns.Options().krylov_rtol if args.fp32_krylov else 1e-5})
+        vt, vst, vp, vsw = variant(oopts)
+        line[f"{other}_krylov"] = {
+            "case_time_s": statistics.mean(vt), "unit": UNIT,
+            "value": sum(s["cell_updates"] for st in vst for s in st) / sum(vt),
+            "newton_iterations_per_case": sum(s["iterations"] for st in vst for s in st) / len(vt),
+            "krylov_iterations_per_case": sum(s["krylov_iters"] for st in vst for s in st) / len(vt),
+            "krylov_rtol": oopts.krylov_rtol}
+        other_state = (vp, vsw)
         if args.mode != "full":
-            fopts = lns.Options(**{**opts.__dict__, "mode": lns.LNS_MODE_FULL})
-            fm = lns.Model(case, fopts)
-            fm.lns_reset()
-            run_case(fm, case)  # warm-up
-            ft, fu, fi = [], 0, 0
-            for _ in range(max(1, min(args.steps, 3))):
-                flush.zero_()
-                fm.lns_reset()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                st = run_case(fm, case)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ft.append(e0.elapsed_time(e1) / 1e3)
-                fu += sum(s["cell_updates"] for s in st)
-                fi += sum(s["iterations"] for s in st)
-            pf, _ = fm.lns_get_state()
-            fm.close()
+            ft, fst, pf, _ = variant(lns.Options(**{**opts.__dict__, "mode": lns.LNS_MODE_FULL}))
             tf = statistics.mean(ft)
-            line["full_newton"] = {"case_time_s": tf, "value": fu / sum(ft), "unit": UNIT,
-                                   "newton_iterations_per_case": fi / len(ft),
+            line["full_newton"] = {"case_time_s": tf, "value": sum(s["cell_updates"] for st in fst for s in st) / sum(ft),
+                                   "unit": UNIT,
+                                   "newton_iterations_per_case": sum(s["iterations"] for st in fst for s in st) / len(ft),
                                    "max_abs_dp_vs_localized_psi": float(np.max(np.abs(pf - p_final))) / lns.PSI}
             line["speedup_vs_full_newton"] = tf / line["case_time_s"]
         # end to end through the C ABI with host buffers
@@ -403,6 +458,34 @@ def main():
         line["e2e"] = {"value": reduce_sum(e2e_u, world) / te, "unit": UNIT,
                        "h2d_bytes_per_step": 2 * 8 * case.n, "d2h_bytes_per_step": 2 * 8 * case.n,
                        "case_time_s": te / max(args.steps, 1)}
+        # batched ensemble: realizations of uneven size advanced together as one union model
+        if args.ensemble > 0:
+            from paper_2008_01539_gb300 import casegen as cg
+
+            t0 = time.perf_counter()
+            ens = cg.ensemble(args.ensemble)
+            t_gen = time.perf_counter() - t0
+            em = lns.Model(ens, opts)
+            em.lns_reset()
+            em.lns_timestep(float(ens.dt_schedule[0]))  # warm-up (first step only)
+            et, est = time_case(em, ens, 1, flush, stream)
+            em.close()
+            line["ensemble"] = {
+                "realizations": args.ensemble, "cells": ens.n, "timesteps": len(ens.dt_schedule),
+                "case_time_s": et[0], "value": sum(s["cell_updates"] for s in est[0]) / et[0], "unit": UNIT,
+                "newton_iterations": sum(s["iterations"] for s in est[0]),
+                "krylov_iterations": sum(s["krylov_iters"] for s in est[0]),
+                "workload": f"{args.ensemble} seeded realizations (N x N matrix, N ~ U{{150..500}}, U{{50..400}} "
+                            f"natural fractures, 2 hydraulic fractures on a producer each) as one union model, "
+                            f"{len(ens.dt_schedule)} timesteps to 30 d, same solver options as the headline",
+                "generate_s": t_gen}
+        # accuracy: final fields against the FP64 oracle's whole case (rank 0, N = 1)
+        if rank == 0 and world == 1:
+            p_ref, sw_ref, t_ref = oracle_case(case, args.mode)
+            line["error_vs_fp64_oracle"] = {
+                "headline": field_error(p_final, sw_final, p_ref, sw_ref),
+                f"{other}_krylov": field_error(other_state[0], other_state[1], p_ref, sw_ref),
+                "oracle_case_time_s": t_ref}
         # CPU oracle on the host cores, bounded sample (rank 0, N = 1)
         if rank == 0 and world == 1:
             u, t, n_ts = oracle_sample(case, args.mode, args.cpu_seconds)

@@ -129,7 +129,7 @@ typedef struct {
   int32_t converged;     /* convergence test of the iteration */
   int32_t step_done;     /* the timestep closed after this iteration */
   int32_t krylov_iters;
-  int32_t krylov_status; /* 0 ok, 1 max iterations, 2 breakdown */
+  int32_t krylov_status; /* 0 ok, 1 max iterations, 2 breakdown, 3 grid barrier wait timed out */
   double max_dp, max_dsw, cnv, krylov_relres;
 } lns_iter_stats;
 

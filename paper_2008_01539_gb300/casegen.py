@@ -422,3 +422,58 @@ def grid_2d(nx: int, ny: int, dx: float = 5.0, seed: int = 3, *, with_well: bool
         b.wells.append((c, 2.0 * math.pi * perm[c] * 1.0 / math.log(0.2 * dx / 0.1), 3000.0 * PSI))
     return _finish(b, f"grid_{nx}x{ny}", fluid, fluid.p_ref, 0.25, doubling_schedule(n_steps, 0.1),
                    nx * ny, dict(nx=nx, ny=ny))
+
+
+def realization(index: int, dx: float = 5.0, n_steps: int = 12) -> Case:
+    """One member of a seeded ensemble of DFN models of uneven size: an N x N matrix with
+    N ~ U{150..500}, U{50..400} natural fractures, and two hydraulic fractures on a producer
+    at 1500 psi through the centre (seed = ``index``)."""
+    rng = np.random.Generator(np.random.PCG64(10_000 + index))
+    nn = int(rng.integers(150, 501))
+    n_dfn = int(rng.integers(50, 401))
+    half = max(4, nn // 10)
+    hf = []
+    for c in (nn // 2 - 2, nn // 2 + 2):
+        x = c * dx + dx / 2
+        hf.append((x, (nn // 2 - half) * dx, x, (nn // 2 + half) * dx, 2 * half))
+    wells = [(i, half, 1500.0 * PSI) for i in range(2)]
+    return dfn_case(nn, nn, dx, n_dfn, index, hf=hf, wells=wells,
+                    dts=geometric_schedule(n_steps, 30.0, dt_max_days=10.0), name=f"real{index}_{nn}x{nn}")
+
+
+def batch(cases: Sequence[Case], name: str = "batch") -> Case:
+    """Disjoint union of models that share the fluid and the timestep schedule: one graph whose
+    connected components are the members, cell ranges in member order (member k starts at
+    ``meta['offsets'][k]``).  A localized solve of the union advances every member at once."""
+    if not cases:
+        raise ValueError("empty batch")
+    f0, dts = cases[0].fluid, cases[0].dt_schedule
+    for c in cases[1:]:
+        if c.fluid != f0:
+            raise ValueError("batched models must share the fluid")
+        if c.dt_schedule.shape != dts.shape or not np.array_equal(c.dt_schedule, dts):
+            raise ValueError("batched models must share the timestep schedule")
+    offs = np.cumsum([0] + [c.n for c in cases])
+    adj = np.cumsum([0] + [c.row_ptr[-1] for c in cases])
+    row_ptr = np.concatenate([cases[0].row_ptr[:1]] + [c.row_ptr[1:] + adj[k] for k, c in enumerate(cases)])
+    nbr = np.concatenate([c.nbr + offs[k] for k, c in enumerate(cases)]).astype(np.int32)
+    line_id, lbase = [], 0
+    for c in cases:
+        li = c.line_id.astype(np.int64)
+        line_id.append(np.where(li >= 0, li + lbase, -1))
+        lbase += int(li.max()) + 1 if (li >= 0).any() else 0
+    cat = np.concatenate
+    return Case(name=name, n=int(offs[-1]), row_ptr=row_ptr.astype(np.int32), nbr=nbr,
+                trans=cat([c.trans for c in cases]), pv_ref=cat([c.pv_ref for c in cases]),
+                depth=cat([c.depth for c in cases]), line_id=cat(line_id).astype(np.int32),
+                always_active=cat([c.always_active for c in cases]).astype(np.uint8),
+                well_cell=cat([c.well_cell + offs[k] for k, c in enumerate(cases)]).astype(np.int32),
+                well_wi=cat([c.well_wi for c in cases]), well_bhp=cat([c.well_bhp for c in cases]),
+                fluid=f0, p0=cat([c.p0 for c in cases]), sw0=cat([c.sw0 for c in cases]),
+                dt_schedule=dts.copy(), n_matrix=int(sum(c.n_matrix for c in cases)),
+                meta=dict(members=[c.name for c in cases], offsets=offs.tolist()))
+
+
+def ensemble(n_real: int = 256, first: int = 0, **kw) -> Case:
+    """The batched ensemble: realizations first .. first+n_real-1 as one union model."""
+    return batch([realization(first + r, **kw) for r in range(n_real)], name=f"ensemble{n_real}")

@@ -30,14 +30,11 @@
 // double-float (two FP32 words, Knuth's TwoSum), after scaling by an exact power of two near
 // 1/||b||^2.  Every block sums the block partials in the same order, so all blocks hold identical
 // scalars (computed once per block by thread 0: FP64 division is a long sequence here).
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
 
 #include "lns_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace lns {
 
@@ -450,6 +447,45 @@ __device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, fl
   }
 }
 
+// ---- grid barrier --------------------------------------------------------------------------
+// All blocks of the (cooperative, hence co-resident) launch add to one counter: block 0 adds
+// 2^31 - (nb - 1), the others 1, so the counter's top bit flips exactly when the last block
+// arrives, and every block waits for the flip of the value it saw when it arrived.  Every wait is
+// bounded: after kBarrierTimeoutNs the block records a timeout and stops waiting, and the kernel
+// ends its loop at the next check (the host reports an error).  Block barriers on both sides.
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void grid_barrier(IterCounters* ctr, unsigned nb) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nb - 1u) : 1u;
+    __threadfence();
+    const unsigned old = atomicAdd(&ctr->bar_count, add);
+    const unsigned long long t0 = global_ns();
+    unsigned k = 0;
+    while (((old ^ ld_acquire(&ctr->bar_count)) & 0x80000000u) == 0u) {
+      if ((++k & 63u) == 0u && global_ns() - t0 > kBarrierTimeoutNs) {
+        atomicExch(&ctr->bar_timeout, 1);
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
 // ---- the solver --------------------------------------------------------------------------
 // A matrix row: off >= 0 is its first entry in the shared-memory pool, off < 0 encodes its first
 // CSR entry e0 as -(e0 + 1) (global memory); deg entries; line: a fracture-line row.
@@ -514,7 +550,6 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   using Ref = RowRef;
   using Acc = typename DotAcc<T>::t;
   constexpr bool kF64 = sizeof(T) == 8;
-  cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double sh[kWarps];
   __shared__ DF s_df[4 * kWarps];
@@ -678,7 +713,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     line_solve<T, 1>(k0, len, f, buf, bstride, dst);
   });
   block_store_f64(l_bb, sh, part, nb);
-  grid.sync();
+  grid_barrier(d.ctr, nb);
+  const bool timed_out = *(volatile int*)&d.ctr->bar_timeout;
   const double bb = grid_sum_f64(part, nb);
   // Dots are scaled by an exact power of two near 1/bb before they are carried in double-float,
   // so that the reductions and the scalar arithmetic stay far from the FP32 range limits (the
@@ -705,11 +741,11 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     sc_zero(s_sc[0]);  // beta_1
     sc_zero(s_sc[1]);  // alpha_0
     sc_zero(s_sc[2]);  // omega_0
-    s_ctl = 0;
+    s_ctl = timed_out ? 1 : 0;
   }
   __syncthreads();
-  int status = 1, it;
-  for (it = 1;; it++) {
+  int status = timed_out ? 3 : 1, it = 1;
+  for (it = 1; !s_ctl; it++) {
     // ---- phase 1 -------------------------------------------------------------------------
     const T beta = sc_t<T>(s_sc[0]), alp = sc_t<T>(s_sc[1]), omp = sc_t<T>(s_sc[2]);
     const T nom = -omp;
@@ -760,14 +796,17 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       const DF vals[2] = {to_df(l_rv), to_df(l_rr)};
       block_store<2>(vals, busy, s_df, part, kSlotS1, nb);
     }
-    grid.sync();
+    grid_barrier(d.ctr, nb);
     {
       DF o[2];
       grid_sum<2>(part, kSlotS1, nb, o);
       if (threadIdx.x == 0) {
         const S rv = sc_from(o[0], S{});
         rr_last = sc_from(o[1], S{});
-        if (sc_le(rr_last, stop2)) {
+        if (*(volatile int*)&d.ctr->bar_timeout) {
+          s_ctl = 1;
+          status = 3;
+        } else if (sc_le(rr_last, stop2)) {
           s_ctl = 1;
           status = 0;
         } else if (it > maxit) {
@@ -826,13 +865,16 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       const DF vals[4] = {to_df(l_ts), to_df(l_tt), to_df(l_rs), to_df(l_rt)};
       block_store<4>(vals, busy, s_df, part, kSlotS2, nb);
     }
-    grid.sync();
+    grid_barrier(d.ctr, nb);
     {
       DF o[4];
       grid_sum<4>(part, kSlotS2, nb, o);
       if (threadIdx.x == 0) {
         const S ts = sc_from(o[0], S{}), t2 = sc_from(o[1], S{}), rs = sc_from(o[2], S{}), rtv = sc_from(o[3], S{});
-        if (!sc_finite(ts) || !sc_finite(t2) || !sc_finite(rs) || !sc_finite(rtv)) {
+        if (*(volatile int*)&d.ctr->bar_timeout) {
+          s_ctl = 1;
+          status = 3;
+        } else if (!sc_finite(ts) || !sc_finite(t2) || !sc_finite(rs) || !sc_finite(rtv)) {
           s_ctl = 1;
           status = 2;
         } else {
@@ -881,6 +923,9 @@ int krylov_grid(int fp32, int sms) {
 }
 
 cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, LaunchCfg c) {
+  // barrier counter and timeout flag start from zero in every launch
+  cudaError_t e = cudaMemsetAsync(&d.ctr->bar_count, 0, 3 * sizeof(unsigned), c.stream);
+  if (e != cudaSuccess) return e;
   Dev dd = d;
   void* args[] = {&dd, &rtol, &maxit};
   count_launches(1);

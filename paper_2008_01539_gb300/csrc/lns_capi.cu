@@ -267,6 +267,7 @@ void annotate_pending(lns_model* m) {
 lns_status krylov_outcome(lns_model* m) {
   const IterCounters& h = *m->d.ctr_h;
   if (h.krylov_status == 2) return fail(LNS_EKRYLOV, "BiCGStab breakdown");
+  if (h.krylov_status == 3) return fail(LNS_EKRYLOV, "BiCGStab grid barrier wait timed out");
   if (h.krylov_status == 1 && !(h.krylov_relres <= m->o.krylov_fail_rtol))
     return fail(LNS_EKRYLOV, "BiCGStab reached krylov_maxit with relative residual " + std::to_string(h.krylov_relres));
   return LNS_OK;

@@ -44,7 +44,7 @@ struct IterCounters {
   int n_lines;         // fracture line blocks in the compacted system (after cutting long lines)
   int n_line_starts;   // fracture lines found by the marking pass (before cutting)
   int krylov_iters;
-  int krylov_status;   // 0 ok, 1 maxit, 2 breakdown
+  int krylov_status;   // 0 ok, 1 maxit, 2 breakdown, 3 grid barrier wait timed out
   int converged;
   int is_expand;
   int halo_flag;       // Algorithm 2 halo test result
@@ -52,7 +52,11 @@ struct IterCounters {
   unsigned long long max_dsw_bits;
   unsigned long long cnv_bits;
   double krylov_relres;
-  double pad[3];
+  unsigned bar_count;  // grid barrier of the Krylov kernel (its top bit flips at each barrier)
+  unsigned bar_pad;
+  int bar_timeout;     // set when a barrier wait gave up (the kernel then stops)
+  int pad_i;
+  double pad[1];
 };
 
 struct Dev {
