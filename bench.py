@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="run only the headline case (for profiler launch lists)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--serve-seconds", type=float, default=15.0,
+                    help="measured window of the serving run (Poisson arrivals); 0 skips it")
+    ap.add_argument("--serve-warmup", type=float, default=4.0, help="serving warm-up before the window (s)")
+    ap.add_argument("--serve-models", type=int, default=32, help="resident models of the serving run")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="request arrival rate (1/s)")
+    ap.add_argument("--serve-workers", type=int, default=4, help="requests run at once")
     ap.add_argument("--ensemble", type=int, default=64,
                     help="realizations in the batched-ensemble run (N ~ U{150..500} grids; 0 skips it)")
     ap.add_argument("--krylov-rtol", type=float, default=None,
@@ -317,6 +323,67 @@ def oracle_case(case, mode):
     return sim.p.copy(), sim.sw.copy(), time.perf_counter() - t0
 
 
+def serving_run(args, opts):
+    """Requests 'advance model k by dt' with Poisson arrivals over resident models of log-uniform
+    size; latency = completion - submission on the server clock."""
+    import numpy as np
+
+    from paper_2008_01539_gb300 import casegen as cg
+    from paper_2008_01539_gb300 import lns
+
+    rng = np.random.default_rng(4)
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(1e6), args.serve_models)).astype(int)
+    t0 = time.perf_counter()
+    srv = lns.Server(workers=args.serve_workers, hbm_budget_bytes=150 << 30)
+    ids = [srv.add_model(cg.serving_model(k, int(c)), opts) for k, c in enumerate(sizes)]
+    t_setup = time.perf_counter() - t0
+    total = args.serve_warmup + args.serve_seconds
+    start = srv.now()
+    t_next, rid, sub, done = start, 0, {}, []
+    while True:
+        now = srv.now()
+        while t_next <= now and t_next - start < total:
+            mid = int(rng.integers(len(ids)))
+            dt = float(np.exp(rng.uniform(np.log(0.1), np.log(30.0)))) * cg.DAY
+            srv.submit(ids[mid], dt, rid)
+            sub[rid] = (t_next - start, ids[mid])
+            rid += 1
+            t_next += float(rng.exponential(1.0 / args.serve_rate))
+        done += srv.poll(512, 0.0)
+        if t_next - start >= total:
+            break
+        time.sleep(max(0.0, min(t_next - srv.now(), 0.002)))
+    srv.drain(600.0)
+    while True:
+        got = srv.poll(512, 0.0)
+        if not got:
+            break
+        done += got
+    st = srv.stats()
+    srv.close()
+    meas = [c for c in done if c["t_submit"] - start >= args.serve_warmup]
+    ok = [c for c in meas if c["status"] == 0]
+    lat = np.array([c["t_done"] - c["t_submit"] for c in ok])
+    t_first = min(c["t_submit"] for c in meas) if meas else 0.0
+    t_last = max(c["t_done"] for c in meas) if meas else 1.0
+    upd = sum(c["stats"]["cell_updates"] for c in ok)
+    return {
+        "workload": f"{len(ids)} resident models (N x N matrix + DFN, {int(sizes.min())}-{int(sizes.max())} cells, "
+                    f"log-uniform), Poisson arrivals at {args.serve_rate:.0f}/s, dt log-uniform 0.1-30 d, model "
+                    f"uniform, {args.serve_workers} workers, HBM budget 150 GB",
+        "window_s": args.serve_seconds, "warmup_s": args.serve_warmup,
+        "requests": len(meas), "failed": len(meas) - len(ok),
+        "failed_by_status": {str(k): sum(1 for c in meas if c["status"] == k) for k in sorted({c["status"] for c in meas})
+                             if k != 0},
+        "p50_latency_ms": float(np.percentile(lat, 50)) * 1e3 if len(lat) else None,
+        "p99_latency_ms": float(np.percentile(lat, 99)) * 1e3 if len(lat) else None,
+        "mean_latency_ms": float(lat.mean()) * 1e3 if len(lat) else None,
+        "value": upd / max(t_last - t_first, 1e-9), "unit": UNIT,
+        "timestep_cuts": int(sum(c["stats"]["dd_outer"] for c in ok)),
+        "resident_models": st["resident_models"], "resident_gb": st["resident_bytes"] / 2 ** 30,
+        "evictions": st["evictions"], "total_cells": int(sizes.sum()), "setup_s": t_setup}
+
+
 def main():
     args = parse()
     args.fp32_krylov = args.fp32_krylov or args.krylov == "fp32"
@@ -479,6 +546,9 @@ def main():
                             f"natural fractures, 2 hydraulic fractures on a producer each) as one union model, "
                             f"{len(ens.dt_schedule)} timesteps to 30 d, same solver options as the headline",
                 "generate_s": t_gen}
+        # serving: requests over many resident models (continuous batching on worker streams)
+        if args.serve_seconds > 0:
+            line["serving"] = serving_run(args, opts)
         # accuracy: final fields against the FP64 oracle's whole case (rank 0, N = 1)
         if rank == 0 and world == 1:
             p_ref, sw_ref, t_ref = oracle_case(case, args.mode)

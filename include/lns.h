@@ -210,8 +210,16 @@ lns_status lns_assemble(lns_model* model, double dt, const uint32_t* va_bits, do
 lns_status lns_get_state(const lns_model* model, double* p, double* sw);
 lns_status lns_set_state(lns_model* model, const double* p, const double* sw, const double* pn,
                          const double* swn);
-/* Device-to-device variants for device-resident callers (pointers are device memory). */
+/* Device-to-device variants for device-resident callers (pointers are device memory).
+ * set_state_device sets u = (p, sw) and u^n = u, and forgets the support, like lns_set_state. */
 lns_status lns_get_state_device(const lns_model* model, double* p, double* sw);
+lns_status lns_set_state_device(lns_model* model, const double* p, const double* sw);
+/* Replace the previous timestep's support set (host bitset of n_cells bits; NULL: none), e.g.
+ * to restore a model saved with lns_get_support/lns_get_state so that its next timestep starts
+ * from the same active set as it would have. */
+lns_status lns_set_support(lns_model* model, const uint32_t* bits);
+/* Move the model to another CUDA stream (after the work queued on the current one finishes). */
+lns_status lns_set_stream(lns_model* model, void* cuda_stream);
 /* Return to the initial state (p0, sw0) without host transfers; forget the support. */
 lns_status lns_reset(lns_model* model);
 /* The previous timestep's support set (the next step's initial active set before the
@@ -249,6 +257,62 @@ lns_status lns_active_set_noalloc(int32_t n_cells, const int32_t* row_ptr, const
                                   const uint32_t* always_bits, const double* dp, const double* dsw, double eps_p,
                                   double eps_sw, int32_t m_layers, int32_t converged, uint32_t* va_bits,
                                   uint32_t* vb_bits, int32_t* is_expand, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: many resident models on one GPU.  The paper has no counterpart (its method advances
+ * one model); this is the request loop of a deployment that advances many.
+ *
+ * Requests "advance model k by dt" (lns_server_submit, any thread, any time) are served by
+ * `workers` threads, each with its own CUDA stream: a worker takes the oldest queued request
+ * whose model is idle and runs lns_timestep on it, so the requests of different models overlap on
+ * the device; the requests of one model run in submission order.  Models stay on the device; they
+ * are created when first needed and admitted against hbm_budget_bytes (0: no limit) -- when a
+ * model does not fit, idle models are evicted least recently used first, their state and support
+ * saved to the host and restored exactly on their next request; a model that does not fit even
+ * then waits for the running requests, and runs alone if it exceeds the budget by itself.  A timestep that does not
+ * converge is retried from its starting state as two half steps (up to 4 levels).  Results are the
+ * same as those of lns_timestep on a model alone (the kernels are deterministic).
+ * --------------------------------------------------------------------------------------- */
+typedef struct lns_server lns_server; /* opaque */
+
+typedef struct {
+  int32_t workers;           /* requests run at once (1..64) */
+  int64_t hbm_budget_bytes;  /* device bytes the resident models may hold; 0: no limit */
+} lns_server_options;
+
+typedef struct {
+  int64_t request_id;        /* as submitted */
+  int32_t model;
+  int32_t status;            /* lns_status of the request */
+  double dt;
+  double t_submit, t_start, t_done;  /* seconds on the server clock (lns_server_now) */
+  lns_step_stats stats;      /* summed over the half steps of any cut; dd_outer = cuts */
+} lns_completion;
+
+typedef struct {
+  int32_t models, resident_models, queued, in_flight;
+  int64_t submitted, completed, failed, admissions, evictions;
+  int64_t resident_bytes;    /* device bytes counted for the resident models */
+  int64_t cell_updates;      /* summed over completed requests */
+} lns_server_stats;
+
+lns_status lns_server_create(const lns_server_options* options, lns_server** out);
+/* Stops the workers after the requests they are running; queued requests are dropped. */
+lns_status lns_server_destroy(lns_server* server);
+/* Registers a model (arrays copied to the host side of the server; validated now, created on
+ * the device at its first request).  opts NULL: lns_options_default. */
+lns_status lns_server_add_model(lns_server* server, const lns_model_desc* desc, const lns_options* opts,
+                                int32_t* model_id);
+lns_status lns_server_submit(lns_server* server, int32_t model_id, double dt, int64_t request_id);
+/* Up to cap completions, waiting up to timeout_s for the first one; *count gets the number. */
+lns_status lns_server_poll(lns_server* server, lns_completion* out, int32_t cap, double timeout_s,
+                           int32_t* count);
+/* Waits until no request is queued or running (LNS_ESTATE after timeout_s). */
+lns_status lns_server_drain(lns_server* server, double timeout_s);
+/* Fields of an idle model (host arrays of n_cells). */
+lns_status lns_server_get_state(lns_server* server, int32_t model_id, double* p, double* sw);
+lns_status lns_server_get_stats(lns_server* server, lns_server_stats* out);
+double lns_server_now(lns_server* server);
 
 /* Number of CUDA kernels the library has launched in this process (all models). */
 int64_t lns_launch_count(void);

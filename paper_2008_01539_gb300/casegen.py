@@ -477,3 +477,18 @@ def batch(cases: Sequence[Case], name: str = "batch") -> Case:
 def ensemble(n_real: int = 256, first: int = 0, **kw) -> Case:
     """The batched ensemble: realizations first .. first+n_real-1 as one union model."""
     return batch([realization(first + r, **kw) for r in range(n_real)], name=f"ensemble{n_real}")
+
+
+def serving_model(index: int, cells: int, dx: float = 5.0) -> Case:
+    """A resident model of about ``cells`` cells for the serving workload: an N x N matrix
+    (N = round(sqrt(cells))) with N * 3/4 natural fractures and two hydraulic fractures on a
+    producer at 1500 psi (seed = ``index``); its timestep sizes come with the requests."""
+    nn = max(20, int(round(math.sqrt(cells))))
+    half = max(3, nn // 10)
+    hf = []
+    for c in (nn // 2 - 2, nn // 2 + 2):
+        x = c * dx + dx / 2
+        hf.append((x, (nn // 2 - half) * dx, x, (nn // 2 + half) * dx, 2 * half))
+    wells = [(i, half, 1500.0 * PSI) for i in range(2)]
+    return dfn_case(nn, nn, dx, (3 * nn) // 4, 20_000 + index, hf=hf, wells=wells,
+                    dts=np.array([DAY]), name=f"serve{index}_{nn}x{nn}")

@@ -32,6 +32,7 @@
 // scalars (computed once per block by thread 0: FP64 division is a long sequence here).
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "lns_internal.cuh"
@@ -922,16 +923,42 @@ int krylov_grid(int fp32, int sms) {
   return a < b ? a : b;
 }
 
+// The solver's blocks fill every SM, so two solves must never be resident at once: launches
+// from different streams (models served concurrently) are chained through one event per device,
+// each waiting for the previous one to finish.
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_coop_mu;
+cudaEvent_t g_coop_ev[kMaxDevices] = {};
+}  // namespace
+
 cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, LaunchCfg c) {
   // barrier counter and timeout flag start from zero in every launch
   cudaError_t e = cudaMemsetAsync(&d.ctr->bar_count, 0, 3 * sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   Dev dd = d;
   void* args[] = {&dd, &rtol, &maxit};
   count_launches(1);
   void* fn = fp32 ? (lines ? (void*)k_bicgstab<float, true> : (void*)k_bicgstab<float, false>)
                   : (lines ? (void*)k_bicgstab<double, true> : (void*)k_bicgstab<double, false>);
-  return cudaLaunchCooperativeKernel(fn, grid, kKryBlk, args, kKrySmem, c.stream);
+  std::lock_guard<std::mutex> lk(g_coop_mu);
+  if (!g_coop_ev[dev]) {
+    e = cudaEventCreateWithFlags(&g_coop_ev[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      g_coop_ev[dev] = nullptr;
+      return e;
+    }
+  } else {
+    e = cudaStreamWaitEvent(c.stream, g_coop_ev[dev], 0);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaLaunchCooperativeKernel(fn, grid, kKryBlk, args, kKrySmem, c.stream);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(g_coop_ev[dev], c.stream);
 }
 
 }  // namespace lns

@@ -546,40 +546,12 @@ lns_status validate_options(const lns_options* o) {
 
 }  // namespace
 
-extern "C" {
+namespace lns {
+lns_status validate_opts(const lns_options* o) { return validate_options(o); }
 
-const char* lns_last_error(void) { return g_err.c_str(); }
-
-int64_t lns_launch_count(void) { return (int64_t)lns::g_launches.load(std::memory_order_relaxed); }
-
-lns_status lns_options_default(lns_options* o) {
-  if (!o) return fail(LNS_EINVAL, "options is NULL");
-  const double psi = 6894.757293168;
-  std::memset(o, 0, sizeof(*o));
-  o->mode = LNS_MODE_LOCAL;
-  o->eps_p = 0.3 * psi;
-  o->eps_sw = 0.0;
-  o->m_layers = 2;
-  o->tol_dp = 0.3 * psi;
-  o->tol_cnv = 1e-6;
-  o->max_newton = 25;
-  o->max_dd_outer = 25;
-  o->sat_chop = 0.2;
-  o->krylov_fp32 = 0;
-  o->precond = LNS_PRECOND_BJAC;
-  o->krylov_rtol = 1e-6;
-  o->krylov_maxit = 2000;
-  o->krylov_fail_rtol = 1e-3;
-  o->p_scale = 0.0;
-  o->profile = 0;
-  return LNS_OK;
-}
-
-lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts, const lns_allocator* allocator,
-                            void* cuda_stream, lns_model** out) {
-  if (!desc || !out) return fail(LNS_EINVAL, "desc and out must be non-NULL");
-  *out = nullptr;
-  TRY(validate_options(opts));
+// Checks of a model description (sizes, arrays, fluid, graph symmetry, wells), on the host.
+lns_status validate_desc(const lns_model_desc* desc) {
+  if (!desc) return fail(LNS_EINVAL, "desc is NULL");
   const int n = desc->n_cells, na = desc->n_adj;
   if (n < 0 || na < 0) return fail(LNS_EINVAL, "negative sizes");
   if (n > 0 && (!desc->row_ptr || !desc->pv_ref || !desc->depth || !desc->line_id || !desc->always_active ||
@@ -618,6 +590,47 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
   for (int w = 0; w < desc->n_wells; w++)
     if (desc->well_cell[w] < 0 || desc->well_cell[w] >= n) return fail(LNS_EINVAL, "well cell out of range");
 
+  return LNS_OK;
+}
+}  // namespace lns
+
+extern "C" {
+
+const char* lns_last_error(void) { return g_err.c_str(); }
+
+int64_t lns_launch_count(void) { return (int64_t)lns::g_launches.load(std::memory_order_relaxed); }
+
+lns_status lns_options_default(lns_options* o) {
+  if (!o) return fail(LNS_EINVAL, "options is NULL");
+  const double psi = 6894.757293168;
+  std::memset(o, 0, sizeof(*o));
+  o->mode = LNS_MODE_LOCAL;
+  o->eps_p = 0.3 * psi;
+  o->eps_sw = 0.0;
+  o->m_layers = 2;
+  o->tol_dp = 0.3 * psi;
+  o->tol_cnv = 1e-6;
+  o->max_newton = 25;
+  o->max_dd_outer = 25;
+  o->sat_chop = 0.2;
+  o->krylov_fp32 = 0;
+  o->precond = LNS_PRECOND_BJAC;
+  o->krylov_rtol = 1e-6;
+  o->krylov_maxit = 2000;
+  o->krylov_fail_rtol = 1e-3;
+  o->p_scale = 0.0;
+  o->profile = 0;
+  return LNS_OK;
+}
+
+lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts, const lns_allocator* allocator,
+                            void* cuda_stream, lns_model** out) {
+  if (!desc || !out) return fail(LNS_EINVAL, "desc and out must be non-NULL");
+  *out = nullptr;
+  TRY(validate_options(opts));
+  TRY(lns::validate_desc(desc));
+  const int n = desc->n_cells, na = desc->n_adj;
+  const lns_fluid& f = desc->fluid;
   lns_model* m = new lns_model();
   m->o = *opts;
   if (allocator && allocator->alloc && allocator->free) {
@@ -824,6 +837,51 @@ lns_status lns_set_state(lns_model* m, const double* p, const double* sw, const 
   m->has_prev = 0;
   m->step_open = false;
   return sync(m);
+}
+
+lns_status lns_set_state_device(lns_model* m, const double* p, const double* sw) {
+  TRY(check_model(m));
+  if (!p || !sw) return fail(LNS_EINVAL, "p and sw must be non-NULL");
+  Dev& d = m->d;
+  const size_t nb = sizeof(double) * (size_t)d.n;
+  if (d.n > 0) {
+    CK(cudaMemcpyAsync(d.p, p, nb, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.sw, sw, nb, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.pn, p, nb, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.swn, sw, nb, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemsetAsync(d.prev, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+  }
+  m->has_prev = 0;
+  m->step_open = false;
+  return sync(m);
+}
+
+lns_status lns_set_support(lns_model* m, const uint32_t* bits) {
+  TRY(check_model(m));
+  if (m->step_open) return fail(LNS_ESTATE, "cannot replace the support inside an open timestep");
+  if (!bits) {
+    if (m->d.W > 0) CK(cudaMemsetAsync(m->d.prev, 0, sizeof(uint32_t) * (size_t)m->d.W, m->stream));
+    m->has_prev = 0;
+    return sync(m);
+  }
+  TRY(bits_to_device(m, m->d.prev, bits));
+  m->has_prev = 1;
+  return sync(m);
+}
+
+lns_status lns_set_stream(lns_model* m, void* cuda_stream) {
+  TRY(check_model(m));
+  cudaStream_t to = (cudaStream_t)cuda_stream;
+  if (to != m->stream) {  // work queued on the old stream comes first (a device-side dependency)
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t r = cudaEventRecord(e, m->stream);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(to, e, 0);
+    cudaEventDestroy(e);
+    CK(r);
+    m->stream = to;
+  }
+  return LNS_OK;
 }
 
 lns_status lns_get_state(const lns_model* cm, double* p, double* sw) {

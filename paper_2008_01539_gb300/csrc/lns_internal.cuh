@@ -100,6 +100,9 @@ struct Dev {
 void count_launches(int k);
 // Message returned by lns_last_error() on the calling thread.
 void set_last_error(const char* msg);
+// Host checks of a model description and of options (lns_model_create runs them first).
+lns_status validate_desc(const lns_model_desc* desc);
+lns_status validate_opts(const lns_options* o);
 
 // ---- launchers (defined in the .cu files) ----
 struct LaunchCfg {

@@ -73,6 +73,23 @@ class lns_step_stats(C.Structure):
                 ("last_max_dp", C.c_double), ("last_cnv", C.c_double)]
 
 
+class lns_server_options(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+
+
+class lns_completion(C.Structure):
+    _fields_ = [("request_id", C.c_int64), ("model", C.c_int32), ("status", C.c_int32), ("dt", C.c_double),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("stats", lns_step_stats)]
+
+
+class lns_server_stats(C.Structure):
+    _fields_ = [("models", C.c_int32), ("resident_models", C.c_int32), ("queued", C.c_int32),
+                ("in_flight", C.c_int32), ("submitted", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("admissions", C.c_int64), ("evictions", C.c_int64),
+                ("resident_bytes", C.c_int64), ("cell_updates", C.c_int64)]
+
+
 class lns_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("total_ms", C.c_double), ("bytes", C.c_double),
                 ("flops", C.c_double)]
@@ -85,9 +102,11 @@ def _as_dict(s: C.Structure) -> Dict:
 _lib = None
 EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_set_options", "lns_timestep",
            "lns_newton_iter", "lns_active_set", "lns_dd_expand", "lns_solve_local", "lns_assemble",
-           "lns_get_state", "lns_set_state", "lns_get_state_device", "lns_reset", "lns_get_support",
-           "lns_kernel_times", "lns_reset_kernel_times", "lns_launch_count", "lns_last_error",
-           "lns_active_set_noalloc"]
+           "lns_get_state", "lns_set_state", "lns_get_state_device", "lns_set_state_device", "lns_set_support",
+           "lns_set_stream", "lns_reset", "lns_get_support", "lns_kernel_times", "lns_reset_kernel_times",
+           "lns_launch_count", "lns_last_error", "lns_active_set_noalloc",
+           "lns_server_create", "lns_server_destroy", "lns_server_add_model", "lns_server_submit",
+           "lns_server_poll", "lns_server_drain", "lns_server_get_state", "lns_server_get_stats", "lns_server_now"]
 
 
 def library_path() -> str:
@@ -121,6 +140,17 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "lns_get_state": [vp, vp, vp],
         "lns_set_state": [vp, vp, vp, vp, vp],
         "lns_get_state_device": [vp, vp, vp],
+        "lns_set_state_device": [vp, vp, vp],
+        "lns_set_support": [vp, vp],
+        "lns_set_stream": [vp, vp],
+        "lns_server_create": [P(lns_server_options), P(vp)],
+        "lns_server_destroy": [vp],
+        "lns_server_add_model": [vp, P(lns_model_desc), P(lns_options), P(i32)],
+        "lns_server_submit": [vp, i32, f64, C.c_int64],
+        "lns_server_poll": [vp, P(lns_completion), i32, f64, P(i32)],
+        "lns_server_drain": [vp, f64],
+        "lns_server_get_state": [vp, i32, vp, vp],
+        "lns_server_get_stats": [vp, P(lns_server_stats)],
         "lns_reset": [vp],
         "lns_get_support": [vp, vp],
         "lns_kernel_times": [vp, P(lns_kernel_time), i32, P(i32)],
@@ -134,6 +164,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     L.lns_last_error.restype = C.c_char_p
     L.lns_launch_count.argtypes = []
     L.lns_launch_count.restype = C.c_int64
+    L.lns_server_now.argtypes = [vp]
+    L.lns_server_now.restype = C.c_double
     L.lns_active_set_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, f64, f64, i32, i32, vp, vp, P(i32), vp]
     L.lns_active_set_noalloc.restype = C.c_int
     _lib = L
@@ -211,6 +243,28 @@ def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
 
 
+def case_desc(case) -> Tuple[lns_model_desc, Dict]:
+    """lns_model_desc of a casegen.Case, and the arrays it points into (keep them alive)."""
+    keep = dict(
+        row_ptr=np.ascontiguousarray(case.row_ptr, np.int32), nbr=np.ascontiguousarray(case.nbr, np.int32),
+        trans=np.ascontiguousarray(case.trans, np.float64), pv_ref=np.ascontiguousarray(case.pv_ref, np.float64),
+        depth=np.ascontiguousarray(case.depth, np.float64), line_id=np.ascontiguousarray(case.line_id, np.int32),
+        always=np.ascontiguousarray(case.always_active, np.uint8),
+        well_cell=np.ascontiguousarray(case.well_cell, np.int32),
+        well_wi=np.ascontiguousarray(case.well_wi, np.float64),
+        well_bhp=np.ascontiguousarray(case.well_bhp, np.float64),
+        p0=np.ascontiguousarray(case.p0, np.float64), sw0=np.ascontiguousarray(case.sw0, np.float64))
+    fl = case.fluid
+    desc = lns_model_desc(
+        int(case.n), int(case.nbr.shape[0]), _ptr(keep["row_ptr"]), _ptr(keep["nbr"]), _ptr(keep["trans"]),
+        _ptr(keep["pv_ref"]), _ptr(keep["depth"]), _ptr(keep["line_id"]), _ptr(keep["always"]),
+        int(case.well_cell.shape[0]), _ptr(keep["well_cell"]), _ptr(keep["well_wi"]), _ptr(keep["well_bhp"]),
+        lns_fluid(fl.p_ref, fl.c_r, fl.b_o_ref, fl.c_o, fl.b_w_ref, fl.c_w, fl.rho_o_ref, fl.rho_w_ref,
+                  fl.mu_o, fl.mu_w, fl.swc, fl.sor, int(fl.n_w), int(fl.n_o), fl.gravity),
+        _ptr(keep["p0"]), _ptr(keep["sw0"]))
+    return desc, keep
+
+
 class Model:
     """A model resident on the GPU (lns_model).  Methods call the C entry points."""
 
@@ -223,23 +277,7 @@ class Model:
         self.n = int(case.n)
         self.n_adj = int(case.nbr.shape[0])
         self.opts = opts or Options()
-        keep = dict(
-            row_ptr=np.ascontiguousarray(case.row_ptr, np.int32), nbr=np.ascontiguousarray(case.nbr, np.int32),
-            trans=np.ascontiguousarray(case.trans, np.float64), pv_ref=np.ascontiguousarray(case.pv_ref, np.float64),
-            depth=np.ascontiguousarray(case.depth, np.float64), line_id=np.ascontiguousarray(case.line_id, np.int32),
-            always=np.ascontiguousarray(case.always_active, np.uint8),
-            well_cell=np.ascontiguousarray(case.well_cell, np.int32),
-            well_wi=np.ascontiguousarray(case.well_wi, np.float64),
-            well_bhp=np.ascontiguousarray(case.well_bhp, np.float64),
-            p0=np.ascontiguousarray(case.p0, np.float64), sw0=np.ascontiguousarray(case.sw0, np.float64))
-        fl = case.fluid
-        desc = lns_model_desc(
-            self.n, self.n_adj, _ptr(keep["row_ptr"]), _ptr(keep["nbr"]), _ptr(keep["trans"]), _ptr(keep["pv_ref"]),
-            _ptr(keep["depth"]), _ptr(keep["line_id"]), _ptr(keep["always"]), int(case.well_cell.shape[0]),
-            _ptr(keep["well_cell"]), _ptr(keep["well_wi"]), _ptr(keep["well_bhp"]),
-            lns_fluid(fl.p_ref, fl.c_r, fl.b_o_ref, fl.c_o, fl.b_w_ref, fl.c_w, fl.rho_o_ref, fl.rho_w_ref,
-                      fl.mu_o, fl.mu_w, fl.swc, fl.sor, int(fl.n_w), int(fl.n_o), fl.gravity),
-            _ptr(keep["p0"]), _ptr(keep["sw0"]))
+        desc, self._keep = case_desc(case)
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         self._alloc = None
         if use_torch_allocator:
@@ -377,3 +415,72 @@ class Model:
 
     def lns_reset_kernel_times(self) -> None:
         _check(load().lns_reset_kernel_times(self.h))
+
+
+class Server:
+    """A request loop over many resident models (lns_server_*): submit 'advance model k by dt'
+    requests from any thread; poll for completions with their timestamps (seconds on the
+    server clock) and step statistics."""
+
+    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblns needs a CUDA GPU")
+        h = C.c_void_p()
+        o = lns_server_options(int(workers), int(hbm_budget_bytes))
+        _check(load().lns_server_create(C.byref(o), C.byref(h)))
+        self.h = h
+        self.n = []
+
+    def add_model(self, case, opts: Optional[Options] = None) -> int:
+        desc, keep = case_desc(case)  # copied by the server during the call
+        oc = (opts or Options()).c()
+        mid = C.c_int32()
+        _check(load().lns_server_add_model(self.h, C.byref(desc), C.byref(oc), C.byref(mid)))
+        del keep
+        self.n.append(int(case.n))
+        return int(mid.value)
+
+    def submit(self, model: int, dt: float, request_id: int) -> None:
+        _check(load().lns_server_submit(self.h, int(model), float(dt), int(request_id)))
+
+    def poll(self, cap: int = 256, timeout_s: float = 0.0) -> List[Dict]:
+        buf = (lns_completion * cap)()
+        cnt = C.c_int32()
+        _check(load().lns_server_poll(self.h, buf, int(cap), float(timeout_s), C.byref(cnt)))
+        out = []
+        for c in buf[: cnt.value]:
+            d = {k: getattr(c, k) for k, _ in c._fields_ if k != "stats"}
+            d["stats"] = _as_dict(c.stats)
+            out.append(d)
+        return out
+
+    def drain(self, timeout_s: float = 600.0) -> None:
+        _check(load().lns_server_drain(self.h, float(timeout_s)))
+
+    def get_state(self, model: int) -> Tuple[np.ndarray, np.ndarray]:
+        n = self.n[model]
+        p = np.empty(n, np.float64)
+        sw = np.empty(n, np.float64)
+        _check(load().lns_server_get_state(self.h, int(model), _ptr(p), _ptr(sw)))
+        return p, sw
+
+    def stats(self) -> Dict:
+        st = lns_server_stats()
+        _check(load().lns_server_get_stats(self.h, C.byref(st)))
+        return _as_dict(st)
+
+    def now(self) -> float:
+        return float(load().lns_server_now(self.h))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().lns_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
