@@ -111,7 +111,8 @@ typedef struct {
   int32_t krylov_maxit;
   double krylov_fail_rtol; /* at krylov_maxit, fail with LNS_EKRYLOV if ||r||/||b|| is above this */
   double p_scale;        /* pressure unknown scaling for the Krylov norm (1/Pa); <= 0: c_r + c_o */
-  int32_t profile;       /* 1: time every kernel class with CUDA events (lns_kernel_times) */
+  int32_t profile;       /* 1: time every kernel class with CUDA events (lns_kernel_times); 2: the
+                          * BiCGStab solves only (one event pair per Newton iteration) */
 } lns_options;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
@@ -226,7 +227,7 @@ lns_status lns_reset(lns_model* model);
  * always-active cells are added). */
 lns_status lns_get_support(const lns_model* model, uint32_t* bits);
 
-/* Kernel timing (options.profile = 1): up to cap entries, *count gets the number. */
+/* Kernel timing (options.profile = 1 or 2): up to cap entries, *count gets the number. */
 lns_status lns_kernel_times(const lns_model* model, lns_kernel_time* out, int32_t cap, int32_t* count);
 lns_status lns_reset_kernel_times(lns_model* model);
 

@@ -26,52 +26,17 @@ namespace lns {
 
 namespace {
 
-constexpr int kAsmBlk = 256;
+constexpr int kAsmBlk = 64;  // small blocks spread the few thousand active rows over all SMs
 
 struct FluidK {
   Fluid f;
   double inv_span, inv_mu[2];
 };
 
-struct Props {
-  double pv, dpv, b[2], db[2], rho[2], drho[2], mob[2], dmob_dp[2], dmob_ds[2];
-};
-
 __device__ __forceinline__ double ipow(double x, int k) {
   double r = 1.0;
   for (int t = 0; t < k; t++) r *= x;
   return r;
-}
-
-__device__ __forceinline__ void cell_props(const FluidK& F, double pv_ref, double p, double sw, Props& q) {
-  const Fluid& f = F.f;
-  const double dpr = p - f.p_ref;
-  q.pv = pv_ref * (1.0 + f.c_r * dpr);
-  q.dpv = pv_ref * f.c_r;
-  q.b[0] = f.b_o_ref * (1.0 + f.c_o * dpr);
-  q.db[0] = f.b_o_ref * f.c_o;
-  q.b[1] = f.b_w_ref * (1.0 + f.c_w * dpr);
-  q.db[1] = f.b_w_ref * f.c_w;
-  q.rho[0] = f.rho_o_ref * q.b[0];
-  q.drho[0] = f.rho_o_ref * q.db[0];
-  q.rho[1] = f.rho_w_ref * q.b[1];
-  q.drho[1] = f.rho_w_ref * q.db[1];
-  double se = (sw - f.swc) * F.inv_span, dse = F.inv_span;
-  if (se <= 0.0) {
-    se = 0.0;
-    dse = 0.0;
-  } else if (se >= 1.0) {
-    se = 1.0;
-    dse = 0.0;
-  }
-  const double kro = ipow(1.0 - se, f.n_o), dkro = -(double)f.n_o * ipow(1.0 - se, f.n_o - 1) * dse;
-  const double krw = ipow(se, f.n_w), dkrw = (double)f.n_w * ipow(se, f.n_w - 1) * dse;
-  q.mob[0] = kro * F.inv_mu[0] * q.b[0];
-  q.dmob_dp[0] = kro * F.inv_mu[0] * q.db[0];
-  q.dmob_ds[0] = dkro * F.inv_mu[0] * q.b[0];
-  q.mob[1] = krw * F.inv_mu[1] * q.b[1];
-  q.dmob_dp[1] = krw * F.inv_mu[1] * q.db[1];
-  q.dmob_ds[1] = dkrw * F.inv_mu[1] * q.b[1];
 }
 
 __device__ __forceinline__ bool bit(const uint32_t* s, int i) { return (s[i >> 5] >> (i & 31)) & 1u; }
@@ -81,128 +46,156 @@ struct alignas(4 * sizeof(T)) Blk4 {
   T a, b, c, d;
 };
 
-// One thread per active row.  Pass 1 evaluates the row's fluxes, accumulation and wells in
-// FP64, writes the raw off-diagonal blocks and marks the row as a boundary cell (V_B: an
-// inactive neighbour); pass 2 scales the row by S D^{-1} in place.
+// Properties of one phase l of a cell and their derivatives, FP64.  (The Jacobian stays FP64 until
+// it is scaled: the diagonal of a pressure row nearly cancels against its off-diagonals, so
+// rounding them separately to FP32 would erase the accumulation term.)
+struct PhaseProps {
+  double b, rho, mob, db, drho, dmob_dp, dmob_ds;
+};
+
+__device__ __forceinline__ PhaseProps phase_props(const FluidK& F, double p, double sw, int l) {
+  const Fluid& f = F.f;
+  const double dpr = p - f.p_ref;
+  const double bref = l ? f.b_w_ref : f.b_o_ref, c = l ? f.c_w : f.c_o, rref = l ? f.rho_w_ref : f.rho_o_ref;
+  PhaseProps q;
+  q.b = bref * (1.0 + c * dpr);
+  const double db = bref * c;
+  q.rho = rref * q.b;
+  q.db = db;
+  q.drho = rref * db;
+  double se = (sw - f.swc) * F.inv_span, dse = F.inv_span;
+  if (se <= 0.0) {
+    se = 0.0;
+    dse = 0.0;
+  } else if (se >= 1.0) {
+    se = 1.0;
+    dse = 0.0;
+  }
+  const int n = l ? f.n_w : f.n_o;
+  const double x = l ? se : 1.0 - se;  // k_rw = Se^n_w, k_ro = (1 - Se)^n_o
+  const double kr = ipow(x, n), dkr = (double)n * ipow(x, n - 1) * (l ? dse : -dse);
+  const double im = F.inv_mu[l];
+  q.mob = kr * im * q.b;
+  q.dmob_dp = kr * im * db;
+  q.dmob_ds = dkr * im * q.b;
+  return q;
+}
+
+// Two lanes per active row, one per phase (l = lane parity: 0 oil, 1 water): each lane evaluates
+// its phase's accumulation, fluxes and well terms (FP64), the pair
+// exchanges its residual and diagonal rows, and both lanes form D^{-1}.  Pass 1 writes each
+// lane's row of the raw off-diagonal blocks (FP64) and marks the row as a boundary cell (V_B: an
+// inactive neighbour); pass 2 scales the blocks by S D^{-1} in place, each lane its own row, the
+// other row coming from its partner by shuffle.  Splitting the phases halves the chain of
+// dependent FP64 instructions a warp issues per row (one FP64 warp instruction per ~64 cycles at
+// most on this GPU), and the rows spread over all SMs.
 template <typename T>
 __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt, double inv_dt, double p_scale,
                                                      double inv_p_scale, int debug) {
   const int nA = d.ctr->n_active;
   const double g = F.f.gravity;
+  const Fluid& f = F.f;
   T* blocks = (T*)d.blocks;
   double* raw = sizeof(T) == sizeof(double) ? (double*)d.blocks : d.raw;
   T* rhs = (T*)d.rhs;
+  const int lane = threadIdx.x & 31, l = lane & 1;
+  const unsigned pm = 3u << (lane & 30);  // this lane pair
   double cnv_max = 0.0;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nA; k += gridDim.x * blockDim.x) {
+  const int pairs = (gridDim.x * blockDim.x) >> 1;
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 1; k < nA; k += pairs) {
     const int i = d.act[k];
     const int e0 = d.row_ptr[i], e1 = d.row_ptr[i + 1];
-    const double p_i = d.p[i], sw_i = d.sw[i], z_i = d.depth[i];
-    Props qi;
-    cell_props(F, d.pv_ref[i], p_i, sw_i, qi);
-    double R0, R1, D00, D01, D10, D11;
+    const double p_i = d.p[i], sw_i = d.sw[i], z_i = d.depth[i], pvr = d.pv_ref[i];
+    const PhaseProps qi = phase_props(F, p_i, sw_i, l);
+    const double pv = pvr * (1.0 + f.c_r * (p_i - f.p_ref)), dpv = pvr * f.c_r;
+    double R, Dp, Ds;  // residual of phase l and row l of the diagonal block (d/dp_i, d/dSw_i)
     {  // accumulation
-      Props qn;
-      const double swn = d.swn[i];
-      cell_props(F, d.pv_ref[i], d.pn[i], swn, qn);
-      const double so = 1.0 - sw_i, son = 1.0 - swn;
-      R0 = (qi.pv * qi.b[0] * so - qn.pv * qn.b[0] * son) * inv_dt;
-      R1 = (qi.pv * qi.b[1] * sw_i - qn.pv * qn.b[1] * swn) * inv_dt;
-      D00 = (qi.dpv * qi.b[0] + qi.pv * qi.db[0]) * so * inv_dt;
-      D01 = -qi.pv * qi.b[0] * inv_dt;
-      D10 = (qi.dpv * qi.b[1] + qi.pv * qi.db[1]) * sw_i * inv_dt;
-      D11 = qi.pv * qi.b[1] * inv_dt;
+      const double pn_i = d.pn[i], swn = d.swn[i];
+      const double pvn = pvr * (1.0 + f.c_r * (pn_i - f.p_ref));
+      const double bn = (l ? f.b_w_ref : f.b_o_ref) * (1.0 + (l ? f.c_w : f.c_o) * (pn_i - f.p_ref));
+      const double S = l ? sw_i : 1.0 - sw_i, Sn = l ? swn : 1.0 - swn;
+      R = (pv * qi.b * S - pvn * bn * Sn) * inv_dt;
+      Dp = (dpv * qi.b + pv * qi.db) * S * inv_dt;
+      Ds = (l ? pv : -pv) * qi.b * inv_dt;
     }
     bool edge = false;
     for (int e = e0; e < e1; e++) {
       const int j = d.nbr[e];
       const double T_e = d.trans[e];
       const double p_j = d.p[j];
-      Props qj;
-      cell_props(F, d.pv_ref[j], p_j, d.sw[j], qj);
+      const PhaseProps qj = phase_props(F, p_j, d.sw[j], l);
       const double dz = z_i - d.depth[j];
-      const double dpp = p_i - p_j;
-      double o[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-      for (int l = 0; l < 2; l++) {
-        const double rho_avg = 0.5 * (qi.rho[l] + qj.rho[l]);
-        const double dphi = dpp - (g * rho_avg) * dz;
-        const bool up_i = dphi > 0.0 || (dphi == 0.0 && i < j);
-        const double tm = T_e * (up_i ? qi.mob[l] : qj.mob[l]);
-        const double rl = tm * dphi;
-        const double dl0 = tm * (1.0 - g * dz * 0.5 * qi.drho[l]);
-        o[2 * l] = tm * (-1.0 - g * dz * 0.5 * qj.drho[l]);
-        double dl0u = 0.0, dl1 = 0.0;
-        if (up_i) {
-          dl0u = T_e * qi.dmob_dp[l] * dphi;
-          dl1 = T_e * qi.dmob_ds[l] * dphi;
-        } else {
-          o[2 * l] += T_e * qj.dmob_dp[l] * dphi;
-          o[2 * l + 1] = T_e * qj.dmob_ds[l] * dphi;
-        }
-        if (l == 0) {
-          R0 += rl;
-          D00 += dl0 + dl0u;
-          D01 += dl1;
-        } else {
-          R1 += rl;
-          D10 += dl0 + dl0u;
-          D11 += dl1;
-        }
+      const double rho_avg = 0.5 * (qi.rho + qj.rho);
+      const double dphi = (p_i - p_j) - (g * rho_avg) * dz;
+      const bool up_i = dphi > 0.0 || (dphi == 0.0 && i < j);
+      const double tm = T_e * (up_i ? qi.mob : qj.mob);
+      R += tm * dphi;
+      const double hgdz = g * dz * 0.5;
+      double o0 = tm * (-1.0 - hgdz * qj.drho), o1 = 0.0;
+      const double dl0 = tm * (1.0 - hgdz * qi.drho);
+      double dl0u = 0.0, dl1 = 0.0;
+      if (up_i) {
+        dl0u = T_e * qi.dmob_dp * dphi;
+        dl1 = T_e * qi.dmob_ds * dphi;
+      } else {
+        o0 += T_e * qj.dmob_dp * dphi;
+        o1 = T_e * qj.dmob_ds * dphi;
       }
+      Dp += dl0 + dl0u;
+      Ds += dl1;
       const bool in = bit(d.va, j);
       edge |= !in;
-      d.colA[e] = in ? d.inv[j] : -1;
+      if (l == 0) d.colA[e] = in ? d.inv[j] : -1;
       if (debug) {
-        d.dbg_off[4 * (size_t)e + 0] = o[0];
-        d.dbg_off[4 * (size_t)e + 1] = o[1];
-        d.dbg_off[4 * (size_t)e + 2] = o[2];
-        d.dbg_off[4 * (size_t)e + 3] = o[3];
+        d.dbg_off[4 * (size_t)e + 2 * l] = o0;
+        d.dbg_off[4 * (size_t)e + 2 * l + 1] = o1;
       }
-      if (in) {  // raw block in FP64 until it is scaled (FP32 rounding before D^{-1} could cancel)
-        Blk4<double> bk = {o[0], o[1], o[2], o[3]};
-        *(Blk4<double>*)&raw[4 * (size_t)e] = bk;
+      if (in) {  // raw row in FP64 until it is scaled
+        raw[4 * (size_t)e + 2 * l] = o0;
+        raw[4 * (size_t)e + 2 * l + 1] = o1;
       }
     }
-    if (edge) atomicOr(&d.vb[i >> 5], 1u << (i & 31));
+    if (edge && l == 0) atomicOr(&d.vb[i >> 5], 1u << (i & 31));
     // producers
     for (int w = d.well_of_cell[i]; w >= 0; w = d.well_next[w]) {
       const double dpw = p_i - d.well_bhp[w];
       if (dpw > 0.0) {
         const double wi = d.well_wi[w];
-        R0 += wi * qi.mob[0] * dpw;
-        R1 += wi * qi.mob[1] * dpw;
-        D00 += wi * (qi.dmob_dp[0] * dpw + qi.mob[0]);
-        D01 += wi * qi.dmob_ds[0] * dpw;
-        D10 += wi * (qi.dmob_dp[1] * dpw + qi.mob[1]);
-        D11 += wi * qi.dmob_ds[1] * dpw;
+        R += wi * qi.mob * dpw;
+        Dp += wi * (qi.dmob_dp * dpw + qi.mob);
+        Ds += wi * qi.dmob_ds * dpw;
       }
     }
+    // the pair's rows: (R0, D00, D01) from lane 0, (R1, D10, D11) from lane 1
+    const double Ro = __shfl_xor_sync(pm, R, 1), bo = __shfl_xor_sync(pm, qi.b, 1);
+    const double Dpo = __shfl_xor_sync(pm, Dp, 1), Dso = __shfl_xor_sync(pm, Ds, 1);
+    const double R0 = l ? Ro : R, R1 = l ? R : Ro;
+    const double D00 = l ? Dpo : Dp, D01 = l ? Dso : Ds;
+    const double D10 = l ? Dp : Dpo, D11 = l ? Ds : Dso;
     const double id = 1.0 / (D00 * D11 - D01 * D10);
     const double I00 = D11 * id, I01 = -D01 * id, I10 = -D10 * id, I11 = D00 * id;
-    rhs[2 * (size_t)k] = (T)(-p_scale * (I00 * R0 + I01 * R1));
-    rhs[2 * (size_t)k + 1] = (T)(-(I10 * R0 + I11 * R1));
-    {  // CNV with one FP64 division: 1/(PV b_l) = b_other / (PV b_o b_w)
-      const double ipbb = dt / (qi.pv * qi.b[0] * qi.b[1]);
-      cnv_max = fmax(cnv_max, fmax(fabs(R0) * qi.b[1] * ipbb, fabs(R1) * qi.b[0] * ipbb));
+    rhs[2 * (size_t)k + l] = l ? (T)(-(I10 * R0 + I11 * R1)) : (T)(-p_scale * (I00 * R0 + I01 * R1));
+    if (l == 0) {  // CNV with one FP64 division: 1/(PV b_l) = b_other / (PV b_o b_w)
+      const double ipbb = dt / (pv * qi.b * bo);
+      cnv_max = fmax(cnv_max, fmax(fabs(R0) * bo * ipbb, fabs(R1) * qi.b * ipbb));
     }
     if (debug) {
-      d.resid[2 * (size_t)i] = R0;
-      d.resid[2 * (size_t)i + 1] = R1;
-      d.dbg_diag[4 * (size_t)i + 0] = D00;
-      d.dbg_diag[4 * (size_t)i + 1] = D01;
-      d.dbg_diag[4 * (size_t)i + 2] = D10;
-      d.dbg_diag[4 * (size_t)i + 3] = D11;
+      d.resid[2 * (size_t)i + l] = R;
+      d.dbg_diag[4 * (size_t)i + 2 * l] = Dp;
+      d.dbg_diag[4 * (size_t)i + 2 * l + 1] = Ds;
     }
-    // pass 2: S D^{-1} O S^{-1} on the blocks of active columns
-    const double sp = p_scale, isp = inv_p_scale;
+    // pass 2: row l of S D^{-1} O S^{-1} on the blocks of active columns (colA of this row was
+    // written by lane 0 of the pair)
+    __syncwarp(pm);
+    const double Il0 = l ? I10 : I00, Il1 = l ? I11 : I01;
     for (int e = e0; e < e1; e++) {
-      if (d.colA[e] < 0) continue;
-      const Blk4<double> bk = *(const Blk4<double>*)&raw[4 * (size_t)e];
-      const double o0 = bk.a, o1 = bk.b, o2 = bk.c, o3 = bk.d;
-      const double m00 = I00 * o0 + I01 * o2, m01 = I00 * o1 + I01 * o3;
-      const double m10 = I10 * o0 + I11 * o2, m11 = I10 * o1 + I11 * o3;
-      Blk4<T> sk = {(T)m00, (T)(m01 * sp), (T)(m10 * isp), (T)m11};
-      *(Blk4<T>*)&blocks[4 * (size_t)e] = sk;
+      if (d.colA[e] < 0) continue;  // same for both lanes
+      const double r0 = raw[4 * (size_t)e + 2 * l], r1 = raw[4 * (size_t)e + 2 * l + 1];  // own row
+      const double q0 = __shfl_xor_sync(pm, r0, 1), q1 = __shfl_xor_sync(pm, r1, 1);  // partner's row
+      const double o00 = l ? q0 : r0, o01 = l ? q1 : r1, o10 = l ? r0 : q0, o11 = l ? r1 : q1;
+      const double m0 = Il0 * o00 + Il1 * o10, m1 = Il0 * o01 + Il1 * o11;
+      blocks[4 * (size_t)e + 2 * l] = l ? (T)(m0 * inv_p_scale) : (T)m0;
+      blocks[4 * (size_t)e + 2 * l + 1] = l ? (T)m1 : (T)(m1 * p_scale);
     }
   }
   // CNV maximum over the block, one atomic per block

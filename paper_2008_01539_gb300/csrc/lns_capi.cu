@@ -55,6 +55,7 @@ const char* kClassName[KC_COUNT] = {"compact", "active_set", "assemble", "line_s
 
 struct PendingEvent {
   int kc;
+  bool on;  // this class is timed at the model's profiling level
   cudaEvent_t a, b;
   double bytes, flops;
 };
@@ -126,7 +127,8 @@ double eff_p_scale(const lns_model* m) {
 lns_status ev_begin(lns_model* m, int kc, PendingEvent* pe) {
   pe->kc = kc;
   pe->bytes = pe->flops = 0.0;
-  if (!m->o.profile) return LNS_OK;
+  pe->on = m->o.profile == 1 || (m->o.profile == 2 && kc == KC_KRYLOV);
+  if (!pe->on) return LNS_OK;
   if (m->ev_pool.size() < 2) {
     for (int k = 0; k < 32; k++) {
       cudaEvent_t e;
@@ -143,7 +145,7 @@ lns_status ev_begin(lns_model* m, int kc, PendingEvent* pe) {
 }
 
 lns_status ev_end(lns_model* m, PendingEvent* pe, double bytes, double flops) {
-  if (!m->o.profile) return LNS_OK;
+  if (!pe->on) return LNS_OK;
   pe->bytes = bytes;
   pe->flops = flops;
   CK(cudaEventRecord(pe->b, m->stream));
