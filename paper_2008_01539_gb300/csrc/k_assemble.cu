@@ -91,7 +91,7 @@ __device__ __forceinline__ PhaseProps phase_props(const FluidK& F, double p, dou
 // most on this GPU), and the rows spread over all SMs.
 template <typename T>
 __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt, double inv_dt, double p_scale,
-                                                     double inv_p_scale, int debug) {
+                                                     double inv_p_scale, int lines, int debug) {
   const int nA = d.ctr->n_active;
   const double g = F.f.gravity;
   const Fluid& f = F.f;
@@ -119,6 +119,10 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt
       Ds = (l ? pv : -pv) * qi.b * inv_dt;
     }
     bool edge = false;
+    // fracture-line links: the couplings to the previous / next cell of the same segment, when that
+    // cell is active too (it is then the previous / next compact row)
+    const int lid_i = lines ? d.line_id[i] : -1;
+    int eprev = -1, enext = -1;
     for (int e = e0; e < e1; e++) {
       const int j = d.nbr[e];
       const double T_e = d.trans[e];
@@ -146,6 +150,12 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt
       const bool in = bit(d.va, j);
       edge |= !in;
       if (l == 0) d.colA[e] = in ? d.inv[j] : -1;
+      if (lid_i >= 0 && in && (j == i - 1 || j == i + 1) && d.line_id[j] == lid_i) {
+        if (j < i)
+          eprev = e;
+        else
+          enext = e;
+      }
       if (debug) {
         d.dbg_off[4 * (size_t)e + 2 * l] = o0;
         d.dbg_off[4 * (size_t)e + 2 * l + 1] = o1;
@@ -156,6 +166,12 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt
       }
     }
     if (edge && l == 0) atomicOr(&d.vb[i >> 5], 1u << (i & 31));
+    if (lines && l == 0) {  // line rows: 2 continues a line, 1 starts one; starts listed in any order
+      d.lnk[k] = make_int2(eprev, enext);
+      const int fl = eprev >= 0 ? 2 : (enext >= 0 ? 1 : 0);
+      d.line_row_flag[k] = fl;
+      if (fl == 1) d.line_start[atomicAdd(&d.ctr->n_line_starts, 1)] = k;
+    }
     // producers
     for (int w = d.well_of_cell[i]; w >= 0; w = d.well_next[w]) {
       const double dpw = p_i - d.well_bhp[w];
@@ -213,39 +229,14 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt
 // ---------------------------------------------------------------------------------------
 // Fracture-line blocks: consecutive compact rows that are consecutive cells of one fracture
 // segment form a block-tridiagonal block of the preconditioner (block Jacobi whose blocks
-// are single cells or whole fracture segments).  Pass 1 marks line rows and lists line
-// starts; pass 2 factors each line in FP32 (block Thomas algorithm; a preconditioner's
-// rounding changes the Krylov convergence rate, not the accuracy of the solution):
+// are single cells or whole fracture segments).  The assembly marks the line rows, links each
+// to its neighbours in the line (CSR entries) and lists the line starts; the factor pass factors
+// each line in FP32 (block Thomas algorithm; a preconditioner's rounding changes the Krylov
+// convergence rate, not the accuracy of the solution):
 //   D'_0 = I, D'_t = I - L_t D'_{t-1}^{-1} U_{t-1},  A_t = -D'_t^{-1} L_t,  G_t = D'_t^{-1} U_t
 // so that M^{-1} r is  w_t = D'_t^{-1} r_t + A_t w_{t-1},  z_t = w_t - G_t z_{t+1}.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ int find_entry(const int* row_ptr, const int* nbr, int i, int j) {
-  for (int e = row_ptr[i]; e < row_ptr[i + 1]; e++)
-    if (nbr[e] == j) return e;
-  return -1;
-}
-
-__global__ void k_line_mark(Dev d) {
-  const int nA = d.ctr->n_active;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nA; k += gridDim.x * blockDim.x) {
-    const int i = d.act[k];
-    const int lid = d.line_id[i];
-    bool cont = false, next = false;
-    if (lid >= 0) {
-      if (k > 0 && d.act[k - 1] == i - 1 && d.line_id[i - 1] == lid)
-        cont = find_entry(d.row_ptr, d.nbr, i, i - 1) >= 0 && find_entry(d.row_ptr, d.nbr, i - 1, i) >= 0;
-      if (k + 1 < nA && d.act[k + 1] == i + 1 && d.line_id[i + 1] == lid)
-        next = find_entry(d.row_ptr, d.nbr, i, i + 1) >= 0 && find_entry(d.row_ptr, d.nbr, i + 1, i) >= 0;
-    }
-    d.line_row_flag[k] = cont ? 2 : (next ? 1 : 0);
-    if (next && !cont) {
-      int pos = atomicAdd(&d.ctr->n_line_starts, 1);
-      d.line_start[pos] = k;
-    }
-  }
-}
-
-// One warp per line.  The lanes find and load the line's coupling blocks (U_t: row t -> t+1,
+// One warp per line.  The lanes load the line's coupling blocks (U_t: row t -> t+1,
 // L_t: row t -> t-1) 32 rows at a time into shared memory, in FP32; lane 0 runs the block
 // Thomas recurrence over the staged rows; the warp stores D'^{-1}, A and G (FP32) per row.
 constexpr int kLineWarps = 4;
@@ -284,13 +275,13 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
       const int t = base + lane;
       float U[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
       if (t < len) {
-        const int i = d.act[k0 + t];
+        const int2 lk = d.lnk[k0 + t];
         if (t + 1 < len && (t + 1) % kMaxLineRows != 0) {
-          const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)find_entry(d.row_ptr, d.nbr, i, i + 1)];
+          const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)lk.y];
           U[0] = (float)b.a, U[1] = (float)b.b, U[2] = (float)b.c, U[3] = (float)b.d;
         }
         if (t >= 1 && t % kMaxLineRows != 0) {
-          const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)find_entry(d.row_ptr, d.nbr, i, i - 1)];
+          const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)lk.x];
           L[0] = (float)b.a, L[1] = (float)b.b, L[2] = (float)b.c, L[3] = (float)b.d;
         }
       }
@@ -364,7 +355,12 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
 
 }  // namespace
 
-cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, int debug, LaunchCfg c) {
+cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, int lines, int debug, LaunchCfg c) {
+  if (lines) {  // the assembly lists the line starts; the factor pass marks the line blocks
+    cudaError_t e = cudaMemsetAsync(&d.ctr->n_lines, 0, 2 * sizeof(int), c.stream);  // n_lines, n_line_starts
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.lblk, 0, sizeof(uint32_t) * (size_t)d.W, c.stream);
+    if (e != cudaSuccess) return e;
+  }
   FluidK F;
   F.f = d.fl;
   F.inv_span = 1.0 / (1.0 - d.fl.swc - d.fl.sor);
@@ -373,24 +369,19 @@ cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, i
   const int grid = 4 * c.sms;
   count_launches(1);
   if (fp32)
-    k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, 1.0 / dt, p_scale, 1.0 / p_scale, debug);
+    k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, 1.0 / dt, p_scale, 1.0 / p_scale, lines, debug);
   else
-    k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, 1.0 / dt, p_scale, 1.0 / p_scale, debug);
+    k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, 1.0 / dt, p_scale, 1.0 / p_scale, lines, debug);
   return cudaGetLastError();
 }
 
 cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c) {
-  cudaError_t e = cudaMemsetAsync(&d.ctr->n_lines, 0, 2 * sizeof(int), c.stream);  // n_lines, n_line_starts
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.lblk, 0, sizeof(uint32_t) * (size_t)d.W, c.stream);
-  if (e != cudaSuccess) return e;
-  count_launches(1);
-  k_line_mark<<<4 * c.sms, 256, 0, c.stream>>>(d);
   count_launches(1);
   if (fp32)
     k_line_factor<float><<<c.sms, 32 * kLineWarps, 0, c.stream>>>(d);
   else
     k_line_factor<double><<<c.sms, 32 * kLineWarps, 0, c.stream>>>(d);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // ascending line-block starts (compact rows < n_active <= n, so the n-bit bitset covers them)
   return launch_compact(d, d.lblk, d.line_start, d.lscratch, &d.ctr->n_lines, c);

@@ -232,9 +232,9 @@ lns_status local_solve(lns_model* m, int debug) {
   TRY(ev_end(m, &pe, d.W * 4.0 * 2 + 0.0, 0.0));
   if (fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
   TRY(ev_begin(m, KC_ASSEMBLE, &pe));
-  CK(lns::launch_assemble(d, m->dt, eff_p_scale(m), fp32, debug, c));
-  TRY(ev_end(m, &pe, 0.0, 0.0));
   const int lines = m->o.precond == LNS_PRECOND_BJAC;
+  CK(lns::launch_assemble(d, m->dt, eff_p_scale(m), fp32, lines, debug, c));
+  TRY(ev_end(m, &pe, 0.0, 0.0));
   if (lines) {
     TRY(ev_begin(m, KC_LINES, &pe));
     CK(lns::launch_line_setup(d, fp32, c));
@@ -717,6 +717,11 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
     AL(d.line_len, N);
     AL(d.lscratch, N);
     AL(d.lblk, W);
+    {
+      int* t2;
+      AL(t2, 2 * N);
+      d.lnk = (int2*)t2;
+    }
     AL(d.line_row_flag, N);
     double** vecs[14] = {(double**)&d.kx,  (double**)&d.kr,   (double**)&d.krh,  (double**)&d.ky0, (double**)&d.ky1,
                          (double**)&d.kv,  (double**)&d.ks,   (double**)&d.kt,   (double**)&d.kz,  (double**)&d.kvt0,
@@ -1090,7 +1095,7 @@ lns_status lns_assemble(lns_model* m, double dt, const uint32_t* va_bits, double
   TRY(reset_iter(m));
   CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, c));
   if (m->o.krylov_fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
-  CK(lns::launch_assemble(d, dt, eff_p_scale(m), m->o.krylov_fp32, 1, c));
+  CK(lns::launch_assemble(d, dt, eff_p_scale(m), m->o.krylov_fp32, 0, 1, c));
   if (F) CK(cudaMemcpyAsync(F, d.resid, sizeof(double) * 2 * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));
   if (Jd) CK(cudaMemcpyAsync(Jd, d.dbg_diag, sizeof(double) * 4 * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));
   if (Jo && d.n_adj > 0)

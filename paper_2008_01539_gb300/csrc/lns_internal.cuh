@@ -87,6 +87,7 @@ struct Dev {
   // starts (after cutting); line_len[k]: rows of the line block starting at compact row k;
   // lblk: bitset of line-block starts; lscratch: compaction scratch
   int *line_start, *line_len, *line_row_flag, *lscratch;
+  int2* lnk;  // per compact row: CSR entries of its couplings to the previous / next row of its line (-1)
   uint32_t* lblk;
   // Krylov vectors
   void *kx, *kr, *krh, *ky0, *ky1, *kv, *ks, *kt, *kz, *kvt0, *kvt1, *krt, *kzf, *ktt;
@@ -134,7 +135,7 @@ cudaError_t launch_halo_check(const Dev& d, const uint32_t* vdb, int since, Laun
 enum WordsOp { kCopy = 0, kOr = 1, kAnd = 2, kAndNot = 3, kAll = 5 };
 
 // k_assemble.cu
-cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, int debug, LaunchCfg c);
+cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, int lines, int debug, LaunchCfg c);
 cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c);
 
 // k_krylov.cu
