@@ -320,9 +320,12 @@ __device__ __forceinline__ typename V2<T>::t row_product(const int* col, const B
 
 // ---- fracture-line solve -----------------------------------------------------------------
 // FP32 block-Thomas recurrences of one 32-row chunk for NR right-hand sides, as inclusive warp
-// scans of 2x2 affine maps.  fwd: w_t = Dinv_t src_t + A_t w_{t-1};  bwd: z_t = w_t - G_t z_{t+1}.
+// scans of 2x2 affine maps, local to the chunk (zero carry-in):
+//   fwd: w_t = Dinv_t src_t + A_t w_{t-1};   bwd: z_t = w_t - G_t z_{t+1}.
+// On return lane t holds c_t and the composite map P_t such that the value of row t is
+// c_t + P_t * (the value entering the chunk).
 template <int NR>
-__device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float> A, const float2 (&carry)[NR], int lane) {
+__device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float>& A, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     M2<float> Ap;
@@ -345,13 +348,10 @@ __device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float> A, const flo
       A = mm(A, Ap);
     }
   }
-#pragma unroll
-  for (int q = 0; q < NR; q++)
-    c[q] = make_float2(c[q].x + A.a * carry[q].x + A.b * carry[q].y, c[q].y + A.c * carry[q].x + A.d * carry[q].y);
 }
 
 template <int NR>
-__device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float> B, const float2 (&carry)[NR], int lane) {
+__device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float>& B, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     M2<float> Bp;
@@ -374,9 +374,11 @@ __device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float> B, const flo
       B = mm(B, Bp);
     }
   }
-#pragma unroll
-  for (int q = 0; q < NR; q++)
-    c[q] = make_float2(c[q].x + B.a * carry[q].x + B.b * carry[q].y, c[q].y + B.c * carry[q].x + B.d * carry[q].y);
+}
+
+// value of a row from its chunk-local scan and the value entering the chunk
+__device__ __forceinline__ float2 apply_carry(float2 c, const M2<float>& P, float2 carry) {
+  return make_float2(c.x + P.a * carry.x + P.b * carry.y, c.y + P.c * carry.x + P.d * carry.y);
 }
 
 // Factors of one line block: row t's D'^{-1}, A and G at fd[t*fs], fa[t*fs], fg[t*fs].
@@ -385,75 +387,92 @@ struct LineFac {
   int fs;
 };
 
+constexpr int kLineChunks = kLineBlockRows / 32;
+
 // M^{-1} on one line block (len <= kLineBlockRows rows) for NR right-hand sides.  Input q of row
-// k0 + t is buf[q * bstride + t] (overwritten by the forward sweep); results are stored to
-// dst[q][k0 + t].  Chunks of 32 rows are swept one after
-// another with the carry passed between them; each lane touches only its own buffer entries.
+// k0 + t is buf[q * bstride + t]; results are stored to dst[q][k0 + t].  The chunks of 32 rows
+// are scanned independently (their shuffle chains overlap), then the values entering each chunk
+// are passed along the chunks: only a 2x2 product per chunk and sweep stays sequential.
 template <typename T, int NR>
-__device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, float2* buf, int bstride,
+__device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, const float2* buf, int bstride,
                                            typename V2<T>::t* const (&dst)[NR]) {
   const int lane = threadIdx.x & 31;
+  float2 w[kLineChunks][NR];
+  M2<float> P[kLineChunks];
+#pragma unroll
+  for (int c = 0; c < kLineChunks; c++) {
+    const int t = c * 32 + lane;
+    P[c] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < NR; q++) w[c][q] = make_float2(0.f, 0.f);
+    if (c * 32 < len) {  // warp-uniform
+      if (t < len) {
+        const float4 Di = f.fd[(size_t)t * f.fs];
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+          const float2 u = buf[q * bstride + t];
+          w[c][q] = make_float2(Di.x * u.x + Di.y * u.y, Di.z * u.x + Di.w * u.y);
+        }
+        const float4 a4 = f.fa[(size_t)t * f.fs];
+        P[c] = {a4.x, a4.y, a4.z, a4.w};
+      }
+      scan_fwd<NR>(w[c], P[c], lane);
+    }
+  }
   float2 carry[NR];
 #pragma unroll
   for (int q = 0; q < NR; q++) carry[q] = make_float2(0.f, 0.f);
-#pragma unroll 1
-  for (int c0 = 0; c0 < len; c0 += 32) {
-    const int t = c0 + lane;
-    M2<float> A = {0.f, 0.f, 0.f, 0.f};
-    float2 w[NR];
 #pragma unroll
-    for (int q = 0; q < NR; q++) w[q] = make_float2(0.f, 0.f);
-    if (t < len) {
-      const float4 Di = f.fd[(size_t)t * f.fs];
+  for (int c = 0; c < kLineChunks; c++)
+    if (c * 32 < len) {
+      const int last = min(31, len - 1 - c * 32);
 #pragma unroll
       for (int q = 0; q < NR; q++) {
-        const float2 u = buf[q * bstride + t];
-        w[q] = make_float2(Di.x * u.x + Di.y * u.y, Di.z * u.x + Di.w * u.y);
+        w[c][q] = apply_carry(w[c][q], P[c], carry[q]);
+        carry[q].x = __shfl_sync(0xffffffffu, w[c][q].x, last);
+        carry[q].y = __shfl_sync(0xffffffffu, w[c][q].y, last);
       }
-      const float4 a4 = f.fa[(size_t)t * f.fs];
-      A = {a4.x, a4.y, a4.z, a4.w};
     }
-    scan_fwd<NR>(w, A, carry, lane);
-    const int last = min(31, len - 1 - c0);
+  // backward sweep: z_t = w_t - G_t z_{t+1}
 #pragma unroll
-    for (int q = 0; q < NR; q++) {
-      if (t < len) buf[q * bstride + t] = w[q];
-      carry[q].x = __shfl_sync(0xffffffffu, w[q].x, last);
-      carry[q].y = __shfl_sync(0xffffffffu, w[q].y, last);
+  for (int c = 0; c < kLineChunks; c++) {
+    const int t = c * 32 + lane;
+    P[c] = {0.f, 0.f, 0.f, 0.f};
+    if (c * 32 < len) {
+      if (t < len) {
+        const float4 g4 = f.fg[(size_t)t * f.fs];
+        P[c] = {-g4.x, -g4.y, -g4.z, -g4.w};
+      } else {
+#pragma unroll
+        for (int q = 0; q < NR; q++) w[c][q] = make_float2(0.f, 0.f);
+      }
+      scan_bwd<NR>(w[c], P[c], lane);
     }
   }
-  __syncwarp();
 #pragma unroll
   for (int q = 0; q < NR; q++) carry[q] = make_float2(0.f, 0.f);
-#pragma unroll 1
-  for (int c0 = ((len - 1) >> 5) << 5; c0 >= 0; c0 -= 32) {
-    const int t = c0 + lane;
-    M2<float> B = {0.f, 0.f, 0.f, 0.f};
-    float2 z[NR];
 #pragma unroll
-    for (int q = 0; q < NR; q++) z[q] = make_float2(0.f, 0.f);
-    if (t < len) {
-      const float4 g4 = f.fg[(size_t)t * f.fs];
-      B = {-g4.x, -g4.y, -g4.z, -g4.w};
+  for (int c = kLineChunks - 1; c >= 0; c--)
+    if (c * 32 < len) {
+      const int t = c * 32 + lane;
 #pragma unroll
-      for (int q = 0; q < NR; q++) z[q] = buf[q * bstride + t];
+      for (int q = 0; q < NR; q++) {
+        const float2 z = apply_carry(w[c][q], P[c], carry[q]);
+        if (t < len) dst[q][k0 + t] = mk<T>((T)z.x, (T)z.y);
+        carry[q].x = __shfl_sync(0xffffffffu, z.x, 0);
+        carry[q].y = __shfl_sync(0xffffffffu, z.y, 0);
+      }
     }
-    scan_bwd<NR>(z, B, carry, lane);
-#pragma unroll
-    for (int q = 0; q < NR; q++) {
-      if (t < len) dst[q][k0 + t] = mk<T>((T)z[q].x, (T)z[q].y);
-      carry[q].x = __shfl_sync(0xffffffffu, z[q].x, 0);
-      carry[q].y = __shfl_sync(0xffffffffu, z[q].y, 0);
-    }
-  }
 }
 
 // ---- grid barrier --------------------------------------------------------------------------
-// All blocks of the (cooperative, hence co-resident) launch add to one counter: block 0 adds
-// 2^31 - (nb - 1), the others 1, so the counter's top bit flips exactly when the last block
-// arrives, and every block waits for the flip of the value it saw when it arrived.  Every wait is
-// bounded: after kBarrierTimeoutNs the block records a timeout and stops waiting, and the kernel
-// ends its loop at the next check (the host reports an error).  Block barriers on both sides.
+// All blocks of the (cooperative, hence co-resident) launch add to one counter (zeroed before the
+// launch): block 0 adds 2^31 - (nb - 1), the others 1, so each barrier adds exactly 2^31 and the
+// counter's top bit flips when the last block arrives; after barrier g it equals g & 1.  The adds
+// are fire-and-forget reductions with release semantics and the waits are acquire loads, so a
+// block pays no round trip for its own arrival.  Every wait is bounded: after kBarrierTimeoutNs
+// the block records a timeout and stops waiting, and the kernel ends its loop at the next check
+// (the host reports an error).  Block barriers on both sides.
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -468,21 +487,24 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ void grid_barrier(IterCounters* ctr, unsigned nb) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// gen: 1 for the first barrier of the launch, 2 for the second, ...
+__device__ __forceinline__ void grid_barrier(IterCounters* ctr, unsigned nb, unsigned gen) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nb - 1u) : 1u;
-    __threadfence();
-    const unsigned old = atomicAdd(&ctr->bar_count, add);
+    red_release_add(&ctr->bar_count, blockIdx.x == 0 ? 0x80000000u - (nb - 1u) : 1u);
+    const unsigned want = (gen & 1u) << 31;
     const unsigned long long t0 = global_ns();
     unsigned k = 0;
-    while (((old ^ ld_acquire(&ctr->bar_count)) & 0x80000000u) == 0u) {
+    while ((ld_acquire(&ctr->bar_count) & 0x80000000u) != want) {
       if ((++k & 63u) == 0u && global_ns() - t0 > kBarrierTimeoutNs) {
         atomicExch(&ctr->bar_timeout, 1);
         break;
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
@@ -563,6 +585,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   const int nb = gridDim.x;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nlines = LINES ? d.ctr->n_lines : 0;
+  unsigned bar_gen = 0;  // grid barriers passed so far
   V* const x = (V*)d.kx;
   V* const r = (V*)d.kr;
   V* const rh = (V*)d.krh;
@@ -714,7 +737,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     line_solve<T, 1>(k0, len, f, buf, bstride, dst);
   });
   block_store_f64(l_bb, sh, part, nb);
-  grid_barrier(d.ctr, nb);
+  grid_barrier(d.ctr, nb, ++bar_gen);
   const bool timed_out = *(volatile int*)&d.ctr->bar_timeout;
   const double bb = grid_sum_f64(part, nb);
   // Dots are scaled by an exact power of two near 1/bb before they are carried in double-float,
@@ -797,7 +820,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       const DF vals[2] = {to_df(l_rv), to_df(l_rr)};
       block_store<2>(vals, busy, s_df, part, kSlotS1, nb);
     }
-    grid_barrier(d.ctr, nb);
+    grid_barrier(d.ctr, nb, ++bar_gen);
     {
       DF o[2];
       grid_sum<2>(part, kSlotS1, nb, o);
@@ -866,7 +889,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       const DF vals[4] = {to_df(l_ts), to_df(l_tt), to_df(l_rs), to_df(l_rt)};
       block_store<4>(vals, busy, s_df, part, kSlotS2, nb);
     }
-    grid_barrier(d.ctr, nb);
+    grid_barrier(d.ctr, nb, ++bar_gen);
     {
       DF o[4];
       grid_sum<4>(part, kSlotS2, nb, o);
