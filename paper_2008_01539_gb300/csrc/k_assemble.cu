@@ -90,9 +90,10 @@ __device__ __forceinline__ PhaseProps phase_props(const FluidK& F, double p, dou
 // dependent FP64 instructions a warp issues per row (one FP64 warp instruction per ~64 cycles at
 // most on this GPU), and the rows spread over all SMs.
 template <typename T>
-__global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double dt, double inv_dt, double p_scale,
-                                                     double inv_p_scale, int lines, int debug) {
+__global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double p_scale, double inv_p_scale, int lines,
+                                                     int debug) {
   const int nA = d.ctr->n_active;
+  const double dt = d.stepp[0], inv_dt = d.stepp[1];
   const double g = F.f.gravity;
   const Fluid& f = F.f;
   T* blocks = (T*)d.blocks;
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
 
 }  // namespace
 
-cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, int lines, int debug, LaunchCfg c) {
+cudaError_t launch_assemble(const Dev& d, double p_scale, int fp32, int lines, int debug, LaunchCfg c) {
   if (lines) {  // the assembly lists the line starts; the factor pass marks the line blocks
     cudaError_t e = cudaMemsetAsync(&d.ctr->n_lines, 0, 2 * sizeof(int), c.stream);  // n_lines, n_line_starts
     if (e == cudaSuccess) e = cudaMemsetAsync(d.lblk, 0, sizeof(uint32_t) * (size_t)d.W, c.stream);
@@ -369,9 +370,9 @@ cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, i
   const int grid = 4 * c.sms;
   count_launches(1);
   if (fp32)
-    k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, 1.0 / dt, p_scale, 1.0 / p_scale, lines, debug);
+    k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, p_scale, 1.0 / p_scale, lines, debug);
   else
-    k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, dt, 1.0 / dt, p_scale, 1.0 / p_scale, lines, debug);
+    k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, p_scale, 1.0 / p_scale, lines, debug);
   return cudaGetLastError();
 }
 

@@ -968,6 +968,11 @@ cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int 
   count_launches(1);
   void* fn = fp32 ? (lines ? (void*)k_bicgstab<float, true> : (void*)k_bicgstab<float, false>)
                   : (lines ? (void*)k_bicgstab<double, true> : (void*)k_bicgstab<double, false>);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(c.stream, &cap);
+  if (e != cudaSuccess) return e;
+  if (cap != cudaStreamCaptureStatusNone)  // captured into a model's graph: ordered by its own stream
+    return cudaLaunchCooperativeKernel(fn, grid, kKryBlk, args, kKrySmem, c.stream);
   std::lock_guard<std::mutex> lk(g_coop_mu);
   if (!g_coop_ev[dev]) {
     e = cudaEventCreateWithFlags(&g_coop_ev[dev], cudaEventDisableTiming);

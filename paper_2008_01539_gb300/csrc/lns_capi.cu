@@ -55,7 +55,8 @@ const char* kClassName[KC_COUNT] = {"compact", "active_set", "assemble", "line_s
 
 struct PendingEvent {
   int kc;
-  bool on;  // this class is timed at the model's profiling level
+  bool on;    // this class is timed at the model's profiling level
+  bool keep;  // the events belong to a captured graph (not returned to the pool)
   cudaEvent_t a, b;
   double bytes, flops;
 };
@@ -84,6 +85,15 @@ struct lns_model {
   std::vector<uint32_t*> dd_va, dd_vb, dd_vdb;
   uint32_t* dd_vt = nullptr;
   std::vector<uint32_t> stage;  // host staging of caller bitsets
+  // dt of the current solve, in device memory (d.stepp) via a pinned staging pair
+  double* dt_host = nullptr;
+  double dt_dev = -1.0;
+  // one Newton iteration captured as a CUDA graph (single-stream models without profiling)
+  bool graph_ok = true;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_kernels = 0;
+  std::vector<PendingEvent> graph_pending;  // event pairs recorded by the graph (profile level 2)
   // profiling
   std::vector<cudaEvent_t> ev_pool;
   std::vector<PendingEvent> pending;
@@ -93,6 +103,31 @@ struct lns_model {
 namespace {
 
 LaunchCfg cfg(const lns_model* m) { return LaunchCfg{m->sms, m->stream}; }
+
+// dt and 1/dt of the next solves to the device (only when dt changes; the previous upload of the
+// pinned pair has completed: every solve ends with a stream synchronization)
+lns_status set_dt(lns_model* m, double dt) {
+  m->dt = dt;
+  if (dt == m->dt_dev) return LNS_OK;
+  m->dt_host[0] = dt;
+  m->dt_host[1] = 1.0 / dt;
+  cudaError_t e = cudaMemcpyAsync(m->d.stepp, m->dt_host, 2 * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+  if (e != cudaSuccess) return fail(LNS_ECUDA, std::string("dt upload: ") + cudaGetErrorString(e));
+  m->dt_dev = dt;
+  return LNS_OK;
+}
+
+void drop_graph(lns_model* m) {
+  if (m->gexec) cudaGraphExecDestroy(m->gexec);
+  if (m->graph) cudaGraphDestroy(m->graph);
+  m->gexec = nullptr;
+  m->graph = nullptr;
+  for (auto& pe : m->graph_pending) {
+    m->ev_pool.push_back(pe.a);
+    m->ev_pool.push_back(pe.b);
+  }
+  m->graph_pending.clear();
+}
 
 lns_status dalloc(lns_model* m, size_t bytes, void** out) {
   bytes = std::max<size_t>(bytes, 256);
@@ -124,9 +159,20 @@ double eff_p_scale(const lns_model* m) {
 }
 
 // ---- profiling ----
+// Record an event on the model's stream; under stream capture as an external event-record node,
+// so that every launch of the graph records it (a plain record would only order the capture).
+cudaError_t record(lns_model* m, cudaEvent_t e) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t r = cudaStreamIsCapturing(m->stream, &cap);
+  if (r != cudaSuccess) return r;
+  if (cap != cudaStreamCaptureStatusNone) return cudaEventRecordWithFlags(e, m->stream, cudaEventRecordExternal);
+  return cudaEventRecord(e, m->stream);
+}
+
 lns_status ev_begin(lns_model* m, int kc, PendingEvent* pe) {
   pe->kc = kc;
   pe->bytes = pe->flops = 0.0;
+  pe->keep = false;
   pe->on = m->o.profile == 1 || (m->o.profile == 2 && kc == KC_KRYLOV);
   if (!pe->on) return LNS_OK;
   if (m->ev_pool.size() < 2) {
@@ -140,7 +186,7 @@ lns_status ev_begin(lns_model* m, int kc, PendingEvent* pe) {
   m->ev_pool.pop_back();
   pe->b = m->ev_pool.back();
   m->ev_pool.pop_back();
-  CK(cudaEventRecord(pe->a, m->stream));
+  CK(record(m, pe->a));
   return LNS_OK;
 }
 
@@ -148,7 +194,7 @@ lns_status ev_end(lns_model* m, PendingEvent* pe, double bytes, double flops) {
   if (!pe->on) return LNS_OK;
   pe->bytes = bytes;
   pe->flops = flops;
-  CK(cudaEventRecord(pe->b, m->stream));
+  CK(record(m, pe->b));
   m->pending.push_back(*pe);
   return LNS_OK;
 }
@@ -163,8 +209,10 @@ lns_status ev_flush(lns_model* m) {
     k.total_ms += ms;
     k.bytes += pe.bytes;
     k.flops += pe.flops;
-    m->ev_pool.push_back(pe.a);
-    m->ev_pool.push_back(pe.b);
+    if (!pe.keep) {
+      m->ev_pool.push_back(pe.a);
+      m->ev_pool.push_back(pe.b);
+    }
   }
   m->pending.clear();
   return LNS_OK;
@@ -233,7 +281,7 @@ lns_status local_solve(lns_model* m, int debug) {
   if (fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
   TRY(ev_begin(m, KC_ASSEMBLE, &pe));
   const int lines = m->o.precond == LNS_PRECOND_BJAC;
-  CK(lns::launch_assemble(d, m->dt, eff_p_scale(m), fp32, lines, debug, c));
+  CK(lns::launch_assemble(d, eff_p_scale(m), fp32, lines, debug, c));
   TRY(ev_end(m, &pe, 0.0, 0.0));
   if (lines) {
     TRY(ev_begin(m, KC_LINES, &pe));
@@ -322,7 +370,7 @@ lns_status open_step(lns_model* m, double dt) {
   Dev& d = m->d;
   LaunchCfg c = cfg(m);
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(LNS_EINVAL, "dt must be positive and finite");
-  m->dt = dt;
+  TRY(set_dt(m, dt));
   CK(cudaMemcpyAsync(d.pn, d.p, sizeof(double) * (size_t)d.n, cudaMemcpyDeviceToDevice, m->stream));
   CK(cudaMemcpyAsync(d.swn, d.sw, sizeof(double) * (size_t)d.n, cudaMemcpyDeviceToDevice, m->stream));
   if (m->o.mode == LNS_MODE_FULL) {
@@ -346,8 +394,10 @@ lns_status close_step(lns_model* m) {
   return LNS_OK;
 }
 
-// One pass of Algorithm 1 lines 4-21 (or of standard Newton).
-lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
+// The device work of one pass of Algorithm 1 lines 4-21 (or of standard Newton), ending with the
+// read-back of the counter block.  Every size is read on the device, so the same sequence serves
+// every iteration of every timestep.
+lns_status enqueue_iteration(lns_model* m) {
   Dev& d = m->d;
   LaunchCfg c = cfg(m);
   const bool local = m->o.mode == LNS_MODE_LOCAL;
@@ -366,6 +416,62 @@ lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
     TRY(ev_end(m, &pe, 0.0, 0.0));
   }
   CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+  return LNS_OK;
+}
+
+// Capture enqueue_iteration once as a CUDA graph (one launch per Newton iteration instead of a
+// dozen kernels, memsets and copies).  Used when nothing in the sequence needs the host: no
+// profiling events, no multi-chunk expansion (m <= 8 layers is one launch), one stream.  A
+// capture that fails leaves the model on the direct path.
+lns_status ensure_graph(lns_model* m) {
+  if (m->gexec) return LNS_OK;
+  const int64_t before = lns::g_launches.load(std::memory_order_relaxed);
+  cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    m->graph_ok = false;
+    cudaGetLastError();
+    return LNS_OK;
+  }
+  lns_status r = enqueue_iteration(m);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(m->stream, &g);
+  if (r != LNS_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    m->graph_ok = false;
+    return LNS_OK;
+  }
+  e = cudaGraphInstantiate(&m->gexec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    m->gexec = nullptr;
+    m->graph_ok = false;
+    return LNS_OK;
+  }
+  m->graph = g;
+  m->graph_kernels = lns::g_launches.load(std::memory_order_relaxed) - before;
+  lns::count_launches((int)-m->graph_kernels);  // nothing ran during the capture
+  m->graph_pending = m->pending;  // event pairs now recorded by every launch of the graph
+  for (auto& pe : m->graph_pending) pe.keep = true;
+  m->pending.clear();
+  return LNS_OK;
+}
+
+// One pass of Algorithm 1 lines 4-21 (or of standard Newton).
+lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
+  Dev& d = m->d;
+  const bool local = m->o.mode == LNS_MODE_LOCAL;
+  if (m->o.krylov_fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
+  const bool graph = m->graph_ok && m->o.profile != 1 && m->o.m_layers <= 8;
+  if (graph) TRY(ensure_graph(m));
+  if (graph && m->gexec) {
+    CK(cudaGraphLaunch(m->gexec, m->stream));
+    lns::count_launches((int)m->graph_kernels);
+    m->pending = m->graph_pending;
+  } else {
+    TRY(enqueue_iteration(m));
+  }
   CK(cudaStreamSynchronize(m->stream));
   annotate_pending(m);
   TRY(ev_flush(m));
@@ -731,9 +837,14 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
     AL(d.partials, (size_t)8 * 4 * m->sms + 64);
   }
   AL(d.ctr, 1);
+  AL(d.stepp, 2);
 #undef AL
   if (cudaMallocHost((void**)&d.ctr_h, sizeof(IterCounters)) != cudaSuccess) {
     d.ctr_h = nullptr;
+    return cleanup_fail(fail(LNS_ENOMEM, "cudaMallocHost failed"));
+  }
+  if (cudaMallocHost((void**)&m->dt_host, 2 * sizeof(double)) != cudaSuccess) {
+    m->dt_host = nullptr;
     return cleanup_fail(fail(LNS_ENOMEM, "cudaMallocHost failed"));
   }
   // host-side derived tables
@@ -790,6 +901,8 @@ lns_status lns_model_destroy(lns_model* m) {
       cudaFree(p);
   }
   if (m->d.ctr_h) cudaFreeHost(m->d.ctr_h);
+  if (m->dt_host) cudaFreeHost(m->dt_host);
+  drop_graph(m);
   for (auto e : m->ev_pool) cudaEventDestroy(e);
   for (auto& pe : m->pending) {
     cudaEventDestroy(pe.a);
@@ -804,6 +917,7 @@ lns_status lns_set_options(lns_model* m, const lns_options* o) {
   TRY(validate_options(o));
   if (m->step_open && o->mode != m->o.mode) return fail(LNS_ESTATE, "cannot change mode inside an open timestep");
   m->o = *o;
+  drop_graph(m);  // captured with the old options
   return LNS_OK;
 }
 
@@ -887,6 +1001,10 @@ lns_status lns_set_stream(lns_model* m, void* cuda_stream) {
     cudaEventDestroy(e);
     CK(r);
     m->stream = to;
+    // a model that moves between streams may run beside other models: its solver launches go
+    // through the cross-stream chain, which a captured graph would bypass
+    drop_graph(m);
+    m->graph_ok = false;
   }
   return LNS_OK;
 }
@@ -1048,7 +1166,7 @@ lns_status lns_solve_local(lns_model* m, double dt, const uint32_t* va_bits, dou
   Dev& d = m->d;
   LaunchCfg c = cfg(m);
   if (d.n == 0) return LNS_OK;
-  m->dt = dt;
+  TRY(set_dt(m, dt));
   const size_t nb = sizeof(double) * (size_t)d.n;
   TRY(bits_to_device(m, d.va, va_bits));
   TRY(reset_iter(m));
@@ -1090,12 +1208,12 @@ lns_status lns_assemble(lns_model* m, double dt, const uint32_t* va_bits, double
   CK(cudaMemsetAsync(d.resid, 0, sizeof(double) * 2 * (size_t)d.n, m->stream));
   CK(cudaMemsetAsync(d.dbg_diag, 0, sizeof(double) * 4 * (size_t)d.n, m->stream));
   CK(cudaMemsetAsync(d.dbg_off, 0, sizeof(double) * 4 * (size_t)std::max(d.n_adj, 1), m->stream));
-  m->dt = dt;
+  TRY(set_dt(m, dt));
   TRY(bits_to_device(m, d.va, va_bits));
   TRY(reset_iter(m));
   CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, c));
   if (m->o.krylov_fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
-  CK(lns::launch_assemble(d, dt, eff_p_scale(m), m->o.krylov_fp32, 0, 1, c));
+  CK(lns::launch_assemble(d, eff_p_scale(m), m->o.krylov_fp32, 0, 1, c));
   if (F) CK(cudaMemcpyAsync(F, d.resid, sizeof(double) * 2 * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));
   if (Jd) CK(cudaMemcpyAsync(Jd, d.dbg_diag, sizeof(double) * 4 * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));
   if (Jo && d.n_adj > 0)

@@ -95,6 +95,8 @@ struct Dev {
   double* partials;
   IterCounters* ctr;   // device
   IterCounters* ctr_h; // pinned host mirror
+  double* stepp;       // device [2]: dt and 1/dt of the current solve (read by the assembly, so a
+                       // captured Newton iteration needs no parameter change between timesteps)
 };
 
 // Process-wide count of kernels launched by the library (lns_launch_count).
@@ -135,7 +137,7 @@ cudaError_t launch_halo_check(const Dev& d, const uint32_t* vdb, int since, Laun
 enum WordsOp { kCopy = 0, kOr = 1, kAnd = 2, kAndNot = 3, kAll = 5 };
 
 // k_assemble.cu
-cudaError_t launch_assemble(const Dev& d, double dt, double p_scale, int fp32, int lines, int debug, LaunchCfg c);
+cudaError_t launch_assemble(const Dev& d, double p_scale, int fp32, int lines, int debug, LaunchCfg c);
 cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c);
 
 // k_krylov.cu

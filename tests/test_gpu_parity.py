@@ -320,3 +320,32 @@ def test_config1_first_steps_match_oracle(big):
     assert np.max(np.abs(p - ref.p) / ref.p) < 1e-7
     assert np.max(np.abs(sw - ref.sw)) < 1e-7 * 0.25
     g.close()
+
+
+# ---------------------------------------------------------------------------------------
+# The captured Newton iteration (CUDA graph, models on a stream of their own) computes exactly
+# what the direct launches compute (legacy default stream, no capture).
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_iteration_matches_direct_launches(mode, fp32):
+    import torch
+
+    case = cg.small_dfn(40, 33, 14, seed=11, n_steps=5)
+    opts = lns.Options(mode=mode, krylov_fp32=fp32, krylov_rtol=1e-5 if fp32 else 1e-8)
+    direct = lns.Model(case, opts, stream=torch.cuda.default_stream())
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        graphed = lns.Model(case, opts, stream=s)
+        n0 = lns.lns_launch_count()
+        for dt in case.dt_schedule:
+            a = graphed.lns_timestep(dt)
+            b = direct.lns_timestep(dt)
+            assert (a["iterations"], a["krylov_iters"], a["cell_updates"]) == \
+                (b["iterations"], b["krylov_iters"], b["cell_updates"])
+        assert lns.lns_launch_count() > n0
+        pg, swg = graphed.lns_get_state()
+    pd, swd = direct.lns_get_state()
+    assert np.array_equal(pg, pd) and np.array_equal(swg, swd)
+    graphed.close()
+    direct.close()
