@@ -45,7 +45,7 @@ typedef enum {
   LNS_ECUDA = -3,    /* a CUDA runtime call or kernel failed (message in lns_last_error) */
   LNS_ENOCONV = -4,  /* Newton loop reached max_newton (or Algorithm 2 max_dd_outer) */
   LNS_EKRYLOV = -5,  /* BiCGStab broke down or reached krylov_maxit above krylov_fail_rtol */
-  LNS_ETIMEOUT = -6, /* reserved: a bounded device-side wait gave up */
+  LNS_ETIMEOUT = -6, /* a bounded device-side wait gave up (the solver grid barrier, 2 s) */
   LNS_ESTATE = -7    /* call not valid in the model's current state */
 } lns_status;
 
@@ -219,6 +219,11 @@ lns_status lns_set_state_device(lns_model* model, const double* p, const double*
  * to restore a model saved with lns_get_support/lns_get_state so that its next timestep starts
  * from the same active set as it would have. */
 lns_status lns_set_support(lns_model* model, const uint32_t* bits);
+/* Failure injection for tests of the device-side error paths (no GPU fault is involved):
+ * code 1 makes the solver's first grid barrier miss one block's arrival, so every bounded wait of
+ * that barrier runs out (2 s) and the next solve returns LNS_ETIMEOUT with the context intact;
+ * code 2 starts BiCGStab with rho = 0, a breakdown (LNS_EKRYLOV); 0 clears the fault. */
+lns_status lns_debug_fault(lns_model* model, int32_t code);
 /* Move the model to another CUDA stream (after the work queued on the current one finishes). */
 lns_status lns_set_stream(lns_model* model, void* cuda_stream);
 /* Return to the initial state (p0, sw0) without host transfers; forget the support. */
@@ -292,7 +297,7 @@ typedef struct {
 
 typedef struct {
   int32_t models, resident_models, queued, in_flight;
-  int64_t submitted, completed, failed, admissions, evictions;
+  int64_t submitted, completed, failed, cancelled, admissions, evictions;
   int64_t resident_bytes;    /* device bytes counted for the resident models */
   int64_t cell_updates;      /* summed over completed requests */
 } lns_server_stats;
@@ -305,6 +310,9 @@ lns_status lns_server_destroy(lns_server* server);
 lns_status lns_server_add_model(lns_server* server, const lns_model_desc* desc, const lns_options* opts,
                                 int32_t* model_id);
 lns_status lns_server_submit(lns_server* server, int32_t model_id, double dt, int64_t request_id);
+/* Cancel a queued request: it completes at once with status LNS_ESTATE and its model is unchanged.
+ * LNS_ESTATE if the request is not queued (unknown, already running or finished). */
+lns_status lns_server_cancel(lns_server* server, int64_t request_id);
 /* Up to cap completions, waiting up to timeout_s for the first one; *count gets the number. */
 lns_status lns_server_poll(lns_server* server, lns_completion* out, int32_t cap, double timeout_s,
                            int32_t* count);

@@ -492,10 +492,11 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 }
 
 // gen: 1 for the first barrier of the launch, 2 for the second, ...
-__device__ __forceinline__ void grid_barrier(IterCounters* ctr, unsigned nb, unsigned gen) {
+// skip: this block does not arrive (injected fault: every wait of this barrier then runs out)
+__device__ __forceinline__ void grid_barrier(IterCounters* ctr, unsigned nb, unsigned gen, bool skip = false) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    red_release_add(&ctr->bar_count, blockIdx.x == 0 ? 0x80000000u - (nb - 1u) : 1u);
+    if (!skip) red_release_add(&ctr->bar_count, blockIdx.x == 0 ? 0x80000000u - (nb - 1u) : 1u);
     const unsigned want = (gen & 1u) << 31;
     const unsigned long long t0 = global_ns();
     unsigned k = 0;
@@ -736,8 +737,10 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     V* const dst[1] = {zf};
     line_solve<T, 1>(k0, len, f, buf, bstride, dst);
   });
+  // injected faults (failure tests): 1 = block 0 never arrives at this barrier, 2 = rho_1 = 0
+  const int fault = *d.fault;
   block_store_f64(l_bb, sh, part, nb);
-  grid_barrier(d.ctr, nb, ++bar_gen);
+  grid_barrier(d.ctr, nb, ++bar_gen, fault == 1 && blockIdx.x == 0);
   const bool timed_out = *(volatile int*)&d.ctr->bar_timeout;
   const double bb = grid_sum_f64(part, nb);
   // Dots are scaled by an exact power of two near 1/bb before they are carried in double-float,
@@ -760,7 +763,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   sc_zero(stop2);
   sc_zero(rr_last);
   if (threadIdx.x == 0) {  // thread 0 tracks the scalars
-    rho = sc_from(df_from(bb * dscale), S{});
+    rho = sc_from(df_from(fault == 2 ? 0.0 : bb * dscale), S{});
     stop2 = sc_from(df_from(rtol * rtol * bb * dscale), S{});
     sc_zero(s_sc[0]);  // beta_1
     sc_zero(s_sc[1]);  // alpha_0

@@ -15,6 +15,8 @@
 
 #include <atomic>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lns_internal.cuh"
 
 namespace {
@@ -317,7 +319,7 @@ void annotate_pending(lns_model* m) {
 lns_status krylov_outcome(lns_model* m) {
   const IterCounters& h = *m->d.ctr_h;
   if (h.krylov_status == 2) return fail(LNS_EKRYLOV, "BiCGStab breakdown");
-  if (h.krylov_status == 3) return fail(LNS_EKRYLOV, "BiCGStab grid barrier wait timed out");
+  if (h.krylov_status == 3) return fail(LNS_ETIMEOUT, "BiCGStab grid barrier wait gave up (bounded wait ran out)");
   if (h.krylov_status == 1 && !(h.krylov_relres <= m->o.krylov_fail_rtol))
     return fail(LNS_EKRYLOV, "BiCGStab reached krylov_maxit with relative residual " + std::to_string(h.krylov_relres));
   return LNS_OK;
@@ -697,6 +699,13 @@ lns_status validate_desc(const lns_model_desc* desc) {
   }
   for (int w = 0; w < desc->n_wells; w++)
     if (desc->well_cell[w] < 0 || desc->well_cell[w] >= n) return fail(LNS_EINVAL, "well cell out of range");
+  for (int i = 0; i < n; i++)
+    if (!std::isfinite(desc->p0[i]) || !std::isfinite(desc->sw0[i]) || !(desc->pv_ref[i] > 0.0) ||
+        !std::isfinite(desc->pv_ref[i]) || !std::isfinite(desc->depth[i]))
+      return fail(LNS_EINVAL, "non-finite initial state or cell data (cell " + std::to_string(i) + ")");
+  for (int e = 0; e < na; e++)
+    if (!std::isfinite(desc->trans[e]) || desc->trans[e] < 0.0)
+      return fail(LNS_EINVAL, "transmissibilities must be finite and >= 0");
 
   return LNS_OK;
 }
@@ -838,6 +847,7 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
   }
   AL(d.ctr, 1);
   AL(d.stepp, 2);
+  AL(d.fault, 1);
 #undef AL
   if (cudaMallocHost((void**)&d.ctr_h, sizeof(IterCounters)) != cudaSuccess) {
     d.ctr_h = nullptr;
@@ -847,6 +857,8 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
     m->dt_host = nullptr;
     return cleanup_fail(fail(LNS_ENOMEM, "cudaMallocHost failed"));
   }
+  if (cudaMemsetAsync(d.fault, 0, sizeof(int), m->stream) != cudaSuccess)
+    return cleanup_fail(fail(LNS_ECUDA, "cannot clear the fault flag"));
   // host-side derived tables
   std::vector<int> woc(N, -1), wnext(NW, -1), alist;
   for (int w = desc->n_wells - 1; w >= 0; w--) {
@@ -940,6 +952,9 @@ lns_status lns_reset(lns_model* m) {
 lns_status lns_set_state(lns_model* m, const double* p, const double* sw, const double* pn, const double* swn) {
   TRY(check_model(m));
   if (!p || !sw) return fail(LNS_EINVAL, "p and sw must be non-NULL");
+  for (int i = 0; i < m->d.n; i++)
+    if (!std::isfinite(p[i]) || !std::isfinite(sw[i]) || (pn && !std::isfinite(pn[i])) || (swn && !std::isfinite(swn[i])))
+      return fail(LNS_EINVAL, "non-finite state value (cell " + std::to_string(i) + ")");
   Dev& d = m->d;
   const size_t nb = sizeof(double) * (size_t)d.n;
   if (d.n > 0) {
@@ -987,6 +1002,13 @@ lns_status lns_set_support(lns_model* m, const uint32_t* bits) {
   }
   TRY(bits_to_device(m, m->d.prev, bits));
   m->has_prev = 1;
+  return sync(m);
+}
+
+lns_status lns_debug_fault(lns_model* m, int32_t code) {
+  TRY(check_model(m));
+  if (code < 0 || code > 2) return fail(LNS_EINVAL, "fault code must be 0, 1 or 2");
+  CK(cudaMemcpyAsync(m->d.fault, &code, sizeof(int), cudaMemcpyHostToDevice, m->stream));
   return sync(m);
 }
 
@@ -1039,8 +1061,14 @@ lns_status lns_get_support(const lns_model* cm, uint32_t* bits) {
   return sync(m);
 }
 
+struct NvtxRange {  // a named range on the profiler's timeline (no-op without a tool attached)
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 lns_status lns_newton_iter(lns_model* m, double dt, lns_iter_stats* out) {
   TRY(check_model(m));
+  NvtxRange range("lns_newton_iter");
   if (m->o.mode == LNS_MODE_DD) return fail(LNS_ESTATE, "lns_newton_iter is not available in LNS_MODE_DD");
   if (m->d.n == 0) return fail(LNS_EINVAL, "empty model");
   if (!m->step_open) TRY(open_step(m, dt));
@@ -1069,6 +1097,7 @@ lns_status lns_newton_iter(lns_model* m, double dt, lns_iter_stats* out) {
 
 lns_status lns_timestep(lns_model* m, double dt, lns_step_stats* out) {
   TRY(check_model(m));
+  NvtxRange range("lns_timestep");
   if (m->d.n == 0) {
     if (out) std::memset(out, 0, sizeof(*out));
     return LNS_OK;

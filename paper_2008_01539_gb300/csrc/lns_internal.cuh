@@ -97,6 +97,7 @@ struct Dev {
   IterCounters* ctr_h; // pinned host mirror
   double* stepp;       // device [2]: dt and 1/dt of the current solve (read by the assembly, so a
                        // captured Newton iteration needs no parameter change between timesteps)
+  int* fault;          // device: injected fault of the solver for failure tests (0: none)
 };
 
 // Process-wide count of kernels launched by the library (lns_launch_count).

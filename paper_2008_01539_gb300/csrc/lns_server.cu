@@ -427,6 +427,27 @@ lns_status lns_server_submit(lns_server* s, int32_t model, double dt, int64_t re
   return LNS_OK;
 }
 
+lns_status lns_server_cancel(lns_server* s, int64_t request_id) {
+  if (!s) return fail(LNS_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+    if (q->id == request_id) {
+      lns_completion c{};
+      c.request_id = q->id;
+      c.model = q->model;
+      c.dt = q->dt;
+      c.status = LNS_ESTATE;  // cancelled before it started; the model is unchanged
+      c.t_submit = q->t_submit;
+      c.t_start = c.t_done = s->now();
+      s->queue.erase(q);
+      s->done.push_back(c);
+      s->st.cancelled++;
+      s->cv_done.notify_all();
+      return LNS_OK;
+    }
+  return fail(LNS_ESTATE, "request is not queued (unknown, running or finished)");
+}
+
 lns_status lns_server_poll(lns_server* s, lns_completion* out, int32_t cap, double timeout_s, int32_t* count) {
   if (!s || !count || (cap > 0 && !out)) return fail(LNS_EINVAL, "bad arguments");
   std::unique_lock<std::mutex> lk(s->mu);

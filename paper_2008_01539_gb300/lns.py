@@ -86,7 +86,7 @@ class lns_completion(C.Structure):
 class lns_server_stats(C.Structure):
     _fields_ = [("models", C.c_int32), ("resident_models", C.c_int32), ("queued", C.c_int32),
                 ("in_flight", C.c_int32), ("submitted", C.c_int64), ("completed", C.c_int64),
-                ("failed", C.c_int64), ("admissions", C.c_int64), ("evictions", C.c_int64),
+                ("failed", C.c_int64), ("cancelled", C.c_int64), ("admissions", C.c_int64), ("evictions", C.c_int64),
                 ("resident_bytes", C.c_int64), ("cell_updates", C.c_int64)]
 
 
@@ -106,7 +106,8 @@ EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_
            "lns_set_stream", "lns_reset", "lns_get_support", "lns_kernel_times", "lns_reset_kernel_times",
            "lns_launch_count", "lns_last_error", "lns_active_set_noalloc",
            "lns_server_create", "lns_server_destroy", "lns_server_add_model", "lns_server_submit",
-           "lns_server_poll", "lns_server_drain", "lns_server_get_state", "lns_server_get_stats", "lns_server_now"]
+           "lns_server_poll", "lns_server_drain", "lns_server_get_state", "lns_server_get_stats", "lns_server_now",
+           "lns_server_cancel", "lns_debug_fault"]
 
 
 def library_path() -> str:
@@ -147,6 +148,8 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "lns_server_destroy": [vp],
         "lns_server_add_model": [vp, P(lns_model_desc), P(lns_options), P(i32)],
         "lns_server_submit": [vp, i32, f64, C.c_int64],
+        "lns_server_cancel": [vp, C.c_int64],
+        "lns_debug_fault": [vp, i32],
         "lns_server_poll": [vp, P(lns_completion), i32, f64, P(i32)],
         "lns_server_drain": [vp, f64],
         "lns_server_get_state": [vp, i32, vp, vp],
@@ -407,6 +410,18 @@ class Model:
         _check(load().lns_get_support(self.h, _ptr(bits)))
         return bits_to_mask(bits, self.n)
 
+    def lns_set_support(self, bits: Optional[np.ndarray]) -> None:
+        """Restore the previous timestep's support (bitset words, e.g. mask_to_bits of
+        lns_get_support); None forgets it."""
+        if bits is None:
+            _check(load().lns_set_support(self.h, None))
+            return
+        b = np.ascontiguousarray(bits, np.uint32)
+        _check(load().lns_set_support(self.h, _ptr(b)))
+
+    def lns_set_state_device(self, p_ptr: int, sw_ptr: int) -> None:
+        _check(load().lns_set_state_device(self.h, C.c_void_p(p_ptr), C.c_void_p(sw_ptr)))
+
     def lns_kernel_times(self) -> List[Dict]:
         arr = (lns_kernel_time * 16)()
         cnt = C.c_int32(0)
@@ -415,6 +430,10 @@ class Model:
 
     def lns_reset_kernel_times(self) -> None:
         _check(load().lns_reset_kernel_times(self.h))
+
+    def lns_debug_fault(self, code: int) -> None:
+        """Inject a solver fault for failure tests (1: a barrier wait runs out, 2: breakdown; 0: none)."""
+        _check(load().lns_debug_fault(self.h, int(code)))
 
 
 class Server:
@@ -444,6 +463,10 @@ class Server:
 
     def submit(self, model: int, dt: float, request_id: int) -> None:
         _check(load().lns_server_submit(self.h, int(model), float(dt), int(request_id)))
+
+    def cancel(self, request_id: int) -> bool:
+        """Cancel a queued request; False if it is not queued (running, finished or unknown)."""
+        return load().lns_server_cancel(self.h, int(request_id)) == LNS_OK
 
     def poll(self, cap: int = 256, timeout_s: float = 0.0) -> List[Dict]:
         buf = (lns_completion * cap)()

@@ -1,0 +1,112 @@
+"""Failure paths on the GPU, none of which faults or hangs the device: a bounded device-side wait
+that runs out (LNS_ETIMEOUT, context still usable), a forced BiCGStab breakdown, non-finite inputs,
+checkpoint and resume (bit-identical), and a cancelled serving request."""
+import numpy as np
+import pytest
+
+from paper_2008_01539_gb300 import casegen as cg
+from paper_2008_01539_gb300 import lns
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need cuda:0"
+    lns.load(build_if_missing=True)
+
+
+def _run(case, opts, dts, model=None):
+    m = model or lns.Model(case, opts)
+    for dt in dts:
+        m.lns_timestep(float(dt))
+    return m
+
+
+def test_barrier_wait_runs_out_with_etimeout_and_the_context_survives():
+    case = cg.config0()
+    m = lns.Model(case, lns.Options(mode=1))
+    m.lns_debug_fault(1)  # one block never arrives at the solver's first grid barrier
+    with pytest.raises(lns.LnsError) as e:
+        m.lns_timestep(case.dt_schedule[0])
+    assert e.value.status == lns.LNS_ETIMEOUT
+    m.lns_debug_fault(0)
+    m.lns_reset()
+    _run(case, None, case.dt_schedule[:3], m)
+    ref = _run(case, lns.Options(mode=1), case.dt_schedule[:3])
+    assert np.array_equal(m.lns_get_state()[0], ref.lns_get_state()[0])
+    m.close()
+    ref.close()
+
+
+def test_forced_breakdown_is_reported():
+    case = cg.config0()
+    m = lns.Model(case, lns.Options(mode=1))
+    m.lns_debug_fault(2)
+    with pytest.raises(lns.LnsError) as e:
+        m.lns_timestep(case.dt_schedule[0])
+    assert e.value.status == lns.LNS_EKRYLOV
+    m.close()
+
+
+def test_non_finite_inputs_are_rejected():
+    case = cg.config0()
+    m = lns.Model(case)
+    p = case.p0.copy()
+    p[7] = np.nan
+    with pytest.raises(lns.LnsError) as e:
+        m.lns_set_state(p, case.sw0)
+    assert e.value.status == lns.LNS_EINVAL
+    m.close()
+    bad = cg.config0()
+    bad.sw0 = bad.sw0.copy()
+    bad.sw0[3] = np.inf
+    with pytest.raises(lns.LnsError):
+        lns.Model(bad)
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_checkpoint_and_resume_is_bit_identical(fp32):
+    case = cg.small_dfn(40, 33, 14, seed=11, n_steps=6)
+    opts = lns.Options(mode=1, krylov_fp32=fp32, krylov_rtol=1e-5 if fp32 else 1e-6)
+    whole = _run(case, opts, case.dt_schedule)
+    first = _run(case, opts, case.dt_schedule[:3])
+    p, sw = first.lns_get_state()
+    supp = lns.mask_to_bits(first.lns_get_support())
+    first.close()
+    resumed = lns.Model(case, opts)
+    resumed.lns_set_state(p, sw)
+    resumed.lns_set_support(supp)
+    _run(case, opts, case.dt_schedule[3:], resumed)
+    pw, sww = whole.lns_get_state()
+    pr, swr = resumed.lns_get_state()
+    assert np.array_equal(pw, pr) and np.array_equal(sww, swr)
+    whole.close()
+    resumed.close()
+
+
+def test_cancelled_request_leaves_its_model_unchanged():
+    cases = [cg.config0(), cg.small_dfn(24, 20, 6, seed=7, n_steps=4)]
+    opts = lns.Options(mode=1)
+    srv = lns.Server(workers=1)
+    ids = [srv.add_model(c, opts) for c in cases]
+    # one worker: the first request runs while the others wait in the queue
+    srv.submit(ids[0], 5.0 * cg.DAY, 0)
+    srv.submit(ids[1], 1.0 * cg.DAY, 1)
+    srv.submit(ids[1], 2.0 * cg.DAY, 2)
+    cancelled = srv.cancel(1)
+    srv.drain()
+    done = {c["request_id"]: c for c in srv.poll(16, 1.0)}
+    assert set(done) == {0, 1, 2}
+    if cancelled:
+        assert done[1]["status"] == lns.LNS_ESTATE
+        ref = _run(cases[1], opts, [2.0 * cg.DAY])
+    else:  # the worker had already taken it
+        assert done[1]["status"] == 0
+        ref = _run(cases[1], opts, [1.0 * cg.DAY, 2.0 * cg.DAY])
+    assert np.array_equal(srv.get_state(ids[1])[0], ref.lns_get_state()[0])
+    assert not srv.cancel(0)  # finished requests cannot be cancelled
+    srv.close()
+    ref.close()
