@@ -113,6 +113,9 @@ typedef struct {
   double p_scale;        /* pressure unknown scaling for the Krylov norm (1/Pa); <= 0: c_r + c_o */
   int32_t profile;       /* 1: time every kernel class with CUDA events (lns_kernel_times); 2: the
                           * BiCGStab solves only (one event pair per Newton iteration) */
+  int32_t fp64_fallback; /* with krylov_fp32: an FP32 solve that breaks down or stops above
+                          * krylov_fail_rtol is redone in FP64 within the same Newton iteration
+                          * (a failed solve changes neither the state nor V_A).  Default 1. */
 } lns_options;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
@@ -131,6 +134,8 @@ typedef struct {
   int32_t step_done;     /* the timestep closed after this iteration */
   int32_t krylov_iters;
   int32_t krylov_status; /* 0 ok, 1 max iterations, 2 breakdown, 3 grid barrier wait timed out */
+  int32_t fp64_retry;    /* 1: the FP32 solve failed and this iteration's solve was redone in FP64
+                          * (krylov_iters counts both solves; status/relres are the FP64 solve's) */
   double max_dp, max_dsw, cnv, krylov_relres;
 } lns_iter_stats;
 
@@ -140,6 +145,7 @@ typedef struct {
   int32_t krylov_iters;  /* summed over iterations */
   int32_t n_subdomains;  /* Algorithm 2: N */
   int32_t dd_outer;      /* Algorithm 2: outer passes */
+  int32_t fp64_retries;  /* iterations whose FP32 solve was redone in FP64 (fp64_fallback) */
   int64_t cell_updates;  /* sum of n_A over iterations */
   double last_max_dp, last_cnv;
 } lns_step_stats;
@@ -222,7 +228,8 @@ lns_status lns_set_support(lns_model* model, const uint32_t* bits);
 /* Failure injection for tests of the device-side error paths (no GPU fault is involved):
  * code 1 makes the solver's first grid barrier miss one block's arrival, so every bounded wait of
  * that barrier runs out (2 s) and the next solve returns LNS_ETIMEOUT with the context intact;
- * code 2 starts BiCGStab with rho = 0, a breakdown (LNS_EKRYLOV); 0 clears the fault. */
+ * code 2 starts BiCGStab with rho = 0, a breakdown (LNS_EKRYLOV); code 3 does so in FP32 solves
+ * only (exercises fp64_fallback); 0 clears the fault. */
 lns_status lns_debug_fault(lns_model* model, int32_t code);
 /* Move the model to another CUDA stream (after the work queued on the current one finishes). */
 lns_status lns_set_stream(lns_model* model, void* cuda_stream);

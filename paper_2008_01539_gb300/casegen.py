@@ -492,3 +492,141 @@ def serving_model(index: int, cells: int, dx: float = 5.0) -> Case:
     wells = [(i, half, 1500.0 * PSI) for i in range(2)]
     return dfn_case(nn, nn, dx, (3 * nn) // 4, 20_000 + index, hf=hf, wells=wells,
                     dts=np.array([DAY]), name=f"serve{index}_{nn}x{nn}")
+
+
+# ---------------------------------------------------------------------------------------
+# 3D: a layered matrix with vertical planar fractures (the large HBM-resident case)
+# ---------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class _Panel:
+    """A vertical planar fracture: horizontal trace (x0, y0)-(x1, y1) over layers [k0, k1)."""
+    x0: float
+    y0: float
+    x1: float
+    y1: float
+    k0: int
+    k1: int
+    n_cells: int  # cells along the trace
+    k_f: float
+    w: float
+
+
+def _add_matrix_3d(b: _Builder, nx: int, ny: int, nz: int, dx: float, dy: float, dz: float, perm: np.ndarray,
+                   poro: float, top: float) -> np.ndarray:
+    n = nx * ny * nz
+    depth = top + (np.arange(nz) + 0.5) * dz
+    ids = b.add_cells(np.full(n, dx * dy * dz * poro), np.repeat(depth, nx * ny))
+    k = perm.reshape(nz, ny, nx)
+    idx = ids.reshape(nz, ny, nx)
+    for axis, area_over_d in ((2, dy * dz / dx), (1, dx * dz / dy), (0, dx * dy / dz)):
+        sl_a = [slice(None)] * 3
+        sl_b = [slice(None)] * 3
+        sl_a[axis] = slice(None, -1)
+        sl_b[axis] = slice(1, None)
+        k1, k2 = k[tuple(sl_a)], k[tuple(sl_b)]
+        b.connect(idx[tuple(sl_a)], idx[tuple(sl_b)], area_over_d * 2.0 * k1 * k2 / (k1 + k2))
+    return ids
+
+
+def _add_panels(b: _Builder, panels: Sequence[_Panel], nx: int, ny: int, dx: float, dy: float, dz: float,
+                k_m: np.ndarray, top: float) -> List[np.ndarray]:
+    """Each panel is a grid of pieces (along the trace x layers).  Pieces are numbered column by
+    column, so each vertical column of a panel is one fracture line (consecutive ids, the strongest
+    coupling when L > dz); pieces connect to the piece above and below, to the neighbouring column
+    in the same layer, and to the matrix cell holding their centre.  Panels that cross do not
+    exchange flow directly (they meet through the matrix).  Returns ids[layer, piece] per panel."""
+    d_avg = (dx + dy) / 8.0
+    out = []
+    for s in panels:
+        L = math.hypot(s.x1 - s.x0, s.y1 - s.y0) / s.n_cells
+        nl = s.k1 - s.k0
+        tmid = (np.arange(s.n_cells) + 0.5) / s.n_cells
+        ix = np.clip(np.floor((s.x0 + tmid * (s.x1 - s.x0)) / dx).astype(np.int64), 0, nx - 1)
+        iy = np.clip(np.floor((s.y0 + tmid * (s.y1 - s.y0)) / dy).astype(np.int64), 0, ny - 1)
+        cols = []
+        for a in range(s.n_cells):
+            line = b.n_lines
+            b.n_lines += 1
+            ids = b.add_cells(np.full(nl, L * s.w * dz), top + (np.arange(s.k0, s.k1) + 0.5) * dz, line=line)
+            if nl > 1:
+                b.connect(ids[:-1], ids[1:], s.k_f * s.w * L / dz)
+            mcell = (np.arange(s.k0, s.k1) * ny + iy[a]) * nx + ix[a]
+            b.connect(ids, mcell, 2.0 * L * dz * k_m[mcell] / d_avg)
+            if cols:
+                b.connect(cols[-1], ids, s.k_f * s.w * dz / L)
+            cols.append(ids)
+        out.append(np.stack(cols, axis=1))  # [layer, piece]
+    return out
+
+
+def dfn3d_case(nx: int, ny: int, nz: int, dx: float, dz: float, n_nf: int, seed: int, *,
+               hf: Sequence[Tuple[float, float, float, int, int, int]] = (),
+               wells: Sequence[Tuple[int, int, int, float]] = (), k_mean_md: float = 1e-4, k_sigma: float = 0.5,
+               poro: float = 0.06, hf_k_md: float = 1e4, hf_w: float = 0.01, nf_k_md: float = 1e3,
+               nf_w: float = 0.001, nf_len: Tuple[float, float] = (20.0, 200.0), nf_layers: Tuple[int, int] = (2, 10),
+               strikes: Tuple[Tuple[float, float], ...] = ((30.0, 10.0), (120.0, 10.0)), top: float = 2500.0,
+               p_top: float = 5000.0 * PSI, sw_init: float = 0.25, dts: Optional[np.ndarray] = None,
+               name: str = "dfn3d") -> Case:
+    """nx x ny x nz matrix of dx x dx x dz cells (depth grows with the layer index), hydraulic
+    fractures ``hf`` = (x, y0, y1, k0, k1, n_cells) as vertical planes at constant x, and ``n_nf``
+    seeded natural fractures as vertical panels over U(nf_layers) layers; ``wells`` lists
+    (hf index, piece along the trace, layer offset, BHP) producers.  The initial pressure follows
+    the oil gradient from p_top at the top (near equilibrium with the dominant phase)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    fluid = Fluid(p_ref=p_top)
+    b = _Builder()
+    perm = _lognormal_perm(rng, nx * ny * nz, k_mean_md, k_sigma)
+    _add_matrix_3d(b, nx, ny, nz, dx, dx, dz, perm, poro, top)
+    n_matrix = b.n
+    Lx, Ly = nx * dx, ny * dx
+    panels = [_Panel(x, y0, x, y1, k0, k1, nc, hf_k_md * MD, hf_w) for (x, y0, y1, k0, k1, nc) in hf]
+    for s_i in range(n_nf):
+        mean, half = strikes[s_i % len(strikes)]
+        ang = math.radians(mean + rng.uniform(-half, half))
+        L = rng.uniform(*nf_len)
+        cx, cy = rng.uniform(0, Lx), rng.uniform(0, Ly)
+        ux, uy = math.cos(ang) * L / 2, math.sin(ang) * L / 2
+        x0 = min(max(cx - ux, 1e-6), Lx - 1e-6)
+        x1 = min(max(cx + ux, 1e-6), Lx - 1e-6)
+        y0 = min(max(cy - uy, 1e-6), Ly - 1e-6)
+        y1 = min(max(cy + uy, 1e-6), Ly - 1e-6)
+        length = math.hypot(x1 - x0, y1 - y0)
+        if length < 0.5 * dx:
+            continue
+        hgt = int(rng.integers(nf_layers[0], nf_layers[1] + 1))
+        k0 = int(rng.integers(0, max(1, nz - hgt + 1)))
+        panels.append(_Panel(x0, y0, x1, y1, k0, min(nz, k0 + hgt), max(1, int(round(length / dx))),
+                             nf_k_md * MD, nf_w))
+    ids = _add_panels(b, panels, nx, ny, dx, dx, dz, perm, top)
+    for (h, piece, layer, bhp) in wells:
+        s = panels[h]
+        b.wells.append((int(ids[h][layer, piece]), _peaceman_wi(s.k_f, s.w, dz, dx), bhp))
+    dts = dts if dts is not None else geometric_schedule(20, 180.0)
+    case = _finish(b, name, fluid, p_top, sw_init, dts, n_matrix,
+                   dict(nx=nx, ny=ny, nz=nz, dx=dx, dz=dz, n_panels=len(panels), n_hf=len(hf)))
+    case.p0 = p_top + fluid.rho_o_ref * GRAVITY * (case.depth - top)
+    return case
+
+
+def config2(seed: int = 2) -> Case:
+    """200 x 200 x 20 matrix of 5 x 5 x 2 m cells, 10 hydraulic-fracture stages (planes of 40 x 12
+    cells) on a horizontal producer at 1500 psi along x through the centre, and 2000 natural
+    fractures as vertical panels; oil-water (the black-oil variant of this geometry is not built)."""
+    nx = ny = 200
+    nz, dx, dz = 20, 5.0, 2.0
+    yc = ny * dx / 2
+    hf = []
+    for s in range(10):
+        x = (30 + 15 * s) * dx + dx / 2
+        hf.append((x, yc - 20 * dx, yc + 20 * dx, 4, 16, 40))
+    wells = [(s, 20, 6, 1500.0 * PSI) for s in range(10)]
+    return dfn3d_case(nx, ny, nz, dx, dz, 2000, seed, hf=hf, wells=wells, name="config2_200x200x20_dfn2000_oilwater")
+
+
+def small_dfn3d(nx: int = 10, ny: int = 8, nz: int = 3, n_nf: int = 3, seed: int = 5, n_steps: int = 5) -> Case:
+    """A few-hundred-cell 3D model (one hydraulic fracture with a producer, a few panels) for tests."""
+    dx, dz = 5.0, 2.0
+    hf = [((nx // 2) * dx + dx / 2, 1.0 * dx, (ny - 1) * dx, 0, nz, ny - 2)]
+    return dfn3d_case(nx, ny, nz, dx, dz, n_nf, seed, hf=hf, wells=[(0, (ny - 2) // 2, nz // 2, 1500.0 * PSI)],
+                      nf_len=(3 * dx, 6 * dx), nf_layers=(1, nz), dts=doubling_schedule(n_steps),
+                      name=f"small3d_{nx}x{ny}x{nz}")

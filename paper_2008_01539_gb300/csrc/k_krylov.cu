@@ -737,7 +737,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     V* const dst[1] = {zf};
     line_solve<T, 1>(k0, len, f, buf, bstride, dst);
   });
-  // injected faults (failure tests): 1 = block 0 never arrives at this barrier, 2 = rho_1 = 0
+  // injected faults (failure tests): 1 = block 0 never arrives at this barrier, 2 = rho_1 = 0,
+  // 3 = rho_1 = 0 in FP32 solves only
   const int fault = *d.fault;
   block_store_f64(l_bb, sh, part, nb);
   grid_barrier(d.ctr, nb, ++bar_gen, fault == 1 && blockIdx.x == 0);
@@ -763,7 +764,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   sc_zero(stop2);
   sc_zero(rr_last);
   if (threadIdx.x == 0) {  // thread 0 tracks the scalars
-    rho = sc_from(df_from(fault == 2 ? 0.0 : bb * dscale), S{});
+    rho = sc_from(df_from(fault == 2 || (fault == 3 && sizeof(T) == 4) ? 0.0 : bb * dscale), S{});
     stop2 = sc_from(df_from(rtol * rtol * bb * dscale), S{});
     sc_zero(s_sc[0]);  // beta_1
     sc_zero(s_sc[1]);  // alpha_0

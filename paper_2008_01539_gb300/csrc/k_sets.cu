@@ -158,9 +158,16 @@ __global__ void k_flag(Dev d, const uint32_t* __restrict__ vb, int apply, int re
   __shared__ double sh[32];
   const double inv_p_scale = 1.0 / p_scale;  // once per thread, outside the row loop
   int nA = d.ctr->n_active;
-  // a failed Krylov solve (breakdown, or stopped far from the tolerance) is not scattered
-  if (x && apply && (d.ctr->krylov_status == 2 || (d.ctr->krylov_status == 1 && !(d.ctr->krylov_relres <= fail_rtol))))
-    apply = 0;
+  // A failed Krylov solve (breakdown, a barrier wait that gave up, or a stop far from the
+  // tolerance) changes nothing: no update, no support, no frontier, so the iteration can be
+  // redone from the same state and set.
+  if (x && apply) {
+    const int st = d.ctr->krylov_status;
+    if (st == 2 || st == 3 || (st == 1 && !(d.ctr->krylov_relres <= fail_rtol))) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) d.ctr->solve_failed = 1;
+      return;
+    }
+  }
   double mdp = 0.0, mds = 0.0;
   int any_s = 0, any_e = 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nA; k += gridDim.x * blockDim.x) {
@@ -247,12 +254,13 @@ __global__ void k_alg1_combine(Dev d, double tol_dp, double tol_cnv, int converg
   double cnv = __longlong_as_double((long long)c->cnv_bits);
   int conv = converged_override >= 0 ? converged_override : (maxdp < tol_dp && cnv < tol_cnv);
   int any_e = c->any_e, any_s = c->any_s;
+  const int failed = c->solve_failed;  // V_A stays as it was for a redo of the iteration
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w == 0) {
-    c->converged = conv;
-    c->is_expand = any_e ? 1 : 0;
+    c->converged = failed ? 0 : conv;
+    c->is_expand = failed ? 0 : (any_e ? 1 : 0);
   }
-  if (w >= d.W) return;
+  if (w >= d.W || failed) return;
   uint32_t va = d.va[w];
   d.uni[w] |= va;
   if (any_e)

@@ -460,6 +460,22 @@ lns_status ensure_graph(lns_model* m) {
   return LNS_OK;
 }
 
+// An FP32 solve that failed numerically (not a barrier wait that gave up) and left the state
+// and V_A untouched is redone in FP64 when the options ask for it.
+bool wants_fp64_retry(const lns_model* m) {
+  const IterCounters& h = *m->d.ctr_h;
+  return m->o.krylov_fp32 && m->o.fp64_fallback && h.solve_failed && h.krylov_status != 3;
+}
+
+// Run `body` with the FP64 Krylov path (direct launches), then restore the FP32 option.
+template <typename F>
+lns_status with_fp64_krylov(lns_model* m, F body) {
+  m->o.krylov_fp32 = 0;
+  const lns_status r = body();
+  m->o.krylov_fp32 = 1;
+  return r;
+}
+
 // One pass of Algorithm 1 lines 4-21 (or of standard Newton).
 lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
   Dev& d = m->d;
@@ -478,11 +494,23 @@ lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
   annotate_pending(m);
   TRY(ev_flush(m));
   const IterCounters& h = *d.ctr_h;
+  int retry = 0, kit_fp32 = 0;
+  if (wants_fp64_retry(m)) {
+    retry = 1;
+    kit_fp32 = h.krylov_iters;
+    TRY(with_fp64_krylov(m, [&]() -> lns_status {
+      TRY(enqueue_iteration(m));
+      CK(cudaStreamSynchronize(m->stream));
+      annotate_pending(m);
+      return ev_flush(m);
+    }));
+    m->cur.fp64_retries += 1;
+  }
   const double maxdp = bits2d(h.max_dp_bits), cnv = bits2d(h.cnv_bits);
   m->converged = local ? h.converged : (maxdp < m->o.tol_dp && cnv < m->o.tol_cnv);
   m->is_expand = local ? h.is_expand : 0;
   m->cur.iterations += 1;
-  m->cur.krylov_iters += h.krylov_iters;
+  m->cur.krylov_iters += kit_fp32 + h.krylov_iters;
   m->cur.cell_updates += h.n_active;
   m->cur.last_max_dp = maxdp;
   m->cur.last_cnv = cnv;
@@ -490,8 +518,9 @@ lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
     st->n_active = h.n_active;
     st->is_expand = m->is_expand;
     st->converged = m->converged;
-    st->krylov_iters = h.krylov_iters;
+    st->krylov_iters = kit_fp32 + h.krylov_iters;
     st->krylov_status = h.krylov_status;
+    st->fp64_retry = retry;
     st->krylov_relres = h.krylov_relres;
     st->max_dp = maxdp;
     st->max_dsw = bits2d(h.max_dsw_bits);
@@ -523,26 +552,35 @@ lns_status dd_ensure(lns_model* m, size_t k) {
 lns_status dd_solve(lns_model* m, uint32_t* va_k, const uint32_t* vb, int solve_id, int* own_big, int* conv) {
   Dev& d = m->d;
   LaunchCfg c = cfg(m);
-  TRY(reset_iter(m));
-  CK(lns::launch_words_op(d, lns::kCopy, d.va, va_k, nullptr, c));
-  CK(lns::launch_words_op(d, lns::kOr, d.uni, d.uni, va_k, c));
-  TRY(local_solve(m, 0));
-  PendingEvent pe;
-  TRY(ev_begin(m, KC_UPDATE, &pe));
-  CK(lns::launch_flag(d, vb, 1, 1, solve_id, m->o.eps_p, m->o.eps_sw, eff_p_scale(m), m->o.sat_chop, m->o.krylov_fp32,
-                      d.kx, m->o.krylov_fail_rtol, c));
-  TRY(ev_end(m, &pe, 0.0, 0.0));
-  if (vb) TRY(dilate(m, m->o.m_layers));
-  CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
-  CK(cudaStreamSynchronize(m->stream));
-  annotate_pending(m);
-  TRY(ev_flush(m));
+  auto once = [&]() -> lns_status {
+    TRY(reset_iter(m));
+    CK(lns::launch_words_op(d, lns::kCopy, d.va, va_k, nullptr, c));
+    CK(lns::launch_words_op(d, lns::kOr, d.uni, d.uni, va_k, c));
+    TRY(local_solve(m, 0));
+    PendingEvent pe;
+    TRY(ev_begin(m, KC_UPDATE, &pe));
+    CK(lns::launch_flag(d, vb, 1, 1, solve_id, m->o.eps_p, m->o.eps_sw, eff_p_scale(m), m->o.sat_chop,
+                        m->o.krylov_fp32, d.kx, m->o.krylov_fail_rtol, c));
+    TRY(ev_end(m, &pe, 0.0, 0.0));
+    if (vb) TRY(dilate(m, m->o.m_layers));
+    CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    annotate_pending(m);
+    return ev_flush(m);
+  };
+  TRY(once());
   const IterCounters& h = *d.ctr_h;
+  int kit_fp32 = 0;
+  if (wants_fp64_retry(m)) {  // a failed solve scattered nothing and stamped nothing
+    kit_fp32 = h.krylov_iters;
+    TRY(with_fp64_krylov(m, once));
+    m->cur.fp64_retries += 1;
+  }
   const double maxdp = bits2d(h.max_dp_bits), cnv = bits2d(h.cnv_bits);
   *own_big = h.any_s;
   *conv = maxdp < m->o.tol_dp && cnv < m->o.tol_cnv;
   m->cur.iterations += 1;
-  m->cur.krylov_iters += h.krylov_iters;
+  m->cur.krylov_iters += kit_fp32 + h.krylov_iters;
   m->cur.cell_updates += h.n_active;
   m->cur.last_max_dp = maxdp;
   m->cur.last_cnv = cnv;
@@ -737,6 +775,7 @@ lns_status lns_options_default(lns_options* o) {
   o->krylov_fail_rtol = 1e-3;
   o->p_scale = 0.0;
   o->profile = 0;
+  o->fp64_fallback = 1;
   return LNS_OK;
 }
 
@@ -1007,7 +1046,7 @@ lns_status lns_set_support(lns_model* m, const uint32_t* bits) {
 
 lns_status lns_debug_fault(lns_model* m, int32_t code) {
   TRY(check_model(m));
-  if (code < 0 || code > 2) return fail(LNS_EINVAL, "fault code must be 0, 1 or 2");
+  if (code < 0 || code > 3) return fail(LNS_EINVAL, "fault code must be 0..3");
   CK(cudaMemcpyAsync(m->d.fault, &code, sizeof(int), cudaMemcpyHostToDevice, m->stream));
   return sync(m);
 }

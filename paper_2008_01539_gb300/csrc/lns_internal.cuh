@@ -55,7 +55,7 @@ struct IterCounters {
   unsigned bar_count;  // grid barrier of the Krylov kernel (its top bit flips at each barrier)
   unsigned bar_pad;
   int bar_timeout;     // set when a barrier wait gave up (the kernel then stops)
-  int pad_i;
+  int solve_failed;    // the update kernel found the Krylov solve failed and applied nothing
   double pad[1];
 };
 

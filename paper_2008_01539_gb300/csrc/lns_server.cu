@@ -202,6 +202,7 @@ lns_status advance(ServedModel& sm, double dt, int depth, lns_step_stats* acc, c
   sm.has_support = true;
   acc->iterations += st.iterations;
   acc->krylov_iters += st.krylov_iters;
+  acc->fp64_retries += st.fp64_retries;
   acc->cell_updates += st.cell_updates;
   acc->last_max_dp = st.last_max_dp;
   acc->last_cnv = st.last_cnv;

@@ -50,7 +50,8 @@ class lns_options(C.Structure):
                 ("tol_dp", C.c_double), ("tol_cnv", C.c_double), ("max_newton", C.c_int32),
                 ("max_dd_outer", C.c_int32), ("sat_chop", C.c_double), ("krylov_fp32", C.c_int32),
                 ("precond", C.c_int32), ("krylov_rtol", C.c_double), ("krylov_maxit", C.c_int32),
-                ("krylov_fail_rtol", C.c_double), ("p_scale", C.c_double), ("profile", C.c_int32)]
+                ("krylov_fail_rtol", C.c_double), ("p_scale", C.c_double), ("profile", C.c_int32),
+                ("fp64_fallback", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -64,12 +65,13 @@ class lns_allocator(C.Structure):
 class lns_iter_stats(C.Structure):
     _fields_ = [("n_active", C.c_int32), ("is_expand", C.c_int32), ("converged", C.c_int32),
                 ("step_done", C.c_int32), ("krylov_iters", C.c_int32), ("krylov_status", C.c_int32),
-                ("max_dp", C.c_double), ("max_dsw", C.c_double), ("cnv", C.c_double), ("krylov_relres", C.c_double)]
+                ("fp64_retry", C.c_int32), ("max_dp", C.c_double), ("max_dsw", C.c_double), ("cnv", C.c_double), ("krylov_relres", C.c_double)]
 
 
 class lns_step_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("krylov_iters", C.c_int32),
-                ("n_subdomains", C.c_int32), ("dd_outer", C.c_int32), ("cell_updates", C.c_int64),
+                ("n_subdomains", C.c_int32), ("dd_outer", C.c_int32), ("fp64_retries", C.c_int32),
+                ("cell_updates", C.c_int64),
                 ("last_max_dp", C.c_double), ("last_cnv", C.c_double)]
 
 
@@ -219,6 +221,7 @@ class Options:
     krylov_fail_rtol: float = 1e-3
     p_scale: float = 0.0
     profile: int = 0
+    fp64_fallback: int = 1
 
     def c(self) -> lns_options:
         return lns_options(*[getattr(self, f.name) for f in dataclasses.fields(self)])

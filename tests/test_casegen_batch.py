@@ -36,3 +36,22 @@ def test_batch_rejects_mismatched_schedules():
 
     with pytest.raises(ValueError):
         cg.batch([cg.small_dfn(n_steps=3), cg.small_dfn(n_steps=4)])
+
+
+def test_3d_generator_structure():
+    c = cg.small_dfn3d()
+    nx, ny, nz = c.meta["nx"], c.meta["ny"], c.meta["nz"]
+    assert c.n_matrix == nx * ny * nz
+    rows = np.repeat(np.arange(c.n), np.diff(c.row_ptr))
+    # symmetric, no self loops, neighbours ascending within a row
+    pairs = set(zip(rows.tolist(), c.nbr.tolist()))
+    assert all((j, i) in pairs for i, j in pairs) and all(i != j for i, j in pairs)
+    assert all(np.all(np.diff(c.nbr[c.row_ptr[i]:c.row_ptr[i + 1]]) > 0) for i in range(c.n))
+    # layers: depth grows with the layer index; the initial pressure follows the oil gradient
+    d = c.depth[: c.n_matrix].reshape(nz, ny, nx)
+    assert np.all(np.diff(d[:, 0, 0]) > 0)
+    assert np.allclose(np.diff(c.p0[: c.n_matrix].reshape(nz, ny, nx)[:, 0, 0]),
+                       c.fluid.rho_o_ref * cg.GRAVITY * c.meta["dz"])
+    # every fracture cell is always active and belongs to a line; the producer sits in the HF
+    assert np.all(c.always_active[c.line_id >= 0] == 1)
+    assert c.line_id[c.well_cell[0]] >= 0

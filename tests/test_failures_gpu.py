@@ -51,6 +51,39 @@ def test_forced_breakdown_is_reported():
     m.close()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_failed_fp32_solve_is_redone_in_fp64(mode):
+    """Every FP32 solve breaks down (injected); with fp64_fallback each iteration's solve is redone
+    in FP64 from the unchanged state and set, so the run equals an FP64 run bit for bit."""
+    case = cg.config0()
+    base = dict(mode=mode, krylov_rtol=1e-6)
+    m = lns.Model(case, lns.Options(**base, krylov_fp32=1))
+    m.lns_debug_fault(3)
+    ref = lns.Model(case, lns.Options(**base))
+    ref.lns_debug_fault(3)  # affects FP32 solves only: the FP64 run is the plain one
+    for dt in case.dt_schedule[:3]:
+        st = m.lns_timestep(float(dt))
+        sr = ref.lns_timestep(float(dt))
+        assert st["fp64_retries"] == st["iterations"] == sr["iterations"] > 0
+        assert sr["fp64_retries"] == 0
+    for a, b in zip(m.lns_get_state(), ref.lns_get_state()):
+        assert np.array_equal(a, b)
+    m.close()
+    ref.close()
+
+
+def test_failed_fp32_solve_without_fallback_is_reported():
+    case = cg.config0()
+    m = lns.Model(case, lns.Options(mode=1, krylov_fp32=1, fp64_fallback=0))
+    p0 = m.lns_get_state()[0].copy()
+    m.lns_debug_fault(3)
+    with pytest.raises(lns.LnsError) as e:
+        m.lns_newton_iter(case.dt_schedule[0])
+    assert e.value.status == lns.LNS_EKRYLOV
+    assert np.array_equal(m.lns_get_state()[0], p0)  # a failed solve scatters nothing
+    m.close()
+
+
 def test_non_finite_inputs_are_rejected():
     case = cg.config0()
     m = lns.Model(case)

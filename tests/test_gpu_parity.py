@@ -349,3 +349,22 @@ def test_graph_iteration_matches_direct_launches(mode, fp32):
     assert np.array_equal(pg, pd) and np.array_equal(swg, swd)
     graphed.close()
     direct.close()
+
+
+# ---------------------------------------------------------------------------------------
+# 3D layered model with vertical planar fractures (gravity acts between layers).
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [0, 1])
+def test_timesteps_match_oracle_3d(mode):
+    case = cg.small_dfn3d()
+    ref = O.Sim(case, O.Options(mode=mode, **TIGHT))
+    g = lns.Model(case, lns.Options(mode=mode, krylov_rtol=1e-12, krylov_maxit=5000, **TIGHT))
+    for dt in case.dt_schedule:
+        a = g.lns_timestep(dt)
+        b = ref.timestep(dt)
+        assert a["status"] == 0 and b["status"] == 0
+        assert abs(a["iterations"] - b["iterations"]) <= 1, (a, b)
+    p, sw = g.lns_get_state()
+    assert np.max(np.abs(p - ref.p) / ref.p) < 1e-7
+    assert np.max(np.abs(sw - ref.sw)) < 1e-7 * 0.25
+    g.close()
