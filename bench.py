@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serve-workers", type=int, default=4, help="requests run at once")
     ap.add_argument("--ensemble", type=int, default=64,
                     help="realizations in the batched-ensemble run (N ~ U{150..500} grids; 0 skips it)")
+    ap.add_argument("--large-3d", type=int, default=1,
+                    help="1: also run the 3D 200x200x20 + 2000-fracture oil-water case once per Krylov precision")
     ap.add_argument("--krylov-rtol", type=float, default=None,
                     help="BiCGStab relative tolerance (default: the library's)")
     return ap.parse_args()
@@ -323,6 +325,49 @@ def oracle_case(case, mode):
     return sim.p.copy(), sim.sw.copy(), time.perf_counter() - t0
 
 
+def large_3d_run(opts, flush, stream):
+    """config2-shaped 3D case, once with FP32 and once with FP64 BiCGStab, kernel classes timed."""
+    import numpy as np
+
+    from paper_2008_01539_gb300 import casegen as cg
+    from paper_2008_01539_gb300 import lns
+
+    hbm, _ = measured_peaks()
+    t0 = time.perf_counter()
+    case = cg.config2()
+    out = {"workload": f"{case.name}: 200x200x20 matrix (5x5x2 m cells) + 10 hydraulic-fracture stages "
+                       f"(40x12 cells) + 2000 natural-fracture panels, n={case.n} cells, "
+                       f"{len(case.dt_schedule)} timesteps to {case.dt_schedule.sum() / 86400:.0f} d, oil-water "
+                       f"(the three-phase black-oil variant is not built), localized Newton",
+           "cells": case.n, "generate_s": time.perf_counter() - t0}
+    states = {}
+    for tag, fp32 in (("fp32_krylov", 1), ("fp64_krylov", 0)):
+        o = lns.Options(**{**opts.__dict__, "krylov_fp32": fp32, "krylov_rtol": 1e-5 if fp32 else 1e-6,
+                           "profile": 1})
+        m = lns.Model(case, o)
+        for dt in case.dt_schedule[:2]:  # warm-up: first two timesteps
+            m.lns_timestep(float(dt))
+        m.lns_reset_kernel_times()
+        t, st = time_case(m, case, 1, flush, stream)
+        kt = m.lns_kernel_times()
+        states[tag] = m.lns_get_state()
+        m.close()
+        st = st[0]
+        r = {"case_time_s": t[0], "value": sum(x["cell_updates"] for x in st) / t[0], "unit": UNIT,
+             "newton_iterations": sum(x["iterations"] for x in st),
+             "krylov_iterations": sum(x["krylov_iters"] for x in st),
+             "fp64_retries": sum(x["fp64_retries"] for x in st),
+             "M_A_per_case": sum(x["cell_updates"] for x in st) / case.n,
+             "kernels": {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 2),
+                                     "GBps": k["bytes"] / (k["total_ms"] / 1e3) / 1e9 if k["total_ms"] > 0 else None,
+                                     "frac_of_measured_hbm": k["bytes"] / (k["total_ms"] / 1e3) / 1e9 / hbm
+                                     if k["total_ms"] > 0 else None}
+                         for k in kt if k["launches"] > 0}}
+        out[tag] = r
+    out["fp32_krylov"]["error_vs_fp64_krylov_gpu"] = field_error(*states["fp32_krylov"], *states["fp64_krylov"])
+    return out
+
+
 def serving_run(args, opts):
     """Requests 'advance model k by dt' with Poisson arrivals over resident models of log-uniform
     size; latency = completion - submission on the server clock."""
@@ -569,6 +614,12 @@ def bench_ours(args, rank, world, local):
                             f"natural fractures, 2 hydraulic fractures on a producer each) as one union model, "
                             f"{len(ens.dt_schedule)} timesteps to 30 d, same solver options as the headline",
                 "generate_s": t_gen}
+        # the 3D 200x200x20 matrix + 10 hydraulic-fracture stages + 2000 natural fractures (oil-water):
+        # one case per Krylov precision with every kernel class timed (large active sets, where the
+        # kernels run at HBM rates); the FP32 run's error is taken against the FP64 GPU run (the
+        # oracle's sparse LU is far too slow at a million cells)
+        if args.large_3d and rank == 0:
+            line["large_3d"] = large_3d_run(opts, flush, stream)
         # serving: requests over many resident models (continuous batching on worker streams)
         if args.serve_seconds > 0:
             # long requested steps on large models need many expansion iterations (the active set

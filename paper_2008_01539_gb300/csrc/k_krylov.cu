@@ -465,6 +465,55 @@ __device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, co
     }
 }
 
+// M^{-1} on one short line block by one thread: the same block-Thomas recurrences run row by row
+// (fwd: w_t = Dinv_t u_t + A_t w_{t-1}, kept in buf; bwd: z_t = w_t - G_t z_{t+1}).  A warp's
+// lanes then solve 32 short lines at once instead of one line with 32-lane scans.
+// FP32 solves stop when ||r|| has not halved for this many iterations (see the phase-1 test)
+#ifndef LNS_STAG_ITERS
+#define LNS_STAG_ITERS 40
+#endif
+constexpr int kStagIters = LNS_STAG_ITERS;
+
+#ifndef LNS_SHORT_LINE
+#define LNS_SHORT_LINE 16
+#endif
+constexpr int kShortLine = LNS_SHORT_LINE;
+
+template <typename T, int NR>
+__device__ __forceinline__ void line_solve_thread(int k0, int len, const LineFac& f, float2* buf, int bstride,
+                                                  typename V2<T>::t* const (&dst)[NR]) {
+  float2 w[NR];
+#pragma unroll
+  for (int q = 0; q < NR; q++) w[q] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int t = 0; t < len; t++) {
+    const float4 Di = f.fd[(size_t)t * f.fs];
+    const float4 a4 = f.fa[(size_t)t * f.fs];
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+      const float2 u = buf[q * bstride + t];
+      float2 c = make_float2(Di.x * u.x + Di.y * u.y, Di.z * u.x + Di.w * u.y);
+      c.x += a4.x * w[q].x + a4.y * w[q].y;
+      c.y += a4.z * w[q].x + a4.w * w[q].y;
+      w[q] = c;
+      buf[q * bstride + t] = c;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NR; q++) w[q] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int t = len - 1; t >= 0; t--) {
+    const float4 g4 = f.fg[(size_t)t * f.fs];
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+      const float2 c = buf[q * bstride + t];
+      const float2 zq = make_float2(c.x - (g4.x * w[q].x + g4.y * w[q].y), c.y - (g4.z * w[q].x + g4.w * w[q].y));
+      dst[q][k0 + t] = mk<T>((T)zq.x, (T)zq.y);
+      w[q] = zq;
+    }
+  }
+}
+
 // ---- grid barrier --------------------------------------------------------------------------
 // All blocks of the (cooperative, hence co-resident) launch add to one counter (zeroed before the
 // launch): block 0 adds 2^31 - (nb - 1), the others 1, so each barrier adds exactly 2^31 and the
@@ -526,6 +575,7 @@ struct RowRef {
 constexpr int kBufRows = 2048;   // chunk rows whose line inputs fit the shared buffer
 constexpr int kFacRows = 512;    // chunk rows whose line factors are staged
 constexpr int kLineCache = 64;   // line blocks of a chunk whose (start, length) are staged
+constexpr int kLongCache = 64;   // long line blocks of a chunk listed for the warp pass
 constexpr size_t kSmRref = (size_t)kRowsCached * kKryBlk * sizeof(RowRef);
 constexpr size_t kSmBuf = (size_t)2 * kBufRows * sizeof(float2);
 constexpr size_t kSmFac = (size_t)kFacRows * 3 * sizeof(float4);
@@ -582,6 +632,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   __shared__ int s_ctl;       // 0 continue, 1 stop
   __shared__ int s_epool;     // next free entry of the shared-memory pool
   __shared__ int s_rng[4];    // chunk start, chunk end, first line block, line-block count
+  __shared__ int s_nlong;     // line blocks longer than kShortLine (solved by a warp each)
+  __shared__ int2 s_long[kLongCache];
   const int nA = d.ctr->n_active;
   const int nb = gridDim.x;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -631,10 +683,15 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       s_rng[2] = l0;
       s_rng[3] = max(0, l1 - l0);
       s_epool = 0;
+      s_nlong = 0;
     }
   }
   __syncthreads();
   const int r0 = s_rng[0], r1 = s_rng[1], l0 = s_rng[2], nlb = s_rng[3];
+  // short line blocks go one per thread only when the block has more line blocks than its warps
+  // can take in two rounds (large systems); otherwise every block is solved by a warp (lower
+  // latency per block)
+  const int short_len = nlb > 2 * kWarps ? kShortLine : 0;
   const int kbeg = r0 + (int)threadIdx.x, kstep = blockDim.x;
   const bool busy = __any_sync(0xffffffffu, kbeg < r1) || (LINES && wib < nlb);  // adds to the dots
   // line inputs: the shared buffer, or (a chunk too long for it) global scratch, two float2 per row
@@ -678,9 +735,14 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
         f[1] = __ldg((const float4*)d.line_a + k);
         f[2] = __ldg((const float4*)d.line_g + k);
       }
-    for (int j = threadIdx.x; j < min(nlb, kLineCache); j += kstep) {
+    for (int j = threadIdx.x; j < nlb; j += kstep) {
       const int k0 = __ldg(&d.line_start[l0 + j]);
-      s_lines[j] = make_int2(k0, __ldg(&d.line_len[k0]));
+      const int2 kl = make_int2(k0, __ldg(&d.line_len[k0]));
+      if (j < kLineCache) s_lines[j] = kl;
+      if (kl.y > short_len) {  // list order does not matter: each line block is solved alone
+        const int p = atomicAdd(&s_nlong, 1);
+        if (p < kLongCache) s_long[p] = kl;
+      }
     }
   }
   __syncthreads();
@@ -690,26 +752,42 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
 #pragma unroll 1
     for (int k = kbeg, q = 0; k < r1; k += kstep, q++) fn(k, q < kRowsCached ? s_rref[q * kKryBlk + threadIdx.x] : global_ref(k));
   };
-  // after a block barrier: M^{-1} on this block's line blocks, one warp per line block
+  // after a block barrier: M^{-1} on this block's line blocks, one thread per short block, then
+  // one warp per long block.  solvefn(k0, len, factors, inputs, by_thread).
+  auto line_at = [&](int j) -> int2 {
+    if (j < kLineCache) return s_lines[j];
+    const int k0 = __ldg(&d.line_start[l0 + j]);
+    return make_int2(k0, __ldg(&d.line_len[k0]));
+  };
   auto lines = [&](auto solvefn) {
     if constexpr (LINES) {
       __syncthreads();
-#pragma unroll 1
-      for (int j = wib; j < nlb; j += kWarps) {
-        int2 kl;
-        if (j < kLineCache) {
-          kl = s_lines[j];
-        } else {
-          kl.x = __ldg(&d.line_start[l0 + j]);
-          kl.y = __ldg(&d.line_len[kl.x]);
-        }
+      auto fac = [&](const int2& kl) -> LineFac {
         const int o = kl.x - r0;
         const float4* fb = &s_fac[3 * (size_t)o];
-        const LineFac f = o + kl.y <= kFacRows
-                              ? LineFac{fb, fb + 1, fb + 2, 3}
-                              : LineFac{(const float4*)d.line_dinv + kl.x, (const float4*)d.line_a + kl.x,
-                                        (const float4*)d.line_g + kl.x, 1};
-        solvefn(kl.x, kl.y, f, lbuf + o);
+        return o + kl.y <= kFacRows ? LineFac{fb, fb + 1, fb + 2, 3}
+                                    : LineFac{(const float4*)d.line_dinv + kl.x, (const float4*)d.line_a + kl.x,
+                                              (const float4*)d.line_g + kl.x, 1};
+      };
+#pragma unroll 1
+      for (int j = threadIdx.x; j < nlb; j += kKryBlk) {
+        const int2 kl = line_at(j);
+        if (kl.y <= short_len) solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), true);
+      }
+      __syncwarp();
+      const int nlong = s_nlong;
+      if (nlong <= kLongCache) {
+#pragma unroll 1
+        for (int j = wib; j < nlong; j += kWarps) {
+          const int2 kl = s_long[j];
+          solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), false);
+        }
+      } else {  // more long blocks than the list holds: scan the whole table
+#pragma unroll 1
+        for (int j = wib; j < nlb; j += kWarps) {
+          const int2 kl = line_at(j);
+          if (kl.y > short_len) solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), false);
+        }
       }
     }
   };
@@ -733,9 +811,12 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     else
       zf[k] = bk;
   });
-  lines([&](int k0, int len, const LineFac& f, float2* buf) {
+  lines([&](int k0, int len, const LineFac& f, float2* buf, bool by_thread) {
     V* const dst[1] = {zf};
-    line_solve<T, 1>(k0, len, f, buf, bstride, dst);
+    if (by_thread)
+      line_solve_thread<T, 1>(k0, len, f, buf, bstride, dst);
+    else
+      line_solve<T, 1>(k0, len, f, buf, bstride, dst);
   });
   // injected faults (failure tests): 1 = block 0 never arrives at this barrier, 2 = rho_1 = 0,
   // 3 = rho_1 = 0 in FP32 solves only
@@ -758,14 +839,17 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     else
       return dot_df(a, fscale);
   };
-  S rho, alpha, stop2, rr_last;
+  S rho, alpha, stop2, rr_last, rr_ref;
   sc_zero(rho);
   sc_zero(alpha);
   sc_zero(stop2);
   sc_zero(rr_last);
+  sc_zero(rr_ref);
+  int it_ref = 0;  // FP32 stagnation test: iteration at which ||r||^2 last fell below rr_ref / 4
   if (threadIdx.x == 0) {  // thread 0 tracks the scalars
     rho = sc_from(df_from(fault == 2 || (fault == 3 && sizeof(T) == 4) ? 0.0 : bb * dscale), S{});
     stop2 = sc_from(df_from(rtol * rtol * bb * dscale), S{});
+    rr_ref = sc_from(df_from(bb * dscale), S{});
     sc_zero(s_sc[0]);  // beta_1
     sc_zero(s_sc[1]);  // alpha_0
     sc_zero(s_sc[2]);  // omega_0
@@ -816,9 +900,12 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       dot_acc(l_rv, rhk.x, vv.x);
       dot_acc(l_rv, rhk.y, vv.y);
     });
-    lines([&](int k0, int len, const LineFac& f, float2* buf) {
+    lines([&](int k0, int len, const LineFac& f, float2* buf, bool by_thread) {
       V* const dst[1] = {vtn};
-      line_solve<T, 1>(k0, len, f, buf, bstride, dst);
+      if (by_thread)
+        line_solve_thread<T, 1>(k0, len, f, buf, bstride, dst);
+      else
+        line_solve<T, 1>(k0, len, f, buf, bstride, dst);
     });
     {
       const DF vals[2] = {to_df(l_rv), to_df(l_rr)};
@@ -831,6 +918,10 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       if (threadIdx.x == 0) {
         const S rv = sc_from(o[0], S{});
         rr_last = sc_from(o[1], S{});
+        if (sc_le(sc_mul(rr_last, sc_from(df_from(4.0), S{})), rr_ref)) {
+          rr_ref = rr_last;
+          it_ref = it;
+        }
         if (*(volatile int*)&d.ctr->bar_timeout) {
           s_ctl = 1;
           status = 3;
@@ -838,6 +929,12 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
           s_ctl = 1;
           status = 0;
         } else if (it > maxit) {
+          s_ctl = 1;
+          status = 1;
+        } else if (!kF64 && it - it_ref > kStagIters) {
+          // FP32 stagnation: ||r|| has not halved in kStagIters iterations, the FP32 rounding
+          // floor of this system is near; stop as at maxit (accepted as an inexact Newton step
+          // when ||r|| / ||b|| <= krylov_fail_rtol, else redone in FP64 by the host)
           s_ctl = 1;
           status = 1;
         } else if (!sc_ok(rv) || !sc_ok(rho)) {
@@ -885,9 +982,12 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       dot_acc(l_rt, rhk.x, tk.x);
       dot_acc(l_rt, rhk.y, tk.y);
     });
-    lines([&](int k0, int len, const LineFac& f, float2* buf) {
+    lines([&](int k0, int len, const LineFac& f, float2* buf, bool by_thread) {
       V* const dst[2] = {zf, tt};
-      line_solve<T, 2>(k0, len, f, buf, bstride, dst);
+      if (by_thread)
+        line_solve_thread<T, 2>(k0, len, f, buf, bstride, dst);
+      else
+        line_solve<T, 2>(k0, len, f, buf, bstride, dst);
     });
     {
       const DF vals[4] = {to_df(l_ts), to_df(l_tt), to_df(l_rs), to_df(l_rt)};
