@@ -167,11 +167,14 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double p_
       }
     }
     if (edge && l == 0) atomicOr(&d.vb[i >> 5], 1u << (i & 31));
-    if (lines && l == 0) {  // line rows: 2 continues a line, 1 starts one; starts listed in any order
-      d.lnk[k] = make_int2(eprev, enext);
-      const int fl = eprev >= 0 ? 2 : (enext >= 0 ? 1 : 0);
-      d.line_row_flag[k] = fl;
-      if (fl == 1) d.line_start[atomicAdd(&d.ctr->n_line_starts, 1)] = k;
+    if (l == 0) {  // line rows: 2 continues a line, 1 starts one; starts listed in any order
+      const int fl = lines ? (eprev >= 0 ? 2 : (enext >= 0 ? 1 : 0)) : 0;
+      if (lines) {
+        d.lnk[k] = make_int2(eprev, enext);
+        d.line_row_flag[k] = fl;
+        if (fl == 1) d.line_start[atomicAdd(&d.ctr->n_line_starts, 1)] = k;
+      }
+      d.arow[k] = make_int2(e0, (e1 - e0) | (fl << 24));  // the solver's row reference, one load
     }
     // producers
     for (int w = d.well_of_cell[i]; w >= 0; w = d.well_next[w]) {

@@ -700,9 +700,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   const int bstride = buf_sm ? kBufRows : r1 - r0;
 
   auto global_ref = [&](int k) -> Ref {
-    const int i = __ldg(&d.act[k]);
-    const int e0 = __ldg(&d.row_ptr[i]);
-    return {-(e0 + 1), __ldg(&d.row_ptr[i + 1]) - e0, LINES ? __ldg(&d.line_row_flag[k]) : 0};
+    const int2 a = __ldg(&d.arow[k]);
+    return {-(a.x + 1), a.y & 0xffffff, LINES ? (a.y >> 24) : 0};
   };
   // stage a row's columns and blocks in the shared pool (placement does not affect the result)
   auto stage = [&](int k) -> Ref {
@@ -747,10 +746,22 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   }
   __syncthreads();
 
-  // fn(k, ref) over this thread's rows of the chunk (one call site: one copy of the row code)
+  // fn(k, ref) over this thread's rows of the chunk (one call site: one copy of the row code); the
+  // next row's reference is loaded before the current row is processed
+  auto ref_of = [&](int k, int q) -> Ref { return q < kRowsCached ? s_rref[q * kKryBlk + threadIdx.x] : global_ref(k); };
   auto rows = [&](auto fn) {
+    if (kbeg >= r1) return;
+    Ref ref = ref_of(kbeg, 0);
 #pragma unroll 1
-    for (int k = kbeg, q = 0; k < r1; k += kstep, q++) fn(k, q < kRowsCached ? s_rref[q * kKryBlk + threadIdx.x] : global_ref(k));
+    for (int k = kbeg, q = 0;; q++) {
+      const int kn = k + kstep;
+      Ref nref = ref;
+      if (kn < r1) nref = ref_of(kn, q + 1);
+      fn(k, ref);
+      if (kn >= r1) break;
+      k = kn;
+      ref = nref;
+    }
   };
   // after a block barrier: M^{-1} on this block's line blocks, one thread per short block, then
   // one warp per long block.  solvefn(k0, len, factors, inputs, by_thread).

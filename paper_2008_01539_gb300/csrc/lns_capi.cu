@@ -875,6 +875,8 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
       int* t2;
       AL(t2, 2 * N);
       d.lnk = (int2*)t2;
+      AL(t2, 2 * N);
+      d.arow = (int2*)t2;
     }
     AL(d.line_row_flag, N);
     double** vecs[14] = {(double**)&d.kx,  (double**)&d.kr,   (double**)&d.krh,  (double**)&d.ky0, (double**)&d.ky1,

@@ -88,6 +88,7 @@ struct Dev {
   // lblk: bitset of line-block starts; lscratch: compaction scratch
   int *line_start, *line_len, *line_row_flag, *lscratch;
   int2* lnk;  // per compact row: CSR entries of its couplings to the previous / next row of its line (-1)
+  int2* arow;  // per compact row: first CSR entry, and degree | line flag << 24 (written by the assembly)
   uint32_t* lblk;
   // Krylov vectors
   void *kx, *kr, *krh, *ky0, *ky1, *kv, *ks, *kt, *kz, *kvt0, *kvt1, *krt, *kzf, *ktt;
