@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["local", "full", "dd"], default="local",
                     help="solver whose case is the headline (default: Algorithm 1)")
-    ap.add_argument("--case", choices=["config1", "config0"], default="config1")
+    ap.add_argument("--case", choices=["config1", "config0", "config2"], default="config1",
+                    help="config1: 400x400 + DFN (the headline); config0: 50x50 + one fracture; config2: the 3D "
+                         "200x200x20 + 2000-fracture oil-water model")
     ap.add_argument("--krylov", choices=["fp32", "fp64"], default="fp32",
                     help="BiCGStab and preconditioner precision: FP32 (inexact Newton, the default) or FP64; "
                          "residual, Jacobian assembly, convergence checks and updates are FP64 in both")
@@ -67,6 +69,14 @@ def parse():
                     help="realizations in the batched-ensemble run (N ~ U{150..500} grids; 0 skips it)")
     ap.add_argument("--large-3d", type=int, default=1,
                     help="1: also run the 3D 200x200x20 + 2000-fracture oil-water case once per Krylov precision")
+    ap.add_argument("--iteration-log", default=None,
+                    help="after the run, write one JSON line per Newton iteration of one more (untimed) case "
+                         "(n_A, Krylov iterations, per kernel class: ms and algorithmic bytes)")
+    ap.add_argument("--write-traffic", default=None, metavar="NCU_RAW_CSV",
+                    help="no GPU work: write profiles/traffic.json from an ncu raw-page CSV of one launch "
+                         "(--kernel-class, its 0-based --launch-index) and the --iteration-log of the same case")
+    ap.add_argument("--kernel-class", default="bicgstab", help="kernel class of --write-traffic")
+    ap.add_argument("--launch-index", type=int, default=0, help="launch of the class captured (ncu -s)")
     ap.add_argument("--krylov-rtol", type=float, default=None,
                     help="BiCGStab relative tolerance (default: the library's)")
     return ap.parse_args()
@@ -75,10 +85,12 @@ def parse():
 def make_case(name):
     from paper_2008_01539_gb300 import casegen as cg
 
-    return cg.config1() if name == "config1" else cg.config0()
+    return {"config1": cg.config1, "config0": cg.config0, "config2": cg.config2}[name]()
 
 
 def workload_name(case, args):
+    if "nz" in case.meta or "nx" not in case.meta:
+        return f"{case.name}, n={case.n} cells, {len(case.dt_schedule)} timesteps"
     mode = {"local": "localized Newton (Algorithm 1, m=2, eps=0.3 psi)", "full": "standard Newton",
             "dd": "adaptive nonlinear DD (Algorithm 2, m=2)"}[args.mode]
     meta = case.meta
@@ -429,9 +441,67 @@ def serving_run(args, opts):
         "evictions": st["evictions"], "total_cells": int(sizes.sum()), "setup_s": t_setup}
 
 
+def write_traffic(args):
+    """profiles/traffic.json: DRAM bytes of one captured launch over its algorithmic bytes, tagged
+    with the hash of the kernel sources (bench.py reports traffic only while they are unchanged)."""
+    import csv
+
+    rows = list(csv.reader(open(args.write_traffic)))
+    hdr, data = rows[0], rows[2:]
+    assert len(data) == 1, "the CSV must hold exactly one captured launch"
+    col = {h: i for i, h in enumerate(hdr)}
+    unit = rows[1]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+
+    def val(name):
+        return float(data[0][col[name]].replace(",", "")) * scale.get(unit[col[name]], 1.0)
+
+    dram = val("dram__bytes_read.sum") + val("dram__bytes_write.sum")
+    its = [json.loads(x) for x in open(args.iteration_log)]
+    launches = [r for r in its if r["kernels"].get(args.kernel_class, {}).get("launches", 0) > 0]
+    rec = launches[args.launch_index]
+    alg = rec["kernels"][args.kernel_class]["bytes"]
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        out = json.load(open(path))
+    except (OSError, ValueError):
+        out = {}
+    if out.get("source_hash") != kernel_source_hash():
+        out = {"source_hash": kernel_source_hash(), "kernels": {}}
+    out["kernels"][args.kernel_class] = {
+        "dram_bytes": dram, "algorithmic_bytes": alg, "dram_over_algorithmic": dram / alg,
+        "launch_index": args.launch_index, "n_active": rec["n_active"], "krylov_iters": rec["krylov_iters"],
+        "case": args.case}
+    json.dump(out, open(path, "w"), indent=1)
+    print(json.dumps(out["kernels"][args.kernel_class]))
+    return 0
+
+
+def iteration_log(model, case, opts, path):
+    """One more case with every kernel class timed, one Newton iteration at a time."""
+    from paper_2008_01539_gb300 import lns
+
+    model.set_options(lns.Options(**{**opts.__dict__, "profile": 1}))
+    model.lns_reset()
+    with open(path, "w") as f:
+        for step, dt in enumerate(case.dt_schedule):
+            while True:
+                model.lns_reset_kernel_times()
+                st = model.lns_newton_iter(float(dt))
+                kt = {k["name"]: {"launches": k["launches"], "ms": k["total_ms"], "bytes": k["bytes"]}
+                      for k in model.lns_kernel_times()}
+                f.write(json.dumps({"step": step, "n_active": st["n_active"], "krylov_iters": st["krylov_iters"],
+                                    "kernels": kt}) + "\n")
+                if st["step_done"]:
+                    break
+    model.set_options(opts)
+
+
 def main():
     args = parse()
     args.fp32_krylov = args.fp32_krylov or args.krylov == "fp32"
+    if args.write_traffic:
+        return write_traffic(args)
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
@@ -512,6 +582,8 @@ def bench_ours(args, rank, world, local):
     torch.cuda.synchronize()
     ktimes = model.lns_kernel_times()
     model.set_options(opts)
+    if args.iteration_log and rank == 0:
+        iteration_log(model, case, opts, args.iteration_log)
 
     # roofline of the dominant kernel (live CUDA-event timing inside the timed region)
     hbm, hbm_src = measured_peaks()
