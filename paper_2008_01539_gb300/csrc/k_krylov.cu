@@ -325,9 +325,11 @@ __device__ __forceinline__ typename V2<T>::t row_product(const int* col, const B
 // On return lane t holds c_t and the composite map P_t such that the value of row t is
 // c_t + P_t * (the value entering the chunk).
 template <int NR>
-__device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float>& A, int lane) {
+__device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float>& A, int lane, int seg = 32) {
+  const int t = lane & (seg - 1);  // position in the segment of seg lanes (a power of two)
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
+    if (o >= seg) break;  // uniform
     M2<float> Ap;
     Ap.a = __shfl_up_sync(0xffffffffu, A.a, o);
     Ap.b = __shfl_up_sync(0xffffffffu, A.b, o);
@@ -339,7 +341,7 @@ __device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float>& A, int lane
       cp[q].x = __shfl_up_sync(0xffffffffu, c[q].x, o);
       cp[q].y = __shfl_up_sync(0xffffffffu, c[q].y, o);
     }
-    if (lane >= o) {
+    if (t >= o) {
 #pragma unroll
       for (int q = 0; q < NR; q++) {
         c[q].x += A.a * cp[q].x + A.b * cp[q].y;
@@ -351,9 +353,11 @@ __device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float>& A, int lane
 }
 
 template <int NR>
-__device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float>& B, int lane) {
+__device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float>& B, int lane, int seg = 32) {
+  const int t = lane & (seg - 1);
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
+    if (o >= seg) break;  // uniform
     M2<float> Bp;
     Bp.a = __shfl_down_sync(0xffffffffu, B.a, o);
     Bp.b = __shfl_down_sync(0xffffffffu, B.b, o);
@@ -365,7 +369,7 @@ __device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float>& B, int lane
       cp[q].x = __shfl_down_sync(0xffffffffu, c[q].x, o);
       cp[q].y = __shfl_down_sync(0xffffffffu, c[q].y, o);
     }
-    if (lane + o < 32) {
+    if (t + o < seg) {
 #pragma unroll
       for (int q = 0; q < NR; q++) {
         c[q].x += B.a * cp[q].x + B.b * cp[q].y;
@@ -465,52 +469,48 @@ __device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, co
     }
 }
 
-// M^{-1} on one short line block by one thread: the same block-Thomas recurrences run row by row
-// (fwd: w_t = Dinv_t u_t + A_t w_{t-1}, kept in buf; bwd: z_t = w_t - G_t z_{t+1}).  A warp's
-// lanes then solve 32 short lines at once instead of one line with 32-lane scans.
+// M^{-1} on short line blocks packed into segments of `seg` lanes (4, 8, 16 or 32; a line block of
+// len <= seg rows per segment, 32 / seg blocks per warp): the same two scans, confined to the
+// segment, so one round of loads and log2(seg) shuffle levels per sweep solve them all.  A lane
+// whose segment holds no block (len = 0) carries zeros.
 // FP32 solves stop when ||r|| has not halved for this many iterations (see the phase-1 test)
 #ifndef LNS_STAG_ITERS
 #define LNS_STAG_ITERS 40
 #endif
 constexpr int kStagIters = LNS_STAG_ITERS;
 
-#ifndef LNS_SHORT_LINE
-#define LNS_SHORT_LINE 16
-#endif
-constexpr int kShortLine = LNS_SHORT_LINE;
+// length class of a line block: 0..3 for len <= 4, 8, 16, 32 (segments of 4 << c lanes), 4 above
+__device__ __forceinline__ int line_class(int len) {
+  return len <= 4 ? 0 : (len <= 8 ? 1 : (len <= 16 ? 2 : (len <= 32 ? 3 : 4)));
+}
 
 template <typename T, int NR>
-__device__ __forceinline__ void line_solve_thread(int k0, int len, const LineFac& f, float2* buf, int bstride,
-                                                  typename V2<T>::t* const (&dst)[NR]) {
+__device__ __forceinline__ void line_solve_seg(int seg, int k0, int len, const LineFac& f, const float2* buf,
+                                               int bstride, typename V2<T>::t* const (&dst)[NR]) {
+  const int lane = threadIdx.x & 31, t = lane & (seg - 1);
+  const bool on = t < len;
   float2 w[NR];
+  M2<float> P = {0.f, 0.f, 0.f, 0.f};
+  float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int q = 0; q < NR; q++) w[q] = make_float2(0.f, 0.f);
-#pragma unroll 2
-  for (int t = 0; t < len; t++) {
+  if (on) {  // every load of the row (both sweeps) is issued before the first scan
     const float4 Di = f.fd[(size_t)t * f.fs];
     const float4 a4 = f.fa[(size_t)t * f.fs];
+    g4 = f.fg[(size_t)t * f.fs];
 #pragma unroll
     for (int q = 0; q < NR; q++) {
       const float2 u = buf[q * bstride + t];
-      float2 c = make_float2(Di.x * u.x + Di.y * u.y, Di.z * u.x + Di.w * u.y);
-      c.x += a4.x * w[q].x + a4.y * w[q].y;
-      c.y += a4.z * w[q].x + a4.w * w[q].y;
-      w[q] = c;
-      buf[q * bstride + t] = c;
+      w[q] = make_float2(Di.x * u.x + Di.y * u.y, Di.z * u.x + Di.w * u.y);
     }
+    P = {a4.x, a4.y, a4.z, a4.w};
   }
+  scan_fwd<NR>(w, P, lane, seg);
+  P = {-g4.x, -g4.y, -g4.z, -g4.w};
+  scan_bwd<NR>(w, P, lane, seg);
+  if (on) {
 #pragma unroll
-  for (int q = 0; q < NR; q++) w[q] = make_float2(0.f, 0.f);
-#pragma unroll 2
-  for (int t = len - 1; t >= 0; t--) {
-    const float4 g4 = f.fg[(size_t)t * f.fs];
-#pragma unroll
-    for (int q = 0; q < NR; q++) {
-      const float2 c = buf[q * bstride + t];
-      const float2 zq = make_float2(c.x - (g4.x * w[q].x + g4.y * w[q].y), c.y - (g4.z * w[q].x + g4.w * w[q].y));
-      dst[q][k0 + t] = mk<T>((T)zq.x, (T)zq.y);
-      w[q] = zq;
-    }
+    for (int q = 0; q < NR; q++) dst[q][k0 + t] = mk<T>((T)w[q].x, (T)w[q].y);
   }
 }
 
@@ -574,12 +574,11 @@ struct RowRef {
 // staged matrix rows (columns and blocks).
 constexpr int kBufRows = 2048;   // chunk rows whose line inputs fit the shared buffer
 constexpr int kFacRows = 512;    // chunk rows whose line factors are staged
-constexpr int kLineCache = 64;   // line blocks of a chunk whose (start, length) are staged
-constexpr int kLongCache = 64;   // long line blocks of a chunk listed for the warp pass
+constexpr int kLineList = 1024;  // line blocks of a chunk listed by length class (else one per warp)
 constexpr size_t kSmRref = (size_t)kRowsCached * kKryBlk * sizeof(RowRef);
 constexpr size_t kSmBuf = (size_t)2 * kBufRows * sizeof(float2);
 constexpr size_t kSmFac = (size_t)kFacRows * 3 * sizeof(float4);
-constexpr size_t kSmLines = (size_t)kLineCache * sizeof(int2);
+constexpr size_t kSmLines = (size_t)kLineList * sizeof(int2);
 constexpr size_t kSmPool = kKrySmem - kSmRref - kSmBuf - kSmFac - kSmLines;
 
 // First row >= k that does not continue a line block (the end of a chunk starting or ending at
@@ -632,8 +631,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   __shared__ int s_ctl;       // 0 continue, 1 stop
   __shared__ int s_epool;     // next free entry of the shared-memory pool
   __shared__ int s_rng[4];    // chunk start, chunk end, first line block, line-block count
-  __shared__ int s_nlong;     // line blocks longer than kShortLine (solved by a warp each)
-  __shared__ int2 s_long[kLongCache];
+  // line blocks by length class c: len <= 4 << c in segments (c < 4), longer ones one per warp (c = 4)
+  __shared__ int s_ccount[5], s_coff[5], s_cfill[5], s_citem[6];
   const int nA = d.ctr->n_active;
   const int nb = gridDim.x;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -683,15 +682,11 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       s_rng[2] = l0;
       s_rng[3] = max(0, l1 - l0);
       s_epool = 0;
-      s_nlong = 0;
+      for (int c = 0; c < 5; c++) s_ccount[c] = 0;
     }
   }
   __syncthreads();
   const int r0 = s_rng[0], r1 = s_rng[1], l0 = s_rng[2], nlb = s_rng[3];
-  // short line blocks go one per thread only when the block has more line blocks than its warps
-  // can take in two rounds (large systems); otherwise every block is solved by a warp (lower
-  // latency per block)
-  const int short_len = nlb > 2 * kWarps ? kShortLine : 0;
   const int kbeg = r0 + (int)threadIdx.x, kstep = blockDim.x;
   const bool busy = __any_sync(0xffffffffu, kbeg < r1) || (LINES && wib < nlb);  // adds to the dots
   // line inputs: the shared buffer, or (a chunk too long for it) global scratch, two float2 per row
@@ -734,13 +729,28 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
         f[1] = __ldg((const float4*)d.line_a + k);
         f[2] = __ldg((const float4*)d.line_g + k);
       }
-    for (int j = threadIdx.x; j < nlb; j += kstep) {
-      const int k0 = __ldg(&d.line_start[l0 + j]);
-      const int2 kl = make_int2(k0, __ldg(&d.line_len[k0]));
-      if (j < kLineCache) s_lines[j] = kl;
-      if (kl.y > short_len) {  // list order does not matter: each line block is solved alone
-        const int p = atomicAdd(&s_nlong, 1);
-        if (p < kLongCache) s_long[p] = kl;
+    // list the chunk's line blocks by length class (the order inside a class does not matter: each
+    // block is solved alone, the same way wherever it sits)
+    if (nlb <= kLineList) {
+      for (int j = threadIdx.x; j < nlb; j += kstep)
+        atomicAdd(&s_ccount[line_class(__ldg(&d.line_len[__ldg(&d.line_start[l0 + j])]))], 1);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int off = 0;
+        s_citem[0] = 0;
+        for (int c = 0; c < 5; c++) {
+          s_coff[c] = off;
+          s_cfill[c] = off;
+          off += s_ccount[c];
+          const int per = c < 4 ? 8 >> c : 1;  // line blocks per warp item
+          s_citem[c + 1] = s_citem[c] + (s_ccount[c] + per - 1) / per;
+        }
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < nlb; j += kstep) {
+        const int k0 = __ldg(&d.line_start[l0 + j]);
+        const int len = __ldg(&d.line_len[k0]);
+        s_lines[atomicAdd(&s_cfill[line_class(len)], 1)] = make_int2(k0, len);
       }
     }
   }
@@ -763,13 +773,9 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       ref = nref;
     }
   };
-  // after a block barrier: M^{-1} on this block's line blocks, one thread per short block, then
-  // one warp per long block.  solvefn(k0, len, factors, inputs, by_thread).
-  auto line_at = [&](int j) -> int2 {
-    if (j < kLineCache) return s_lines[j];
-    const int k0 = __ldg(&d.line_start[l0 + j]);
-    return make_int2(k0, __ldg(&d.line_len[k0]));
-  };
+  // after a block barrier: M^{-1} on this block's line blocks.  The warps share out items: 32 / seg
+  // short blocks of one length class in segments of seg lanes, or one block longer than 32 rows.
+  // solvefn(k0, len, factors, inputs, seg), seg = 0 for a whole-warp multi-chunk solve.
   auto lines = [&](auto solvefn) {
     if constexpr (LINES) {
       __syncthreads();
@@ -780,24 +786,28 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
                                     : LineFac{(const float4*)d.line_dinv + kl.x, (const float4*)d.line_a + kl.x,
                                               (const float4*)d.line_g + kl.x, 1};
       };
+      if (nlb <= kLineList) {
+        const int nit = s_citem[5];
 #pragma unroll 1
-      for (int j = threadIdx.x; j < nlb; j += kKryBlk) {
-        const int2 kl = line_at(j);
-        if (kl.y <= short_len) solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), true);
-      }
-      __syncwarp();
-      const int nlong = s_nlong;
-      if (nlong <= kLongCache) {
-#pragma unroll 1
-        for (int j = wib; j < nlong; j += kWarps) {
-          const int2 kl = s_long[j];
-          solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), false);
+        for (int it = wib; it < nit; it += kWarps) {
+          int c = 0;
+          while (c < 4 && it >= s_citem[c + 1]) c++;
+          const int idx = it - s_citem[c];
+          if (c < 4) {
+            const int seg = 4 << c, li = idx * (8 >> c) + (lane >> (c + 2));
+            const int2 kl = li < s_ccount[c] ? s_lines[s_coff[c] + li] : make_int2(r0, 0);
+            solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), seg);
+          } else {
+            const int2 kl = s_lines[s_coff[4] + idx];
+            solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), 0);
+          }
         }
-      } else {  // more long blocks than the list holds: scan the whole table
+      } else {  // more line blocks than the list holds: one warp per block, in table order
 #pragma unroll 1
         for (int j = wib; j < nlb; j += kWarps) {
-          const int2 kl = line_at(j);
-          if (kl.y > short_len) solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), false);
+          const int k0 = __ldg(&d.line_start[l0 + j]);
+          const int2 kl = make_int2(k0, __ldg(&d.line_len[k0]));
+          solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), 0);
         }
       }
     }
@@ -822,10 +832,10 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     else
       zf[k] = bk;
   });
-  lines([&](int k0, int len, const LineFac& f, float2* buf, bool by_thread) {
+  lines([&](int k0, int len, const LineFac& f, float2* buf, int seg) {
     V* const dst[1] = {zf};
-    if (by_thread)
-      line_solve_thread<T, 1>(k0, len, f, buf, bstride, dst);
+    if (seg)
+      line_solve_seg<T, 1>(seg, k0, len, f, buf, bstride, dst);
     else
       line_solve<T, 1>(k0, len, f, buf, bstride, dst);
   });
@@ -911,10 +921,10 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       dot_acc(l_rv, rhk.x, vv.x);
       dot_acc(l_rv, rhk.y, vv.y);
     });
-    lines([&](int k0, int len, const LineFac& f, float2* buf, bool by_thread) {
+    lines([&](int k0, int len, const LineFac& f, float2* buf, int seg) {
       V* const dst[1] = {vtn};
-      if (by_thread)
-        line_solve_thread<T, 1>(k0, len, f, buf, bstride, dst);
+      if (seg)
+        line_solve_seg<T, 1>(seg, k0, len, f, buf, bstride, dst);
       else
         line_solve<T, 1>(k0, len, f, buf, bstride, dst);
     });
@@ -993,10 +1003,10 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       dot_acc(l_rt, rhk.x, tk.x);
       dot_acc(l_rt, rhk.y, tk.y);
     });
-    lines([&](int k0, int len, const LineFac& f, float2* buf, bool by_thread) {
+    lines([&](int k0, int len, const LineFac& f, float2* buf, int seg) {
       V* const dst[2] = {zf, tt};
-      if (by_thread)
-        line_solve_thread<T, 2>(k0, len, f, buf, bstride, dst);
+      if (seg)
+        line_solve_seg<T, 2>(seg, k0, len, f, buf, bstride, dst);
       else
         line_solve<T, 2>(k0, len, f, buf, bstride, dst);
     });
