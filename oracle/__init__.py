@@ -104,7 +104,8 @@ def lib():
 
 @dataclasses.dataclass
 class Options:
-    """Solver options.  mode: 0 standard Newton, 1 Algorithm 1, 2 Algorithm 2.
+    """Solver options.  mode: 0 standard Newton, 1 Algorithm 1, 2 Algorithm 2, 3 residual-based
+    active sets (unconverged cells inflated by m_layers; the Lu-Beckner estimate the paper cites).
     Cutoffs and tolerances in SI (Pa); eps_p = 0.3 psi as in the paper's runs."""
     mode: int = 1
     eps_p: float = 0.3 * 6894.757293168

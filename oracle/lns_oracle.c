@@ -839,6 +839,49 @@ int orc_timestep(const orc_model* m, const orc_opts* o, double* p, double* sw, u
       converged = dp_max < o->tol_dp && cnv_max < o->tol_cnv; /* check convergence */
       orc_active_set_update(m, o, va, dp, dsw, converged, vb, &is_expand);
     }
+  } else if (o->mode == 3) {
+    /* Residual-based active set (the Lu-Beckner estimate the paper cites in Section 1 and
+     * Section 4.2 as the alternative a-priori strategy): the cells whose scaled residual is not
+     * converged (CNV_i >= tol_cnv, the full-domain residual at u^nu), inflated by m layers of
+     * neighbours, form the next active set.  Converged when no cell is unconverged and the last
+     * update is below tol_dp (at nu = 0: no cell unconverged).  An empty unconverged set before
+     * convergence keeps the previous active set. */
+    double* F = (double*)malloc(sizeof(double) * 2 * nn);
+    double* Jd = (double*)malloc(sizeof(double) * 4 * nn);
+    double* Jo = (double*)malloc(sizeof(double) * 4 * (size_t)(m->n_adj > 0 ? m->n_adj : 1));
+    double* cnv = (double*)malloc(sizeof(double) * nn);
+    uint8_t* unconv = (uint8_t*)malloc(nn);
+    memset(va, 0, nn);
+    for (;;) {
+      orc_assemble(m, p, sw, pn, swn, dt, F, Jd, Jo);
+      orc_cnv(m, p, F, dt, cnv);
+      int32_t n_unconv = 0;
+      for (int32_t i = 0; i < n; i++) {
+        unconv[i] = (uint8_t)(cnv[i] >= o->tol_cnv);
+        n_unconv += unconv[i];
+      }
+      if (n_unconv == 0 && (it == 0 || dp_max < o->tol_dp)) break; /* converged */
+      if (it >= o->max_newton) {
+        status = -4;
+        break;
+      }
+      if (n_unconv > 0) orc_dilate(m, unconv, o->m_layers, va);
+      int32_t na = count_set(n, va);
+      if (orc_local_solve(m, o, p, sw, pn, swn, dt, va, dp, dsw, &cnv_max, &dp_max) != 0) {
+        status = -1;
+        break;
+      }
+      apply_update(n, va, p, sw, dp, dsw);
+      or_into(n, union_out, va);
+      if (trace && it < trace_cap) trace[it] = na;
+      st->cell_updates += na;
+      it++;
+    }
+    free(F);
+    free(Jd);
+    free(Jo);
+    free(cnv);
+    free(unconv);
   } else { /* Algorithm 2 */
     int32_t cap = o->max_newton > 0 ? o->max_newton : 1;
     uint8_t** VA = (uint8_t**)calloc(cap + 1, sizeof(uint8_t*));

@@ -16,6 +16,8 @@
  *   - Section 4.1: Newton's method J du = -F, support set supp du = {i : |du_i| >= eps}.
  *   - Section 4.3, Algorithm 1: localized Newton (expand / shrink active set).
  *   - Section 4.4, Algorithm 2: adaptive nonlinear domain decomposition.
+ *   - Section 1 / Section 4.2: the residual-based active set the paper compares against
+ *     (unconverged cells plus layers of neighbours), as mode 3.
  * The linear step is a hand-written block sparse LU (nested-dissection ordering,
  * symbolic factorization by elimination tree, row-by-row Doolittle elimination
  * with 2x2 block pivots).
@@ -24,7 +26,9 @@
  * slightly compressible flow into a constant-pressure fracture; cumulative mass
  * balance; central-difference Jacobian; dense LU on small systems; brute-force
  * graph distances for the neighbour sets; hydrostatic column; special cases of
- * Algorithms 1 and 2.
+ * Algorithms 1 and 2; for mode 3 (tests/test_oracle_residual_sets.py) the first set against
+ * scipy graph distances from the unconverged cells, full inflation against standard Newton's
+ * iterates, an equilibrium, and the converged fields against standard Newton.
  */
 #ifndef LNS_ORACLE_H
 #define LNS_ORACLE_H
@@ -52,7 +56,7 @@ typedef struct {
 } orc_model;
 
 typedef struct {
-  int32_t mode;        /* 0 full Newton, 1 Algorithm 1, 2 Algorithm 2 */
+  int32_t mode;        /* 0 full Newton, 1 Algorithm 1, 2 Algorithm 2, 3 residual-based sets */
   double eps_p;        /* cutoff on |dp| (Pa) */
   double eps_sw;       /* cutoff on |dSw|; <= 0 disables */
   int32_t m_layers;    /* m of the neighbour set */
