@@ -49,7 +49,13 @@ typedef enum {
   LNS_ESTATE = -7    /* call not valid in the model's current state */
 } lns_status;
 
-enum { LNS_MODE_FULL = 0, LNS_MODE_LOCAL = 1, LNS_MODE_DD = 2 };
+/* LNS_MODE_RESIDUAL: residual-based active sets, the alternative a-priori estimate the paper
+ * cites (Section 1, Section 4.2): each iteration evaluates the full-domain residual and solves on
+ * the cells whose scaled residual CNV_i = max_l |R_l,i| dt / (PV_i b_l,i) >= tol_cnv, inflated by
+ * m_layers of neighbours (an empty unconverged set before convergence keeps the previous set);
+ * converged when no cell is unconverged and the last update's max |dp| < tol_dp.  For
+ * comparison with Algorithm 1; lns_timestep only. */
+enum { LNS_MODE_FULL = 0, LNS_MODE_LOCAL = 1, LNS_MODE_DD = 2, LNS_MODE_RESIDUAL = 3 };
 enum {
   LNS_PRECOND_BJAC = 0,     /* block Jacobi whose blocks are single cells and whole fracture segments
                                (block tridiagonal along each segment) */
@@ -176,7 +182,7 @@ lns_status lns_timestep(lns_model* model, double dt, lns_step_stats* out);
 
 /* One Newton iteration of Algorithm 1 (or standard Newton): opens a timestep of size dt
  * if none is open, runs lines 4-21 once, and closes the timestep once the loop condition
- * (is_expand or not converged) is false.  Not available in LNS_MODE_DD. */
+ * (is_expand or not converged) is false.  Not available in LNS_MODE_DD or LNS_MODE_RESIDUAL. */
 lns_status lns_newton_iter(lns_model* model, double dt, lns_iter_stats* out);
 
 /* Algorithm 1, lines 8-20 (steps 3-4 of Section 4.3) on a caller-given update: with

@@ -20,6 +20,8 @@
 // column scan and is written here too.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "lns_internal.cuh"
 
 namespace lns {
@@ -231,6 +233,73 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double p_
 }
 
 // ---------------------------------------------------------------------------------------
+// Residual-based active sets (the estimate the paper compares against, Section 1 / 4.2): the
+// full-domain residual at the current iterate, one thread per cell (both phases), and the cells
+// whose CNV_i = max_l |R_l,i| dt / (PV_i b_l,i) >= tol_cnv go to the `reach` bitset and frontier
+// list 0 (the seed of the m-layer inflation).  Max CNV over all cells to the counters.  The same
+// residual terms as k_assemble, without the Jacobian.
+// ---------------------------------------------------------------------------------------
+constexpr int kResBlk = 128;
+
+__global__ void __launch_bounds__(kResBlk) k_residual_flags(Dev d, FluidK F, double tol_cnv) {
+  const double dt = d.stepp[0], inv_dt = d.stepp[1];
+  const Fluid& f = F.f;
+  const double g = f.gravity;
+  double cmax = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
+    const double p_i = d.p[i], sw_i = d.sw[i], z_i = d.depth[i], pvr = d.pv_ref[i];
+    const PhaseProps qo = phase_props(F, p_i, sw_i, 0), qw = phase_props(F, p_i, sw_i, 1);
+    const double pv = pvr * (1.0 + f.c_r * (p_i - f.p_ref));
+    const double pn_i = d.pn[i], swn = d.swn[i];
+    const double pvn = pvr * (1.0 + f.c_r * (pn_i - f.p_ref));
+    const double bno = f.b_o_ref * (1.0 + f.c_o * (pn_i - f.p_ref));
+    const double bnw = f.b_w_ref * (1.0 + f.c_w * (pn_i - f.p_ref));
+    double Ro = (pv * qo.b * (1.0 - sw_i) - pvn * bno * (1.0 - swn)) * inv_dt;
+    double Rw = (pv * qw.b * sw_i - pvn * bnw * swn) * inv_dt;
+    for (int e = d.row_ptr[i]; e < d.row_ptr[i + 1]; e++) {
+      const int j = d.nbr[e];
+      const double T_e = d.trans[e], p_j = d.p[j], sw_j = d.sw[j];
+      const PhaseProps jo = phase_props(F, p_j, sw_j, 0), jw = phase_props(F, p_j, sw_j, 1);
+      const double dz = z_i - d.depth[j];
+      {
+        const double dphi = (p_i - p_j) - (g * (0.5 * (qo.rho + jo.rho))) * dz;
+        const bool up_i = dphi > 0.0 || (dphi == 0.0 && i < j);
+        Ro += T_e * (up_i ? qo.mob : jo.mob) * dphi;
+      }
+      {
+        const double dphi = (p_i - p_j) - (g * (0.5 * (qw.rho + jw.rho))) * dz;
+        const bool up_i = dphi > 0.0 || (dphi == 0.0 && i < j);
+        Rw += T_e * (up_i ? qw.mob : jw.mob) * dphi;
+      }
+    }
+    for (int w = d.well_of_cell[i]; w >= 0; w = d.well_next[w]) {
+      const double dpw = p_i - d.well_bhp[w];
+      if (dpw > 0.0) {
+        const double wi = d.well_wi[w];
+        Ro += wi * qo.mob * dpw;
+        Rw += wi * qw.mob * dpw;
+      }
+    }
+    const double c0 = fabs(Ro) * dt / (pv * qo.b), c1 = fabs(Rw) * dt / (pv * qw.b);
+    const double c = c0 > c1 ? c0 : c1;
+    if (c >= tol_cnv) {
+      atomicOr(&d.reach[i >> 5], 1u << (i & 31));
+      d.fr0[atomicAdd(&d.ctr->n_frontier[0], 1)] = i;  // list order does not change the dilation
+    }
+    cmax = fmax(cmax, c);
+  }
+  __shared__ double sh[kResBlk / 32];
+  for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = cmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int w = 0; w < kResBlk / 32; w++) mx = fmax(mx, sh[w]);
+    atomicMax(&d.ctr->cnv_bits, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Fracture-line blocks: consecutive compact rows that are consecutive cells of one fracture
 // segment form a block-tridiagonal block of the preconditioner (block Jacobi whose blocks
 // are single cells or whole fracture segments).  The assembly marks the line rows, links each
@@ -376,6 +445,19 @@ cudaError_t launch_assemble(const Dev& d, double p_scale, int fp32, int lines, i
     k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, p_scale, 1.0 / p_scale, lines, debug);
   else
     k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, p_scale, 1.0 / p_scale, lines, debug);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_flags(const Dev& d, double tol_cnv, LaunchCfg c) {
+  if (d.n == 0) return cudaSuccess;
+  FluidK F;
+  F.f = d.fl;
+  F.inv_span = 1.0 / (1.0 - d.fl.swc - d.fl.sor);
+  F.inv_mu[0] = 1.0 / d.fl.mu_o;
+  F.inv_mu[1] = 1.0 / d.fl.mu_w;
+  const int grid = std::min((d.n + kResBlk - 1) / kResBlk, 16 * c.sms);
+  count_launches(1);
+  k_residual_flags<<<grid, kResBlk, 0, c.stream>>>(d, F, tol_cnv);
   return cudaGetLastError();
 }
 

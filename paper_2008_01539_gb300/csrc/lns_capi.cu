@@ -378,6 +378,9 @@ lns_status open_step(lns_model* m, double dt) {
   if (m->o.mode == LNS_MODE_FULL) {
     CK(lns::launch_words_op(d, lns::kAll, d.va, nullptr, nullptr, c));
     CK(lns::launch_words_op(d, lns::kAll, d.uni, nullptr, nullptr, c));
+  } else if (m->o.mode == LNS_MODE_RESIDUAL) {  // the first set comes from the first residual
+    CK(cudaMemsetAsync(d.uni, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+    CK(cudaMemsetAsync(d.va, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
   } else {
     CK(cudaMemsetAsync(d.uni, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
     TRY(initial_set(m, d.va));
@@ -528,6 +531,78 @@ lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
     st->step_done = 0;
   }
   return krylov_outcome(m);
+}
+
+// ---------------------------------------------------------------------------------------
+// Residual-based active sets (LNS_MODE_RESIDUAL; the estimate the paper compares against,
+// Section 1 / Section 4.2).  Each iteration: the full-domain residual at u^nu flags the
+// unconverged cells (CNV_i >= tol_cnv); converged when none is and (nu = 0 or) the last update's
+// max |dp| < tol_dp; else V_A = the flagged cells inflated by m layers (an empty flagged set keeps
+// V_A), one local solve on V_A, u += R_A^T du_A.
+// ---------------------------------------------------------------------------------------
+lns_status residual_timestep(lns_model* m, double dt, lns_step_stats* out) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  TRY(open_step(m, dt));
+  const IterCounters& h = *d.ctr_h;
+  double last_dp = 0.0;
+  lns_status s = LNS_OK;
+  for (int it = 0;; it++) {
+    TRY(reset_iter(m));
+    CK(lns::launch_residual_flags(d, m->o.tol_cnv, c));
+    TRY(read_counters(m));
+    const int n_unconv = h.n_frontier[0];
+    const double cnv = bits2d(h.cnv_bits);
+    if (n_unconv == 0 && (it == 0 || last_dp < m->o.tol_dp)) {
+      m->converged = 1;
+      break;
+    }
+    if (it >= m->o.max_newton) {
+      s = fail(LNS_ENOCONV, "Newton loop reached max_newton");
+      break;
+    }
+    if (n_unconv > 0) {  // reach = flagged cells; inflate by m layers from frontier list 0
+      TRY(dilate(m, m->o.m_layers));
+      CK(lns::launch_words_op(d, lns::kCopy, d.va, d.reach, nullptr, c));
+    }
+    CK(lns::launch_words_op(d, lns::kOr, d.uni, d.uni, d.va, c));
+    auto solve = [&]() -> lns_status {
+      TRY(reset_iter(m));
+      TRY(local_solve(m, 0));
+      PendingEvent pe;
+      TRY(ev_begin(m, KC_UPDATE, &pe));
+      CK(lns::launch_flag(d, nullptr, 1, 0, 0, m->o.eps_p, m->o.eps_sw, eff_p_scale(m), m->o.sat_chop,
+                          m->o.krylov_fp32, d.kx, m->o.krylov_fail_rtol, c));
+      TRY(ev_end(m, &pe, 0.0, 0.0));
+      CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+      CK(cudaStreamSynchronize(m->stream));
+      annotate_pending(m);
+      return ev_flush(m);
+    };
+    TRY(solve());
+    int kit_fp32 = 0;
+    if (wants_fp64_retry(m)) {
+      kit_fp32 = h.krylov_iters;
+      TRY(with_fp64_krylov(m, solve));
+      m->cur.fp64_retries += 1;
+    }
+    m->cur.iterations += 1;
+    m->cur.krylov_iters += kit_fp32 + h.krylov_iters;
+    m->cur.cell_updates += h.n_active;
+    last_dp = bits2d(h.max_dp_bits);
+    m->cur.last_max_dp = last_dp;
+    m->cur.last_cnv = cnv;
+    s = krylov_outcome(m);
+    if (s != LNS_OK) break;
+  }
+  if (s == LNS_OK) {
+    TRY(close_step(m));
+  } else {
+    m->step_open = false;
+  }
+  m->cur.status = s;
+  if (out) *out = m->cur;
+  return s;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -682,7 +757,7 @@ lns_status check_model(const lns_model* m) {
 
 lns_status validate_options(const lns_options* o) {
   if (!o) return fail(LNS_EINVAL, "options is NULL");
-  if (o->mode < 0 || o->mode > 2) return fail(LNS_EINVAL, "mode must be 0, 1 or 2");
+  if (o->mode < 0 || o->mode > 3) return fail(LNS_EINVAL, "mode must be 0, 1, 2 or 3");
   if (o->m_layers < 0 || o->m_layers > 100000) return fail(LNS_EINVAL, "m_layers out of range");
   if (o->max_newton < 1 || o->max_dd_outer < 1) return fail(LNS_EINVAL, "max_newton and max_dd_outer must be >= 1");
   if (o->krylov_maxit < 1) return fail(LNS_EINVAL, "krylov_maxit must be >= 1");
@@ -1110,7 +1185,8 @@ struct NvtxRange {  // a named range on the profiler's timeline (no-op without a
 lns_status lns_newton_iter(lns_model* m, double dt, lns_iter_stats* out) {
   TRY(check_model(m));
   NvtxRange range("lns_newton_iter");
-  if (m->o.mode == LNS_MODE_DD) return fail(LNS_ESTATE, "lns_newton_iter is not available in LNS_MODE_DD");
+  if (m->o.mode == LNS_MODE_DD || m->o.mode == LNS_MODE_RESIDUAL)
+    return fail(LNS_ESTATE, "lns_newton_iter is not available in LNS_MODE_DD or LNS_MODE_RESIDUAL");
   if (m->d.n == 0) return fail(LNS_EINVAL, "empty model");
   if (!m->step_open) TRY(open_step(m, dt));
   lns_iter_stats st{};
@@ -1145,6 +1221,7 @@ lns_status lns_timestep(lns_model* m, double dt, lns_step_stats* out) {
   }
   if (m->o.mode == LNS_MODE_DD) return dd_timestep(m, dt, out);
   if (m->step_open) return fail(LNS_ESTATE, "a timestep opened by lns_newton_iter is still open");
+  if (m->o.mode == LNS_MODE_RESIDUAL) return residual_timestep(m, dt, out);
   TRY(open_step(m, dt));
   lns_status s = LNS_OK;
   for (;;) {

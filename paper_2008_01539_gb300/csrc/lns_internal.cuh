@@ -143,6 +143,7 @@ cudaError_t launch_assemble(const Dev& d, double p_scale, int fp32, int lines, i
 cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c);
 
 // k_krylov.cu
+cudaError_t launch_residual_flags(const Dev& d, double tol_cnv, LaunchCfg c);
 cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, LaunchCfg c);
 int krylov_grid(int fp32, int sms);
 

@@ -19,7 +19,7 @@ from . import build as _build
 PSI = 6894.757293168
 
 LNS_OK, LNS_EINVAL, LNS_ENOMEM, LNS_ECUDA, LNS_ENOCONV, LNS_EKRYLOV, LNS_ETIMEOUT, LNS_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-LNS_MODE_FULL, LNS_MODE_LOCAL, LNS_MODE_DD = 0, 1, 2
+LNS_MODE_FULL, LNS_MODE_LOCAL, LNS_MODE_DD, LNS_MODE_RESIDUAL = 0, 1, 2, 3
 LNS_PRECOND_BJAC, LNS_PRECOND_BJAC_CELL = 0, 1
 _STATUS = {0: "LNS_OK", -1: "LNS_EINVAL", -2: "LNS_ENOMEM", -3: "LNS_ECUDA", -4: "LNS_ENOCONV",
            -5: "LNS_EKRYLOV", -6: "LNS_ETIMEOUT", -7: "LNS_ESTATE"}

@@ -185,6 +185,50 @@ def test_timesteps_fp32_krylov_within_1e6(mode):
     g.close()
 
 
+@pytest.mark.parametrize("case_fn", [cg.config0, lambda: cg.small_dfn(n_steps=6)])
+def test_residual_sets_match_oracle_fp64(case_fn):
+    """Residual-based active sets (mode 3) at the default tolerances, where the sets are local:
+    the same number of iterations and the same active-set sizes per step as the oracle, and the
+    same fields to 1e-7."""
+    case = case_fn()
+    ref = O.Sim(case, O.Options(mode=3, m_layers=1))
+    g = lns.Model(case, lns.Options(mode=3, m_layers=1, krylov_rtol=1e-12, krylov_maxit=5000))
+    local = False
+    for dt in case.dt_schedule:
+        a = g.lns_timestep(dt)
+        b = ref.timestep(dt)
+        assert a["status"] == 0 and b["status"] == 0
+        assert a["iterations"] == b["iterations"] and a["cell_updates"] == b["cell_updates"], (a, b)
+        local |= 0 < b["cell_updates"] < b["iterations"] * case.n
+        p, sw = g.lns_get_state()
+        assert np.max(np.abs(p - ref.p) / ref.p) < 1e-7
+        assert np.max(np.abs(sw - ref.sw)) < 1e-7 * 0.25
+    assert local
+    g.close()
+
+
+def test_residual_sets_fp32_krylov_within_newton_tolerance():
+    case = cg.config0()
+    ref = O.Sim(case, O.Options(mode=3, m_layers=1))
+    g = lns.Model(case, lns.Options(mode=3, m_layers=1, krylov_fp32=1, krylov_rtol=1e-5))
+    for dt in case.dt_schedule:
+        assert g.lns_timestep(dt)["status"] == 0
+        assert ref.timestep(dt)["status"] == 0
+    p, sw = g.lns_get_state()
+    assert np.max(np.abs(p - ref.p)) < 0.3 * cg.PSI
+    assert np.max(np.abs(sw - ref.sw)) < 1e-5
+    g.close()
+
+
+def test_residual_mode_rejects_newton_iter():
+    case = cg.config0()
+    g = lns.Model(case, lns.Options(mode=3))
+    with pytest.raises(lns.LnsError) as e:
+        g.lns_newton_iter(case.dt_schedule[0])
+    assert e.value.status == lns.LNS_ESTATE
+    g.close()
+
+
 def test_newton_iter_steps_through_algorithm1():
     case = cg.small_dfn(n_steps=2)
     ref = O.Sim(case, O.Options(mode=1, **TIGHT))
