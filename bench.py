@@ -645,8 +645,20 @@ def bench_ours(args, rank, world, local):
                                    "newton_iterations_per_case": sum(s["iterations"] for st in fst for s in st) / len(ft),
                                    "max_abs_dp_vs_localized_psi": float(np.max(np.abs(pf - p_final))) / lns.PSI}
             line["speedup_vs_full_newton"] = tf / line["case_time_s"]
-            # the residual-based estimate the paper compares against (unconverged cells + 1 layer)
-            rt, rst, pr, swr = variant(lns.Options(**{**opts.__dict__, "mode": lns.LNS_MODE_RESIDUAL, "m_layers": 1}))
+            # the residual-based estimate the paper compares against (unconverged cells + 1 layer);
+            # it grows the set one layer per iteration, so long steps take many more iterations
+            try:
+                rm = lns.Model(case, lns.Options(**{**opts.__dict__, "mode": lns.LNS_MODE_RESIDUAL, "m_layers": 1,
+                                                    "max_newton": 3000}))
+                for dt in case.dt_schedule[:2]:  # warm-up
+                    rm.lns_timestep(float(dt))
+                rt, rst = time_case(rm, case, 1, flush, stream)
+                pr, swr = rm.lns_get_state()
+                rm.close()
+            except lns.LnsError as err:
+                rt = None
+                line["residual_sets"] = {"failed": str(err)}
+        if args.mode != "full" and rt is not None:
             line["residual_sets"] = {
                 "case_time_s": statistics.mean(rt), "unit": UNIT,
                 "value": sum(s["cell_updates"] for st in rst for s in st) / sum(rt),
@@ -655,7 +667,8 @@ def bench_ours(args, rank, world, local):
                 "M_A_per_case": sum(s["cell_updates"] for st in rst for s in st) / len(rt) / case.n,
                 "max_abs_dp_vs_localized_psi": float(np.max(np.abs(pr - p_final))) / lns.PSI,
                 "note": "active set = cells with CNV >= tol_cnv on the full-domain residual, plus 1 layer "
-                        "(the estimate the paper compares against); same Krylov settings as the headline"}
+                        "(the estimate the paper compares against); same Krylov settings as the headline, "
+                        "max_newton 3000, one timed case"}
         # end to end through the C ABI with host buffers
         p_h = torch.from_numpy(np.ascontiguousarray(case.p0)).pin_memory()
         s_h = torch.from_numpy(np.ascontiguousarray(case.sw0)).pin_memory()
