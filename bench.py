@@ -645,6 +645,18 @@ def bench_ours(args, rank, world, local):
                                    "newton_iterations_per_case": sum(s["iterations"] for st in fst for s in st) / len(ft),
                                    "max_abs_dp_vs_localized_psi": float(np.max(np.abs(pf - p_final))) / lns.PSI}
             line["speedup_vs_full_newton"] = tf / line["case_time_s"]
+            # Algorithm 2 (adaptive nonlinear domain decomposition) on the same case
+            try:
+                dt_, dst, pd, _ = variant(lns.Options(**{**opts.__dict__, "mode": lns.LNS_MODE_DD}))
+                line["algorithm2_dd"] = {
+                    "case_time_s": statistics.mean(dt_), "unit": UNIT,
+                    "value": sum(s["cell_updates"] for st in dst for s in st) / sum(dt_),
+                    "local_solves_per_case": sum(s["iterations"] for st in dst for s in st) / len(dt_),
+                    "krylov_iterations_per_case": sum(s["krylov_iters"] for st in dst for s in st) / len(dt_),
+                    "M_A_per_case": sum(s["cell_updates"] for st in dst for s in st) / len(dt_) / case.n,
+                    "max_abs_dp_vs_localized_psi": float(np.max(np.abs(pd - p_final))) / lns.PSI}
+            except lns.LnsError as err:
+                line["algorithm2_dd"] = {"failed": str(err)}
             # the residual-based estimate the paper compares against (unconverged cells + 1 layer);
             # it grows the set one layer per iteration, so long steps take many more iterations
             try:

@@ -309,16 +309,18 @@ __global__ void __launch_bounds__(kResBlk) k_residual_flags(Dev d, FluidK F, dou
 //   D'_0 = I, D'_t = I - L_t D'_{t-1}^{-1} U_{t-1},  A_t = -D'_t^{-1} L_t,  G_t = D'_t^{-1} U_t
 // so that M^{-1} r is  w_t = D'_t^{-1} r_t + A_t w_{t-1},  z_t = w_t - G_t z_{t+1}.
 // ---------------------------------------------------------------------------------------
-// One warp per line.  The lanes load the line's coupling blocks (U_t: row t -> t+1,
-// L_t: row t -> t-1) 32 rows at a time into shared memory, in FP32; lane 0 runs the block
-// Thomas recurrence over the staged rows; the warp stores D'^{-1}, A and G (FP32) per row.
+// One warp per line.  The lanes load the coupling blocks of a whole line block (up to
+// kMaxLineRows rows, four rows per lane, all loads in flight together) into shared memory, in
+// FP32; lane 0 runs the block Thomas recurrence over the staged rows; the warp stores D'^{-1}, A
+// and G (FP32) per row.
 constexpr int kLineWarps = 4;
 constexpr int kMaxLineRows = kLineBlockRows;
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
-  __shared__ float s_in[kLineWarps][32][8];
-  __shared__ float s_out[kLineWarps][32][12];
+  constexpr int kQ = kMaxLineRows / 32;  // rows per lane in one block
+  __shared__ float s_in[kLineWarps][kMaxLineRows][8];
+  __shared__ float s_out[kLineWarps][kMaxLineRows][12];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -330,46 +332,63 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
   float* lg = (float*)d.line_g;
   for (int l = gwarp; l < nl; l += nwarps) {
     const int k0 = d.line_start[l];
-    // line length: the start row plus the continuation rows that follow it
+    // line length: the start row plus the continuation rows that follow it (kMaxLineRows rows per
+    // round of loads)
     int len = 1;
-    for (int base = k0 + 1;; base += 32) {
-      const int k = base + lane;
-      const bool cont = k < nA && d.line_row_flag[k] == 2;
-      const unsigned m = __ballot_sync(0xffffffffu, cont);
-      if (m == 0xffffffffu) {
-        len += 32;
-        continue;
-      }
-      len += __ffs(~m) - 1;
-      break;
-    }
-    float Gp[4] = {0.f, 0.f, 0.f, 0.f};  // G of the previous row (lane 0)
-    for (int base = 0; base < len; base += 32) {
-      const int t = base + lane;
-      float U[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
-      if (t < len) {
-        const int2 lk = d.lnk[k0 + t];
-        if (t + 1 < len && (t + 1) % kMaxLineRows != 0) {
-          const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)lk.y];
-          U[0] = (float)b.a, U[1] = (float)b.b, U[2] = (float)b.c, U[3] = (float)b.d;
-        }
-        if (t >= 1 && t % kMaxLineRows != 0) {
-          const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)lk.x];
-          L[0] = (float)b.a, L[1] = (float)b.b, L[2] = (float)b.c, L[3] = (float)b.d;
-        }
-      }
+    for (int base = k0 + 1;; base += kMaxLineRows) {
+      bool cont[kQ];
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        s_in[wib][lane][q] = U[q];
-        s_in[wib][lane][4 + q] = L[q];
+      for (int q = 0; q < kQ; q++) {
+        const int k = base + 32 * q + lane;
+        cont[q] = k < nA && d.line_row_flag[k] == 2;
+      }
+      bool ended = false;
+#pragma unroll
+      for (int q = 0; q < kQ; q++) {
+        if (ended) break;  // uniform
+        const unsigned m = __ballot_sync(0xffffffffu, cont[q]);
+        if (m == 0xffffffffu) {
+          len += 32;
+        } else {
+          len += __ffs(~m) - 1;
+          ended = true;
+        }
+      }
+      if (ended) break;
+    }
+    // each block of up to kMaxLineRows rows: its couplings (U_t: row t -> t+1, L_t: row t -> t-1)
+    // are staged in FP32 (all loads of the block issued together), lane 0 runs the recurrence, the
+    // lanes store D'^{-1}, A and G.  Couplings across a cut are left out, so a block starts from
+    // D'_0 = I.
+    for (int b0 = 0; b0 < len; b0 += kMaxLineRows) {
+      const int blen = min(kMaxLineRows, len - b0);
+#pragma unroll
+      for (int q = 0; q < kQ; q++) {
+        const int j = 32 * q + lane;
+        float U[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
+        if (j < blen) {
+          const int2 lk = d.lnk[k0 + b0 + j];
+          if (j + 1 < blen) {
+            const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)lk.y];
+            U[0] = (float)b.a, U[1] = (float)b.b, U[2] = (float)b.c, U[3] = (float)b.d;
+          }
+          if (j >= 1) {
+            const Blk4<T> b = *(const Blk4<T>*)&blocks[4 * (size_t)lk.x];
+            L[0] = (float)b.a, L[1] = (float)b.b, L[2] = (float)b.c, L[3] = (float)b.d;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          s_in[wib][j][c] = U[c];
+          s_in[wib][j][4 + c] = L[c];
+        }
       }
       __syncwarp();
       if (lane == 0) {
-        const int cnt = min(32, len - base);
-        for (int j = 0; j < cnt; j++) {
-          const int tt = base + j;
+        float Gp[4] = {0.f, 0.f, 0.f, 0.f};  // G of the previous row
+        for (int j = 0; j < blen; j++) {
           float Di[4], A[4];
-          if (tt == 0) {
+          if (j == 0) {
             Di[0] = 1.f, Di[1] = 0.f, Di[2] = 0.f, Di[3] = 1.f;
             A[0] = A[1] = A[2] = A[3] = 0.f;
           } else {
@@ -393,23 +412,25 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
           G[2] = Di[2] * Ut[0] + Di[3] * Ut[2];
           G[3] = Di[2] * Ut[1] + Di[3] * Ut[3];
 #pragma unroll
-          for (int q = 0; q < 4; q++) {
-            s_out[wib][j][q] = Di[q];
-            s_out[wib][j][4 + q] = A[q];
-            s_out[wib][j][8 + q] = G[q];
-            Gp[q] = G[q];
+          for (int c = 0; c < 4; c++) {
+            s_out[wib][j][c] = Di[c];
+            s_out[wib][j][4 + c] = A[c];
+            s_out[wib][j][8 + c] = G[c];
+            Gp[c] = G[c];
           }
         }
       }
       __syncwarp();
-      if (t < len) {
-        const size_t k = (size_t)(k0 + t);
-        *(float4*)&ldinv[4 * k] = make_float4(s_out[wib][lane][0], s_out[wib][lane][1], s_out[wib][lane][2],
-                                               s_out[wib][lane][3]);
-        *(float4*)&la[4 * k] = make_float4(s_out[wib][lane][4], s_out[wib][lane][5], s_out[wib][lane][6],
-                                            s_out[wib][lane][7]);
-        *(float4*)&lg[4 * k] = make_float4(s_out[wib][lane][8], s_out[wib][lane][9], s_out[wib][lane][10],
-                                            s_out[wib][lane][11]);
+#pragma unroll
+      for (int q = 0; q < kQ; q++) {
+        const int j = 32 * q + lane;
+        if (j < blen) {
+          const size_t k = (size_t)(k0 + b0 + j);
+          const float* o = s_out[wib][j];
+          *(float4*)&ldinv[4 * k] = make_float4(o[0], o[1], o[2], o[3]);
+          *(float4*)&la[4 * k] = make_float4(o[4], o[5], o[6], o[7]);
+          *(float4*)&lg[4 * k] = make_float4(o[8], o[9], o[10], o[11]);
+        }
       }
       __syncwarp();
     }

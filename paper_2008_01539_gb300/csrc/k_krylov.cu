@@ -23,10 +23,12 @@
 // recurrence residual stays the true residual of x up to FP64 rounding.  r~ is rebuilt each
 // iteration from the directly preconditioned s, so the FP32 rounding of M^{-1} does not accumulate.
 //
-// Ownership: non-line rows go to threads in contiguous chunks spread over all SMs; the rows of a
-// fracture line block go to one warp (line l lives in block l mod gridDim), lane t holding rows
-// t, t+32, t+64, t+96.  Matrix rows (columns and blocks) and line factors are staged in shared
-// memory once per solve.  Reductions: per-row products in FP64; across lanes, warps and blocks in
+// Ownership: each block owns a contiguous chunk of rows whose ends never split a fracture-line
+// block; its threads take the chunk's rows, leave the line-solve inputs in a block buffer, and
+// after a block barrier its warps apply M^{-1} to the chunk's line blocks (short blocks packed into
+// warp segments, long ones a warp each).  Matrix rows (columns and blocks), row references and line
+// factors are staged in shared memory once per solve.  Reductions: per-row products in FP64 (FP32
+// path: exact FP32 products in double-float); across lanes, warps and blocks in
 // double-float (two FP32 words, Knuth's TwoSum), after scaling by an exact power of two near
 // 1/||b||^2.  Every block sums the block partials in the same order, so all blocks hold identical
 // scalars (computed once per block by thread 0: FP64 division is a long sequence here).
