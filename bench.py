@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-Newton-updates/s & case time, localized vs full Newton; p99 req latency"
 UNIT = "cell-Newton-updates/s"
 FALLBACK_HBM_GBS = 6800.0
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (vector and tensor), see the design doc
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 rate (vector and tensor alike)
 L2_FLUSH_BYTES = 256 << 20
 
 
