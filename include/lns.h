@@ -180,6 +180,37 @@ lns_status lns_set_options(lns_model* model, const lns_options* opts);
  * Algorithm 1 or 2).  On LNS_ENOCONV the state is left at the last iterate. */
 lns_status lns_timestep(lns_model* model, double dt, lns_step_stats* out);
 
+/* Adaptive time stepping over an interval.  The paper advances with simple time stepping
+ * (Section 5); this is the usual controller around lns_timestep: a step that fails to converge
+ * (LNS_ENOCONV, or LNS_EKRYLOV from the local solve) is undone -- state and the support set that
+ * seeds the next step's active set are restored -- and retried with dt * cut; a step that
+ * converges in at most easy_iters Newton iterations lets the next one grow to dt * grow (at most
+ * dt_max).  The last step is shortened to end exactly at t_span. */
+typedef struct {
+  double dt_init;        /* first step (s) */
+  double dt_min;         /* give up (LNS_ENOCONV, state at the last accepted step) below this (s) */
+  double dt_max;         /* largest step (s) */
+  double grow;           /* >= 1 */
+  double cut;            /* in (0, 1) */
+  int32_t easy_iters;    /* Newton iterations (Algorithm 2: local solves) of an easy step */
+} lns_dt_control;
+
+typedef struct {
+  int32_t status;        /* lns_status of the call */
+  int32_t steps;         /* accepted steps */
+  int32_t cuts;          /* failed (undone) steps */
+  int32_t iterations;    /* Newton iterations over all steps, failed ones included */
+  int64_t krylov_iters;
+  int64_t cell_updates;
+  double t_done;         /* time advanced (s) */
+  double dt_next;        /* the controller's next step (s), for a following call */
+} lns_advance_stats;
+
+/* Advance the model by t_span seconds with the controller above.  Errors other than LNS_ENOCONV /
+ * LNS_EKRYLOV return at once (the state is then that of the failed step).  ctl NULL: dt_init =
+ * t_span, dt_min = t_span / 1024, dt_max = t_span, grow 2, cut 0.5, easy_iters 4. */
+lns_status lns_advance(lns_model* model, double t_span, const lns_dt_control* ctl, lns_advance_stats* out);
+
 /* One Newton iteration of Algorithm 1 (or standard Newton): opens a timestep of size dt
  * if none is open, runs lines 4-21 once, and closes the timestep once the loop condition
  * (is_expand or not converged) is false.  Not available in LNS_MODE_DD or LNS_MODE_RESIDUAL. */

@@ -303,3 +303,35 @@ class Sim:
 
     def run(self, dts) -> list:
         return [self.timestep(float(dt)) for dt in dts]
+
+    def advance(self, t_span: float, dt_init: float, dt_min: float, dt_max: float, grow: float = 2.0,
+                cut: float = 0.5, easy_iters: int = 4) -> dict:
+        """Advance by t_span with the usual cut/grow controller: a step that fails (Newton
+        iteration limit or a singular local solve) is undone and retried with dt * cut; a step of
+        at most easy_iters iterations lets the next grow to min(dt * grow, dt_max); the last step
+        ends exactly at t_span.  Returns counts, the time advanced and the next dt."""
+        out = dict(status=0, steps=0, cuts=0, iterations=0, krylov_iters=0, cell_updates=0, t_done=0.0,
+                   dt_next=0.0, dts=[])
+        t, dt = 0.0, min(dt_init, dt_max)
+        while t < t_span:
+            h = min(dt, t_span - t)
+            saved = (self.p.copy(), self.sw.copy(), self.prev_supp.copy(), self.has_prev.value)
+            st = self.timestep(h)
+            out["iterations"] += st["iterations"]
+            out["cell_updates"] += st["cell_updates"]
+            if st["status"] == 0:
+                t = t_span if h == t_span - t else t + h
+                out["steps"] += 1
+                out["dts"].append(h)
+                if st["iterations"] <= easy_iters:
+                    dt = min(dt * grow, dt_max)
+                continue
+            self.p, self.sw, self.prev_supp = saved[0], saved[1], saved[2]
+            self.has_prev.value = saved[3]
+            out["cuts"] += 1
+            dt = h * cut
+            if dt < dt_min:
+                out["status"] = -4
+                break
+        out["t_done"], out["dt_next"] = t, dt
+        return out

@@ -92,6 +92,8 @@ struct lns_model {
   double dt_dev = -1.0;
   // one Newton iteration captured as a CUDA graph (single-stream models without profiling)
   bool graph_ok = true;
+  double* ck_state = nullptr;  // lns_advance: p and Sw at the start of the step being tried
+  uint32_t* ck_prev = nullptr;  // lns_advance: the support set seeding that step
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_kernels = 0;
@@ -1210,6 +1212,66 @@ lns_status lns_newton_iter(lns_model* m, double dt, lns_iter_stats* out) {
   }
   if (out) *out = st;
   return LNS_OK;
+}
+
+lns_status lns_advance(lns_model* m, double t_span, const lns_dt_control* ctl, lns_advance_stats* out) {
+  TRY(check_model(m));
+  if (out) std::memset(out, 0, sizeof(*out));
+  if (m->step_open) return fail(LNS_ESTATE, "a timestep opened by lns_newton_iter is still open");
+  if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(LNS_EINVAL, "t_span must be positive and finite");
+  lns_dt_control c{t_span, t_span / 1024.0, t_span, 2.0, 0.5, 4};
+  if (ctl) c = *ctl;
+  if (!(c.dt_init > 0.0) || !(c.dt_min > 0.0) || !(c.dt_max >= c.dt_min) || !(c.grow >= 1.0) || !(c.cut > 0.0) ||
+      !(c.cut < 1.0) || !std::isfinite(c.dt_init) || !std::isfinite(c.dt_max) || !std::isfinite(c.grow))
+    return fail(LNS_EINVAL, "bad time-step controller");
+  Dev& d = m->d;
+  const size_t n = (size_t)d.n;
+  if (!m->ck_state) TRY(dalloc_t(m, 2 * std::max<size_t>(n, 1), &m->ck_state));
+  if (!m->ck_prev) TRY(dalloc_t(m, (size_t)std::max(d.W, 1), &m->ck_prev));
+  lns_advance_stats a{};
+  double t = 0.0, dt = std::min(c.dt_init, c.dt_max);
+  lns_status s = LNS_OK;
+  while (t < t_span) {
+    const double h = std::min(dt, t_span - t);
+    if (n > 0) {
+      CK(cudaMemcpyAsync(m->ck_state, d.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+      CK(cudaMemcpyAsync(m->ck_state + n, d.sw, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+      CK(cudaMemcpyAsync(m->ck_prev, d.prev, sizeof(uint32_t) * (size_t)d.W, cudaMemcpyDeviceToDevice, m->stream));
+    }
+    const int had_prev = m->has_prev;
+    lns_step_stats st{};
+    s = lns_timestep(m, h, &st);
+    a.iterations += st.iterations;
+    a.krylov_iters += st.krylov_iters;
+    a.cell_updates += st.cell_updates;
+    if (s == LNS_OK) {
+      t = (h == t_span - t) ? t_span : t + h;
+      a.steps += 1;
+      if (st.iterations <= c.easy_iters) dt = std::min(dt * c.grow, c.dt_max);
+      continue;
+    }
+    if (s != LNS_ENOCONV && s != LNS_EKRYLOV) break;
+    // undo the failed step
+    if (n > 0) {
+      CK(cudaMemcpyAsync(d.p, m->ck_state, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+      CK(cudaMemcpyAsync(d.sw, m->ck_state + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+      CK(cudaMemcpyAsync(d.prev, m->ck_prev, sizeof(uint32_t) * (size_t)d.W, cudaMemcpyDeviceToDevice, m->stream));
+    }
+    m->has_prev = had_prev;
+    a.cuts += 1;
+    dt = h * c.cut;
+    if (dt < c.dt_min) {
+      s = fail(LNS_ENOCONV, "time step fell below dt_min");
+      break;
+    }
+    s = LNS_OK;
+  }
+  TRY(sync(m));
+  a.status = s;
+  a.t_done = t;
+  a.dt_next = dt;
+  if (out) *out = a;
+  return s;
 }
 
 lns_status lns_timestep(lns_model* m, double dt, lns_step_stats* out) {

@@ -75,6 +75,17 @@ class lns_step_stats(C.Structure):
                 ("last_max_dp", C.c_double), ("last_cnv", C.c_double)]
 
 
+class lns_dt_control(C.Structure):
+    _fields_ = [("dt_init", C.c_double), ("dt_min", C.c_double), ("dt_max", C.c_double), ("grow", C.c_double),
+                ("cut", C.c_double), ("easy_iters", C.c_int32)]
+
+
+class lns_advance_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("steps", C.c_int32), ("cuts", C.c_int32), ("iterations", C.c_int32),
+                ("krylov_iters", C.c_int64), ("cell_updates", C.c_int64), ("t_done", C.c_double),
+                ("dt_next", C.c_double)]
+
+
 class lns_server_options(C.Structure):
     _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
 
@@ -109,7 +120,7 @@ EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_
            "lns_launch_count", "lns_last_error", "lns_active_set_noalloc",
            "lns_server_create", "lns_server_destroy", "lns_server_add_model", "lns_server_submit",
            "lns_server_poll", "lns_server_drain", "lns_server_get_state", "lns_server_get_stats", "lns_server_now",
-           "lns_server_cancel", "lns_debug_fault"]
+           "lns_server_cancel", "lns_debug_fault", "lns_advance"]
 
 
 def library_path() -> str:
@@ -152,6 +163,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "lns_server_submit": [vp, i32, f64, C.c_int64],
         "lns_server_cancel": [vp, C.c_int64],
         "lns_debug_fault": [vp, i32],
+        "lns_advance": [vp, C.c_double, P(lns_dt_control), P(lns_advance_stats)],
         "lns_server_poll": [vp, P(lns_completion), i32, f64, P(i32)],
         "lns_server_drain": [vp, f64],
         "lns_server_get_state": [vp, i32, vp, vp],
@@ -332,6 +344,18 @@ class Model:
         d = _as_dict(st)
         d["rc"] = rc
         return d
+
+    def lns_advance(self, t_span: float, dt_init: Optional[float] = None, dt_min: Optional[float] = None,
+                    dt_max: Optional[float] = None, grow: float = 2.0, cut: float = 0.5, easy_iters: int = 4,
+                    allow_noconv: bool = False) -> Dict:
+        """Advance by t_span seconds with the cut/grow time-step controller (lns_advance)."""
+        ctl = lns_dt_control(float(dt_init if dt_init is not None else t_span),
+                             float(dt_min if dt_min is not None else t_span / 1024.0),
+                             float(dt_max if dt_max is not None else t_span), float(grow), float(cut), int(easy_iters))
+        st = lns_advance_stats()
+        rc = load().lns_advance(self.h, float(t_span), C.byref(ctl), C.byref(st))
+        _check(rc, allow=(LNS_ENOCONV,) if allow_noconv else ())
+        return _as_dict(st)
 
     def lns_newton_iter(self, dt: float) -> Dict:
         st = lns_iter_stats()

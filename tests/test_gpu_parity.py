@@ -229,6 +229,32 @@ def test_residual_mode_rejects_newton_iter():
     g.close()
 
 
+def test_advance_controller_matches_oracle():
+    """lns_advance (cut on failure, grow after easy steps) against the oracle's controller: the same
+    accepted steps, cuts and Newton iterations, the same fields to 1e-7; and the undo is exact: the
+    accepted steps replayed as plain timesteps on a fresh model give the same bits."""
+    case = cg.config0()
+    span = 30.0 * 86400.0
+    ctl = dict(dt_init=span, dt_min=span / 4096, dt_max=span)
+    ref = O.Sim(case, O.Options(mode=1, max_newton=5))
+    r = ref.advance(span, **ctl)
+    assert r["status"] == 0 and r["cuts"] >= 1
+    g = lns.Model(case, lns.Options(mode=1, max_newton=5, krylov_rtol=1e-12, krylov_maxit=5000))
+    a = g.lns_advance(span, **ctl)
+    assert a["status"] == 0 and a["t_done"] == span
+    assert (a["steps"], a["cuts"], a["iterations"]) == (r["steps"], r["cuts"], r["iterations"]), (a, r)
+    p, sw = g.lns_get_state()
+    assert np.max(np.abs(p - ref.p) / ref.p) < 1e-7
+    assert np.max(np.abs(sw - ref.sw)) < 1e-7 * 0.25
+    plain = lns.Model(case, lns.Options(mode=1, max_newton=5, krylov_rtol=1e-12, krylov_maxit=5000))
+    for h in r["dts"]:
+        plain.lns_timestep(h)
+    p2, sw2 = plain.lns_get_state()
+    assert np.array_equal(p, p2) and np.array_equal(sw, sw2)
+    g.close()
+    plain.close()
+
+
 def test_newton_iter_steps_through_algorithm1():
     case = cg.small_dfn(n_steps=2)
     ref = O.Sim(case, O.Options(mode=1, **TIGHT))

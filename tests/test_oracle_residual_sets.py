@@ -70,3 +70,41 @@ def test_matches_standard_newton_config0():
     assert np.abs(res.p - full.p).max() < 0.3 * PSI
     assert np.abs(res.sw - full.sw).max() < 1e-6
     assert sum(s["cell_updates"] for s in s3) / case.n < 0.5 * sum(s["iterations"] for s in s0)
+
+
+# ---------------------------------------------------------------------------------------
+# The oracle's time-step controller (cut on failure, grow after easy steps)
+# ---------------------------------------------------------------------------------------
+def test_controller_single_step_equals_plain_timestep():
+    case = cg.config0()
+    dt = float(case.dt_schedule[3])
+    a = O.Sim(case, O.Options(mode=1))
+    out = a.advance(dt, dt_init=dt, dt_min=dt / 64, dt_max=dt)
+    b = O.Sim(case, O.Options(mode=1))
+    st = b.timestep(dt)
+    assert out["status"] == 0 and out["steps"] == 1 and out["cuts"] == 0 and out["iterations"] == st["iterations"]
+    assert np.array_equal(a.p, b.p) and np.array_equal(a.sw, b.sw)
+
+
+def test_controller_cuts_then_matches_the_same_steps_taken_plainly():
+    """With a small Newton limit a long step fails and is cut; the accepted steps, replayed as
+    plain timesteps from the same start, give the same state bit for bit (the undo is exact)."""
+    case = cg.config0()
+    o = O.Options(mode=1, max_newton=5)
+    span = 30.0 * 86400.0
+    a = O.Sim(case, o)
+    out = a.advance(span, dt_init=span, dt_min=span / 4096, dt_max=span)
+    assert out["status"] == 0 and out["cuts"] >= 1 and abs(sum(out["dts"]) - span) <= 1e-6 * span
+    b = O.Sim(case, o)
+    for h in out["dts"]:
+        assert b.timestep(h)["status"] == 0
+    assert np.array_equal(a.p, b.p) and np.array_equal(a.sw, b.sw)
+
+
+def test_controller_gives_up_below_dt_min_with_the_state_unchanged():
+    case = cg.config0()
+    a = O.Sim(case, O.Options(mode=1, max_newton=1))
+    span = 365.0 * 86400.0
+    out = a.advance(span, dt_init=span, dt_min=span / 8, dt_max=span)
+    assert out["status"] == -4 and out["steps"] == 0 and out["cuts"] >= 3
+    assert np.array_equal(a.p, case.p0) and np.array_equal(a.sw, case.sw0)
