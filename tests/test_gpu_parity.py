@@ -255,6 +255,29 @@ def test_advance_controller_matches_oracle():
     plain.close()
 
 
+def test_line_list_overflow_path_solves_the_same_system():
+    """Chunks with more line blocks than the solver lists in shared memory (1024) solve each block
+    with one warp, in table order.  Every cell active (standard Newton) and every pair of
+    consecutive cells a line block: 320k rows, ~1,050 blocks per chunk.  One Newton iteration gives
+    the same update as the same model without line blocks (a unique solution, solved to 1e-12)."""
+    import copy
+
+    base = cg.grid_2d(640, 500, n_steps=1)
+    paired = copy.deepcopy(base)
+    paired.line_id = (np.arange(base.n) // 2).astype(np.int32)
+    dt = float(base.dt_schedule[0])
+    out = []
+    for case in (paired, base):
+        g = lns.Model(case, lns.Options(mode=0, max_newton=1, krylov_rtol=1e-12, krylov_maxit=20000))
+        st = g.lns_timestep(dt, allow_noconv=True)
+        assert st["iterations"] == 1
+        out.append(g.lns_get_state()[0])
+        g.close()
+    du = np.abs(out[1] - base.p0).max()
+    assert du > 0
+    assert np.abs(out[0] - out[1]).max() <= 1e-6 * du
+
+
 def test_newton_iter_steps_through_algorithm1():
     case = cg.small_dfn(n_steps=2)
     ref = O.Sim(case, O.Options(mode=1, **TIGHT))
