@@ -60,8 +60,11 @@ def test_struct_layouts_match_c():
     src = "#include <stdio.h>\n#include <stddef.h>\n#include \"lns.h\"\nint main(void){\n"
     for s in structs:
         src += f'  printf("{s} %zu\\n", sizeof({s}));\n'
-    src += '  printf("off_fluid %zu\\n", offsetof(lns_model_desc, fluid));\n'
-    src += '  printf("off_profile %zu\\n", offsetof(lns_options, profile));\n  return 0;\n}\n'
+    # every field of every mirrored structure: same name, same offset in C and in ctypes
+    for s in structs:
+        for name, _ in getattr(lns, s)._fields_:
+            src += f'  printf("{s}.{name} %zu\\n", offsetof({s}, {name}));\n'
+    src += "  return 0;\n}\n"
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "t.c")
         exe = os.path.join(d, "t")
@@ -70,9 +73,10 @@ def test_struct_layouts_match_c():
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
     got = {ln.split()[0]: int(ln.split()[1]) for ln in out if ln.strip()}
     for s in structs:
-        assert got[s] == C.sizeof(getattr(lns, s)), s
-    assert got["off_fluid"] == lns.lns_model_desc.fluid.offset
-    assert got["off_profile"] == lns.lns_options.profile.offset
+        st = getattr(lns, s)
+        assert got[s] == C.sizeof(st), s
+        for name, _ in st._fields_:
+            assert got[f"{s}.{name}"] == getattr(st, name).offset, (s, name)
 
 
 @pytest.mark.parametrize("n", [0, 1, 31, 32, 33, 1000])
