@@ -74,32 +74,76 @@ class StepStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+def _configure(L):
+    vp = C.c_void_p
+    L.orc_assemble.argtypes = [C.POINTER(_Model), vp, vp, vp, vp, C.c_double, vp, vp, vp]
+    L.orc_cnv.argtypes = [C.POINTER(_Model), vp, vp, C.c_double, vp]
+    L.orc_lu_solve.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_int64)]
+    L.orc_lu_solve.restype = C.c_int
+    L.orc_dilate.argtypes = [C.POINTER(_Model), vp, C.c_int32, vp]
+    L.orc_boundary.argtypes = [C.POINTER(_Model), vp, vp]
+    L.orc_outer_halo.argtypes = [C.POINTER(_Model), vp, vp]
+    L.orc_active_set_update.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, vp, vp, C.c_int32,
+                                        vp, C.POINTER(C.c_int32)]
+    L.orc_dd_expand.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, vp, vp, vp, vp, vp, vp,
+                                C.POINTER(C.c_int32)]
+    L.orc_local_solve.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, vp, vp, vp, C.c_double, vp,
+                                  vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.orc_local_solve.restype = C.c_int
+    L.orc_timestep.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, vp, vp, C.POINTER(C.c_int32),
+                               C.c_double, C.POINTER(StepStats), vp, C.c_int32, vp]
+    L.orc_timestep.restype = C.c_int
+    L.orc_initial_set.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, C.c_int32, vp]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            vp = C.c_void_p
-            L.orc_assemble.argtypes = [C.POINTER(_Model), vp, vp, vp, vp, C.c_double, vp, vp, vp]
-            L.orc_cnv.argtypes = [C.POINTER(_Model), vp, vp, C.c_double, vp]
-            L.orc_lu_solve.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_int64)]
-            L.orc_lu_solve.restype = C.c_int
-            L.orc_dilate.argtypes = [C.POINTER(_Model), vp, C.c_int32, vp]
-            L.orc_boundary.argtypes = [C.POINTER(_Model), vp, vp]
-            L.orc_outer_halo.argtypes = [C.POINTER(_Model), vp, vp]
-            L.orc_active_set_update.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, vp, vp, C.c_int32,
-                                                vp, C.POINTER(C.c_int32)]
-            L.orc_dd_expand.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, vp, vp, vp, vp, vp, vp,
-                                        C.POINTER(C.c_int32)]
-            L.orc_local_solve.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, vp, vp, vp, C.c_double, vp,
-                                          vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
-            L.orc_local_solve.restype = C.c_int
-            L.orc_timestep.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, vp, vp, C.POINTER(C.c_int32),
-                                       C.c_double, C.POINTER(StepStats), vp, C.c_int32, vp]
-            L.orc_timestep.restype = C.c_int
-            L.orc_initial_set.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), vp, C.c_int32, vp]
-            _lib = L
+            _lib = _configure(C.CDLL(build()))
     return _lib
+
+
+def build_variant(src_text: str, out_dir: str, name: str) -> str:
+    """Compile a modified copy of the oracle source (used by the tests that plant a mistake in
+    the oracle to show that a pin catches it); returns the library path."""
+    src = os.path.join(out_dir, name + ".c")
+    with open(src, "w") as fh:
+        fh.write(src_text)
+    import shutil
+    shutil.copy(_HDR, os.path.join(out_dir, "lns_oracle.h"))
+    so = os.path.join(out_dir, "lib" + name + ".so")
+    subprocess.run(["gcc", "-O1", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared",
+                    "-o", so, src, "-lm"], check=True)
+    return so
+
+
+class use_library:
+    """Context manager: route every oracle call through the library at `path` (a variant
+    built by build_variant), restoring the regular build afterwards."""
+
+    def __init__(self, path: str) -> None:
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        lib()
+        with _lock:
+            self._saved = _lib
+            _lib = _configure(C.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self._saved
+        return False
+
+
+def source_text() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
 
 
 @dataclasses.dataclass

@@ -29,6 +29,11 @@
  * Algorithms 1 and 2; for mode 3 (tests/test_oracle_residual_sets.py) the first set against
  * scipy graph distances from the unconverged cells, full inflation against standard Newton's
  * iterates, an equilibrium, and the converged fields against standard Newton.
+ * Two-phase terms (tests/test_oracle_two_phase_pins.py): face fluxes at interior saturations
+ * against Corey relative permeabilities written out as fractions (fractional-flow ratio,
+ * endpoints, saturation-independent total flux for linear Corey); the scaled residual (CNV) of
+ * a pure-accumulation cell equals its saturation change, plus a worked example.  Planted
+ * mistakes in those terms (tests/test_oracle_mutants.py) each fail one of these pins.
  */
 #ifndef LNS_ORACLE_H
 #define LNS_ORACLE_H
