@@ -241,6 +241,14 @@ lns_status lns_dd_expand(lns_model* model, const double* dp, const double* dsw, 
 lns_status lns_solve_local(lns_model* model, double dt, const uint32_t* va_bits, double* dp, double* dsw,
                            lns_iter_stats* out);
 
+/* Compaction of the active set (step a2 of an iteration; Section 4.3: R_A restricts to V_A, and
+ * F_A, J_A = R_A J R_A^T are built directly on the active rows): the ascending list of the cells
+ * of V_A = va_bits (host bitset), act [n_A] (host, capacity n_cells; may be NULL), and the inverse
+ * map inv [n_cells] (host; may be NULL): inv[act[k]] = k, -1 for cells outside V_A.  *n_active
+ * gets n_A.  The compacted system of lns_solve_local and every Newton iteration numbers its rows
+ * in this order.  Bit-exact: integer work only. */
+lns_status lns_compact(lns_model* model, const uint32_t* va_bits, int32_t* act, int32_t* inv, int32_t* n_active);
+
 /* The residual F_A and Jacobian blocks of the active rows at the current state
  * (Appendix A).  F: [2 n_cells] (oil, water), Jd: [4 n_cells] diagonal blocks,
  * Jo: [4 n_adj] off-diagonal blocks (row i, column nbr[e]); blocks row-major

@@ -1401,6 +1401,30 @@ lns_status lns_solve_local(lns_model* m, double dt, const uint32_t* va_bits, dou
   return krylov_outcome(m);
 }
 
+lns_status lns_compact(lns_model* m, const uint32_t* va_bits, int32_t* act, int32_t* inv, int32_t* n_active) {
+  TRY(check_model(m));
+  if (!va_bits || !n_active) return fail(LNS_EINVAL, "va_bits and n_active must not be NULL");
+  if (m->step_open) return fail(LNS_ESTATE, "a timestep is open");
+  Dev& d = m->d;
+  *n_active = 0;
+  if (d.n == 0) return LNS_OK;
+  TRY(bits_to_device(m, d.va, va_bits));
+  TRY(reset_iter(m));
+  CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, cfg(m)));
+  TRY(read_counters(m));
+  const int na = d.ctr_h->n_active;
+  *n_active = na;
+  if (act && na > 0) CK(cudaMemcpyAsync(act, d.act, sizeof(int32_t) * (size_t)na, cudaMemcpyDeviceToHost, m->stream));
+  if (inv) CK(cudaMemcpyAsync(inv, d.inv, sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, m->stream));
+  TRY(sync(m));
+  if (inv) {  // the device map is defined on V_A only; report -1 elsewhere
+    const std::vector<uint32_t>& w = m->stage;  // V_A as uploaded (bits past n cleared)
+    for (int i = 0; i < d.n; i++)
+      if (!((w[i >> 5] >> (i & 31)) & 1u)) inv[i] = -1;
+  }
+  return LNS_OK;
+}
+
 lns_status lns_assemble(lns_model* m, double dt, const uint32_t* va_bits, double* F, double* Jd, double* Jo) {
   TRY(check_model(m));
   if (!va_bits) return fail(LNS_EINVAL, "va_bits is NULL");

@@ -120,7 +120,7 @@ EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_
            "lns_launch_count", "lns_last_error", "lns_active_set_noalloc",
            "lns_server_create", "lns_server_destroy", "lns_server_add_model", "lns_server_submit",
            "lns_server_poll", "lns_server_drain", "lns_server_get_state", "lns_server_get_stats", "lns_server_now",
-           "lns_server_cancel", "lns_debug_fault", "lns_advance"]
+           "lns_server_cancel", "lns_debug_fault", "lns_advance", "lns_compact"]
 
 
 def library_path() -> str:
@@ -151,6 +151,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "lns_dd_expand": [vp, vp, vp, i32, vp, vp, vp, vp, vp, P(i32)],
         "lns_solve_local": [vp, f64, vp, vp, vp, P(lns_iter_stats)],
         "lns_assemble": [vp, f64, vp, vp, vp, vp],
+        "lns_compact": [vp, vp, vp, vp, P(i32)],
         "lns_get_state": [vp, vp, vp],
         "lns_set_state": [vp, vp, vp, vp, vp],
         "lns_get_state_device": [vp, vp, vp],
@@ -399,6 +400,16 @@ class Model:
         st = lns_iter_stats()
         _check(load().lns_solve_local(self.h, float(dt), _ptr(va), _ptr(dp), _ptr(dsw), C.byref(st)))
         return dp, dsw, _as_dict(st)
+
+    def lns_compact(self, va_mask) -> Tuple[np.ndarray, np.ndarray]:
+        """Compaction of V_A: (act, inv) -- the ascending active cells and the inverse map
+        (-1 outside V_A)."""
+        va = mask_to_bits(va_mask)
+        act = np.zeros(max(self.n, 1), np.int32)
+        inv = np.zeros(max(self.n, 1), np.int32)
+        na = C.c_int32(0)
+        _check(load().lns_compact(self.h, _ptr(va), _ptr(act), _ptr(inv), C.byref(na)))
+        return act[: na.value].copy(), inv[: self.n].copy()
 
     def lns_assemble(self, dt: float, va_mask):
         va = mask_to_bits(va_mask)
