@@ -122,6 +122,10 @@ typedef struct {
   int32_t fp64_fallback; /* with krylov_fp32: an FP32 solve that breaks down or stops above
                           * krylov_fail_rtol is redone in FP64 within the same Newton iteration
                           * (a failed solve changes neither the state nor V_A).  Default 1. */
+  int32_t krylov_cluster; /* local systems small enough for one thread-block cluster (up to 16 SMs,
+                           * vectors in distributed shared memory) are solved there, larger ones by
+                           * the grid solver over every SM: the largest cluster in CTAs (2, 4, 8 or
+                           * 16); 0: the grid solver only; < 0: the default (16).  Default -1. */
 } lns_options;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
@@ -143,6 +147,7 @@ typedef struct {
   int32_t fp64_retry;    /* 1: the FP32 solve failed and this iteration's solve was redone in FP64
                           * (krylov_iters counts both solves; status/relres are the FP64 solve's) */
   double max_dp, max_dsw, cnv, krylov_relres;
+  int32_t krylov_solver; /* solver of the (last) solve: 1 cluster, 2 grid (options.krylov_cluster) */
 } lns_iter_stats;
 
 typedef struct {

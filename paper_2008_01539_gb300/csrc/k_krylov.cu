@@ -619,7 +619,7 @@ __device__ __forceinline__ int line_lower_bound(const int* ls, int n, int k) {
 }
 
 template <typename T, bool LINES>
-__global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int maxit) {
+__global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int maxit, int cl_cap) {
   using V = typename V2<T>::t;
   using B = B4<T>;
   using Ref = RowRef;
@@ -636,6 +636,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   // line blocks by length class c: len <= 4 << c in segments (c < 4), longer ones one per warp (c = 4)
   __shared__ int s_ccount[5], s_coff[5], s_cfill[5], s_citem[6];
   const int nA = d.ctr->n_active;
+  if (nA <= cl_cap && *d.fault != 1) return;  // the cluster solver takes this system (uniform exit)
   const int nb = gridDim.x;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nlines = LINES ? d.ctr->n_lines : 0;
@@ -847,7 +848,14 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   block_store_f64(l_bb, sh, part, nb);
   grid_barrier(d.ctr, nb, ++bar_gen, fault == 1 && blockIdx.x == 0);
   const bool timed_out = *(volatile int*)&d.ctr->bar_timeout;
-  const double bb = grid_sum_f64(part, nb);
+  // ||b||^2 is summed by warp 0; every thread scales its dot products by the same power of two
+  __shared__ double s_bbv;
+  {
+    const double bb0 = grid_sum_f64(part, nb);
+    if (threadIdx.x == 0) s_bbv = bb0;
+  }
+  __syncthreads();
+  const double bb = s_bbv;
   // Dots are scaled by an exact power of two near 1/bb before they are carried in double-float,
   // so that the reductions and the scalar arithmetic stay far from the FP32 range limits (the
   // scalars are ratios of dots and do not depend on the scale).  2^(1023 - E) with E the unbiased
@@ -1051,8 +1059,561 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     d.ctr->krylov_iters = it - 1;
     d.ctr->krylov_status = status;
+    d.ctr->krylov_solver = 2;
     d.ctr->krylov_relres = bb > 0.0 ? sqrt(sc_double(rr_last) / (bb * dscale)) : 0.0;
   }
+}
+
+// =========================================================================================
+// Cluster BiCGStab for small local systems.
+//
+// The same recurrence as k_bicgstab, run by ONE thread-block cluster of C CTAs (C <= 16) instead
+// of a cooperative grid over every SM.  The local systems of the localized method are small
+// (thousands of rows), so an iteration of the grid solver is bound by latency: two ~1 us grid
+// barriers, L2 round trips for every neighbour gather and for the 152 block partials.  Here:
+//   - each CTA owns a contiguous chunk of rows (ends never split a fracture-line block, as in the
+//     grid solver); a row's own vectors (x, r, r^, v, s, t, z) stay in the owning thread's
+//     registers for the whole solve, the vectors its neighbours read (y, v~ of both parities, r~,
+//     t~, z^) sit in the CTA's shared memory, indexed by local row;
+//   - a neighbour in another CTA of the cluster is read through distributed shared memory
+//     (mapa + ld.shared::cluster), so no vector goes through L2 during the iterations;
+//   - a reduction is a block reduction into the CTA's shared memory, one barrier.cluster
+//     (arrive.release / wait.acquire), and a read of the C partials by DSMEM in a fixed order, so
+//     every CTA holds identical scalars; the cluster barrier is a hardware barrier of CTAs the
+//     launch guarantees co-scheduled (no spin-wait);
+//   - matrix rows (columns and blocks), row references and line factors are staged in shared
+//     memory once per solve (rows beyond the pool are read from L2).
+// The kernel and the grid solver are both launched for every solve; a size test on the device
+// (n_A <= cap, computed by the host from C and the chunk capacity) makes exactly one of them run
+// it, so the choice needs no host round trip and fits a captured CUDA graph.
+// =========================================================================================
+constexpr int kClThreads = 256;
+constexpr int kClWarps = kClThreads / 32;
+constexpr int kClMaxCtas = 16;
+template <typename T>
+struct ClShape {
+  static constexpr int kRpt = sizeof(T) == 4 ? 4 : 2;  // rows per thread (own vectors in registers)
+  static constexpr int kRows = kClThreads * kRpt;       // rows per CTA
+};
+constexpr int kClLineList = 1024;
+constexpr size_t kClSmem = 220 * 1024;
+
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// all threads of all CTAs of the cluster; shared-memory writes before it are visible to
+// ld.shared::cluster of any CTA after it
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cl_addr(const void* local, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float2 ld_cl(const float2* local, unsigned rank) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(cl_addr(local, rank)) : "memory");
+  return v;
+}
+__device__ __forceinline__ double2 ld_cl(const double2* local, unsigned rank) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(cl_addr(local, rank)) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_cl(const double* local, unsigned rank) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(cl_addr(local, rank)) : "memory");
+  return v;
+}
+
+// Sum of NV double-float values over the cluster: block reduction into this CTA's s_part, one
+// cluster barrier, then warp 0 reads the C partials (lane c from CTA c) and reduces them in a fixed
+// tree; thread 0 holds the result (identical in every CTA).
+template <int NV>
+__device__ __forceinline__ void cl_sum(const DF (&vals)[NV], bool busy, DF* sdf, float2* s_part, unsigned C,
+                                       DF (&out)[NV]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  DF a[NV];
+#pragma unroll
+  for (int q = 0; q < NV; q++) a[q] = busy ? vals[q] : DF{0.f, 0.f};
+  if (busy) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < NV; q++) a[q] = df_add(a[q], df_shfl_xor(a[q], o));
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; q++) sdf[q * kClWarps + w] = a[q];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; q++) a[q] = lane < kClWarps ? sdf[q * kClWarps + lane] : DF{0.f, 0.f};
+#pragma unroll
+    for (int o = kClWarps / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < NV; q++) a[q] = df_add(a[q], df_shfl_xor(a[q], o));
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NV; q++) s_part[q] = make_float2(a[q].hi, a[q].lo);
+  }
+  cl_sync();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      const float2 x = lane < (int)C ? ld_cl(&s_part[q], (unsigned)lane) : make_float2(0.f, 0.f);
+      a[q] = {x.x, x.y};
+    }
+#pragma unroll
+    for (int o = kClMaxCtas / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < NV; q++) a[q] = df_add(a[q], df_shfl_xor(a[q], o));
+  }
+#pragma unroll
+  for (int q = 0; q < NV; q++) out[q] = a[q];
+}
+
+template <typename T, bool LINES>
+__global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rtol, int maxit, int cap) {
+  using V = typename V2<T>::t;
+  using B = B4<T>;
+  using Ref = RowRef;
+  using Acc = typename DotAcc<T>::t;
+  constexpr bool kF64 = sizeof(T) == 8;
+  constexpr int RPT = ClShape<T>::kRpt;
+  constexpr int R = ClShape<T>::kRows;
+  const int nA = d.ctr->n_active;
+  if (nA > cap || *d.fault == 1) return;  // the grid solver takes this system (uniform exit)
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ double sh[kClWarps];
+  __shared__ double s_bb;
+  __shared__ DF s_df[4 * kClWarps];
+  __shared__ float2 s_part[2][4];  // this CTA's partial sums: [0] phase 1 / init, [1] phase 2
+  using S = std::conditional_t<kF64, double, DF>;
+  __shared__ S s_sc[4];
+  __shared__ int s_ctl, s_epool, s_nlb, s_l0;
+  __shared__ int s_cb[kClMaxCtas + 1];
+  __shared__ int s_ccount[5], s_coff[5], s_cfill[5], s_citem[6];
+  const unsigned C = cl_size(), me = cl_rank();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nlines = LINES ? d.ctr->n_lines : 0;
+  // shared-memory layout: neighbour-read vectors [7][R] (y0, y1, vt0, vt1, r~, t~, z^), line inputs
+  // [2][R], line factors [3][R], row references [R], line-block list, then the matrix pool
+  V* const s_vec = (V*)dsm;
+  V* const sy[2] = {s_vec, s_vec + R};
+  V* const svt[2] = {s_vec + 2 * R, s_vec + 3 * R};
+  V* const srt = s_vec + 4 * R;
+  V* const stt = s_vec + 5 * R;
+  V* const szf = s_vec + 6 * R;
+  float2* const lbuf = (float2*)(dsm + 7 * (size_t)R * sizeof(V));
+  float4* const s_fac = (float4*)((unsigned char*)lbuf + 2 * (size_t)R * sizeof(float2));
+  Ref* const s_ref = (Ref*)((unsigned char*)s_fac + 3 * (size_t)R * sizeof(float4));
+  int2* const s_lines = (int2*)((unsigned char*)s_ref + (size_t)R * sizeof(Ref));
+  unsigned char* const pool = (unsigned char*)s_lines + (size_t)kClLineList * sizeof(int2);
+  const size_t pool_bytes = kClSmem - (size_t)(pool - dsm);
+  const int ecap = (int)(pool_bytes / (sizeof(int) + sizeof(B)));
+  B* const s_blk = (B*)pool;
+  int* const s_col = (int*)(pool + (size_t)ecap * sizeof(B));
+  const T* blocks = (const T*)d.blocks;
+  const V* b = (const V*)d.rhs;
+
+  // ---- chunk boundaries of every CTA (identical in all CTAs) -----------------------------
+  {
+    const int R0 = (nA + (int)C - 1) / (int)C;
+    for (int w = wib; w < (int)C; w += kClWarps) {  // warp-uniform
+      if (w == 0) continue;
+      int e = min(nA, w * R0);
+      if (LINES) e = chunk_edge(d, e, nA);
+      if (lane == 0) s_cb[w] = e;
+    }
+    if (threadIdx.x == 0) {
+      s_cb[0] = 0;
+      s_cb[C] = nA;
+      s_epool = 0;
+      for (int c = 0; c < 5; c++) s_ccount[c] = 0;
+    }
+  }
+  __syncthreads();
+  const int c0 = s_cb[me], c1 = max(c0, s_cb[me + 1]);
+  const int nr = c1 - c0;
+  if (LINES && wib == 0) {
+    int l0 = 0, l1 = 0;
+    if (nlines > 0) {
+      l0 = line_lower_bound(d.line_start, nlines, c0);
+      l1 = line_lower_bound(d.line_start, nlines, c1);
+    }
+    if (lane == 0) {
+      s_l0 = l0;
+      s_nlb = max(0, l1 - l0);
+    }
+  }
+  // owner CTA of compact row j: the last c with s_cb[c] <= j
+  auto owner = [&](int j) -> unsigned {
+    unsigned o = 0;
+#pragma unroll
+    for (int c = 1; c < kClMaxCtas; c++) o += (c < (int)C && s_cb[c] <= j) ? 1u : 0u;
+    return o;
+  };
+  auto global_ref = [&](int k) -> Ref {
+    const int2 a = __ldg(&d.arow[k]);
+    return {-(a.x + 1), a.y & 0xffffff, LINES ? (a.y >> 24) : 0};
+  };
+  auto stage = [&](int k) -> Ref {
+    const Ref g = global_ref(k);
+    const int off = atomicAdd(&s_epool, g.deg);
+    if (off + g.deg > ecap) return g;
+    const int e0 = -(g.off + 1);
+    for (int j = 0; j < g.deg; j++) {
+      s_col[off + j] = __ldg(&d.colA[e0 + j]);
+      s_blk[off + j] = *(const B*)&blocks[4 * (size_t)(e0 + j)];
+    }
+    return {off, g.deg, g.line};
+  };
+  auto product = [&](const Ref& ref, const V& own, auto load, auto comb) -> V {
+    if (ref.off >= 0) return row_product<T>(s_col + ref.off, s_blk + ref.off, ref.deg, own, load, comb);
+    const size_t e0 = (size_t)(-(ref.off + 1));
+    return row_product<T>(d.colA + e0, (const B*)&blocks[4 * e0], ref.deg, own, load, comb);
+  };
+  __syncthreads();
+  const int nlb = LINES ? s_nlb : 0, l0 = LINES ? s_l0 : 0;
+  for (int i = threadIdx.x; i < nr; i += kClThreads) {
+    s_ref[i] = stage(c0 + i);
+    if (LINES && __ldg(&d.line_row_flag[c0 + i])) {
+      s_fac[3 * (size_t)i + 0] = __ldg((const float4*)d.line_dinv + c0 + i);
+      s_fac[3 * (size_t)i + 1] = __ldg((const float4*)d.line_a + c0 + i);
+      s_fac[3 * (size_t)i + 2] = __ldg((const float4*)d.line_g + c0 + i);
+    }
+  }
+  if (LINES && nlb <= kClLineList) {
+    for (int j = threadIdx.x; j < nlb; j += kClThreads)
+      atomicAdd(&s_ccount[line_class(__ldg(&d.line_len[__ldg(&d.line_start[l0 + j])]))], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int off = 0;
+      s_citem[0] = 0;
+      for (int c = 0; c < 5; c++) {
+        s_coff[c] = off;
+        s_cfill[c] = off;
+        off += s_ccount[c];
+        const int per = c < 4 ? 8 >> c : 1;
+        s_citem[c + 1] = s_citem[c] + (s_ccount[c] + per - 1) / per;
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nlb; j += kClThreads) {
+      const int k0 = __ldg(&d.line_start[l0 + j]);
+      const int len = __ldg(&d.line_len[k0]);
+      s_lines[atomicAdd(&s_cfill[line_class(len)], 1)] = make_int2(k0 - c0, len);  // local start
+    }
+  }
+  __syncthreads();
+
+  // after a block barrier: M^{-1} on this CTA's line blocks (inputs lbuf by local row, outputs by
+  // local row); solvefn(k0 local, len, factors, inputs, seg)
+  auto lines = [&](auto solvefn) {
+    if constexpr (LINES) {
+      __syncthreads();
+      auto fac = [&](int k0) -> LineFac {
+        const float4* fb = &s_fac[3 * (size_t)k0];
+        return LineFac{fb, fb + 1, fb + 2, 3};
+      };
+      if (nlb <= kClLineList) {
+        const int nit = s_citem[5];
+#pragma unroll 1
+        for (int it = wib; it < nit; it += kClWarps) {
+          int c = 0;
+          while (c < 4 && it >= s_citem[c + 1]) c++;
+          const int idx = it - s_citem[c];
+          if (c < 4) {
+            const int seg = 4 << c, li = idx * (8 >> c) + (lane >> (c + 2));
+            const int2 kl = li < s_ccount[c] ? s_lines[s_coff[c] + li] : make_int2(0, 0);
+            solvefn(kl.x, kl.y, fac(kl.x), lbuf + kl.x, seg);
+          } else {
+            const int2 kl = s_lines[s_coff[4] + idx];
+            solvefn(kl.x, kl.y, fac(kl.x), lbuf + kl.x, 0);
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int j = wib; j < nlb; j += kClWarps) {
+          const int k0 = __ldg(&d.line_start[l0 + j]);
+          const int2 kl = make_int2(k0 - c0, __ldg(&d.line_len[k0]));
+          solvefn(kl.x, kl.y, fac(kl.x), lbuf + kl.x, 0);
+        }
+      }
+    }
+  };
+
+  // ---- own rows: registers --------------------------------------------------------------
+  V ox[RPT], o_r[RPT], orh[RPT], ov[RPT], os[RPT], ot[RPT], oz[RPT];
+  Ref oref[RPT];
+  const V zero = mk<T>(0, 0);
+  double l_bb = 0.0;
+#pragma unroll
+  for (int q = 0; q < RPT; q++) {
+    const int i = threadIdx.x + q * kClThreads;
+    ox[q] = zero;
+    oz[q] = zero;
+    ot[q] = zero;
+    ov[q] = zero;
+    o_r[q] = zero;
+    os[q] = zero;
+    orh[q] = zero;
+    oref[q] = Ref{0, 0, 0};
+    if (i < nr) {
+      const V bk = b[c0 + i];
+      oref[q] = s_ref[i];
+      os[q] = bk;
+      orh[q] = bk;
+      l_bb += (double)bk.x * bk.x + (double)bk.y * bk.y;
+      stt[i] = zero;
+      sy[0][i] = zero;
+      svt[0][i] = zero;
+      if (LINES && oref[q].line)
+        lbuf[i] = make_float2((float)bk.x, (float)bk.y);
+      else
+        szf[i] = bk;
+    }
+  }
+  lines([&](int k0, int len, const LineFac& f, const float2* buf, int seg) {
+    V* const dst[1] = {szf};
+    if (seg)
+      line_solve_seg<T, 1>(seg, k0, len, f, buf, R, dst);
+    else
+      line_solve<T, 1>(k0, len, f, buf, R, dst);
+  });
+  // ||b||^2 over the cluster in FP64
+  {
+    double a = l_bb;
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[wib] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < kClWarps; k++) t += sh[k];
+      s_bb = t;
+    }
+  }
+  cl_sync();
+  __shared__ double s_bbv;  // the cluster sum, read by every thread (all scale their dots alike)
+  if (threadIdx.x < 32) {
+    double a = threadIdx.x < C ? ld_cl(&s_bb, threadIdx.x) : 0.0;
+    for (int o = kClMaxCtas / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (threadIdx.x == 0) s_bbv = a;
+  }
+  __syncthreads();
+  const double bb = s_bbv;
+  long long eb = bb > 0.0 ? ((__double_as_longlong(bb) >> 52) & 0x7ff) - 1023 : 0;
+  eb = eb < -126 ? -126 : (eb > 126 ? 126 : eb);
+  const double dscale = __longlong_as_double((1023 - eb) << 52);
+  const float fscale = (float)dscale;
+  auto to_df = [&](const Acc& a) -> DF {
+    if constexpr (kF64)
+      return dot_df(a, dscale);
+    else
+      return dot_df(a, fscale);
+  };
+  const int fault = *d.fault;
+  S rho, alpha, stop2, rr_last, rr_ref;
+  sc_zero(rho);
+  sc_zero(alpha);
+  sc_zero(stop2);
+  sc_zero(rr_last);
+  sc_zero(rr_ref);
+  int it_ref = 0;
+  if (threadIdx.x == 0) {
+    rho = sc_from(df_from(fault == 2 || (fault == 3 && sizeof(T) == 4) ? 0.0 : bb * dscale), S{});
+    stop2 = sc_from(df_from(rtol * rtol * bb * dscale), S{});
+    rr_ref = sc_from(df_from(bb * dscale), S{});
+    sc_zero(s_sc[0]);
+    sc_zero(s_sc[1]);
+    sc_zero(s_sc[2]);
+    s_ctl = 0;
+  }
+  __syncthreads();
+  const bool busy = __any_sync(0xffffffffu, (int)threadIdx.x < nr) || (LINES && wib < nlb);
+  int status = 1, it = 1;
+  for (it = 1; !s_ctl; it++) {
+    // ---- phase 1 ---------------------------------------------------------------------------
+    const T beta = sc_t<T>(s_sc[0]), alp = sc_t<T>(s_sc[1]), omp = sc_t<T>(s_sc[2]);
+    const T nom = -omp;
+    const int po = (it & 1) ? 0 : 1, pn = 1 - po;
+    const V* const yo = sy[po];
+    V* const yn = sy[pn];
+    const V* const vto = svt[po];
+    V* const vtn = svt[pn];
+    struct Raw1 {
+      V tt, zf, vt, y;
+    };
+    auto ld1 = [&](int j) {
+      const unsigned o = owner(j);
+      const int i = j - s_cb[o];
+      return Raw1{ld_cl(&stt[i], o), ld_cl(&szf[i], o), ld_cl(&vto[i], o), ld_cl(&yo[i], o)};
+    };
+    auto rt_of = [&](const Raw1& a) { return axpy(nom, a.tt, a.zf); };
+    auto y_of = [&](const Raw1& a, const V& rtc) { return axpy(beta, axpy(nom, a.vt, a.y), rtc); };
+    auto cb1 = [&](const Raw1& a) { return y_of(a, rt_of(a)); };
+    Acc l_rv, l_rr;
+    dot_zero(l_rv);
+    dot_zero(l_rr);
+#pragma unroll
+    for (int q = 0; q < RPT; q++) {
+      const int i = threadIdx.x + q * kClThreads;
+      if (i < nr) {
+        const Raw1 own{stt[i], szf[i], vto[i], yo[i]};
+        const V rtk = rt_of(own);
+        const V ynk = y_of(own, rtk);
+        const V vv = product(oref[q], ynk, ld1, cb1);
+        const V rk = axpy(nom, ot[q], os[q]);
+        ox[q] = mk<T>(ox[q].x + alp * own.y.x + omp * oz[q].x, ox[q].y + alp * own.y.y + omp * oz[q].y);
+        o_r[q] = rk;
+        srt[i] = rtk;
+        yn[i] = ynk;
+        ov[q] = vv;
+        if (LINES && oref[q].line)
+          lbuf[i] = make_float2((float)vv.x, (float)vv.y);
+        else
+          vtn[i] = vv;
+        dot_acc(l_rr, rk.x, rk.x);
+        dot_acc(l_rr, rk.y, rk.y);
+        dot_acc(l_rv, orh[q].x, vv.x);
+        dot_acc(l_rv, orh[q].y, vv.y);
+      }
+    }
+    lines([&](int k0, int len, const LineFac& f, const float2* buf, int seg) {
+      V* const dst[1] = {vtn};
+      if (seg)
+        line_solve_seg<T, 1>(seg, k0, len, f, buf, R, dst);
+      else
+        line_solve<T, 1>(k0, len, f, buf, R, dst);
+    });
+    {
+      const DF vals[2] = {to_df(l_rv), to_df(l_rr)};
+      DF o[2];
+      cl_sum<2>(vals, busy, s_df, s_part[0], C, o);
+      if (threadIdx.x == 0) {
+        const S rv = sc_from(o[0], S{});
+        rr_last = sc_from(o[1], S{});
+        if (sc_le(sc_mul(rr_last, sc_from(df_from(4.0), S{})), rr_ref)) {
+          rr_ref = rr_last;
+          it_ref = it;
+        }
+        if (sc_le(rr_last, stop2)) {
+          s_ctl = 1;
+          status = 0;
+        } else if (it > maxit) {
+          s_ctl = 1;
+          status = 1;
+        } else if (!kF64 && it - it_ref > kStagIters) {
+          s_ctl = 1;
+          status = 1;
+        } else if (!sc_ok(rv) || !sc_ok(rho)) {
+          s_ctl = 1;
+          status = 2;
+        } else {
+          alpha = sc_div(rho, rv);
+          s_sc[3] = alpha;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_ctl) break;
+    // ---- phase 2 ---------------------------------------------------------------------------
+    const T nal = -sc_t<T>(s_sc[3]);
+    auto ld2 = [&](int j) {
+      const unsigned o = owner(j);
+      const int i = j - s_cb[o];
+      return V2pair<V>{ld_cl(&vtn[i], o), ld_cl(&srt[i], o)};
+    };
+    auto cb2 = [&](const V2pair<V>& a) { return axpy(nal, a.a, a.b); };
+    Acc l_ts, l_tt, l_rs, l_rt;
+    dot_zero(l_ts);
+    dot_zero(l_tt);
+    dot_zero(l_rs);
+    dot_zero(l_rt);
+#pragma unroll
+    for (int q = 0; q < RPT; q++) {
+      const int i = threadIdx.x + q * kClThreads;
+      if (i < nr) {
+        const V zk = cb2(V2pair<V>{vtn[i], srt[i]});
+        const V tk = product(oref[q], zk, ld2, cb2);
+        const V sk = axpy(nal, ov[q], o_r[q]);
+        os[q] = sk;
+        oz[q] = zk;
+        ot[q] = tk;
+        if (LINES && oref[q].line) {
+          lbuf[i] = make_float2((float)sk.x, (float)sk.y);
+          lbuf[R + i] = make_float2((float)tk.x, (float)tk.y);
+        } else {
+          szf[i] = sk;
+          stt[i] = tk;
+        }
+        dot_acc(l_ts, tk.x, sk.x);
+        dot_acc(l_ts, tk.y, sk.y);
+        dot_acc(l_tt, tk.x, tk.x);
+        dot_acc(l_tt, tk.y, tk.y);
+        dot_acc(l_rs, orh[q].x, sk.x);
+        dot_acc(l_rs, orh[q].y, sk.y);
+        dot_acc(l_rt, orh[q].x, tk.x);
+        dot_acc(l_rt, orh[q].y, tk.y);
+      }
+    }
+    lines([&](int k0, int len, const LineFac& f, const float2* buf, int seg) {
+      V* const dst[2] = {szf, stt};
+      if (seg)
+        line_solve_seg<T, 2>(seg, k0, len, f, buf, R, dst);
+      else
+        line_solve<T, 2>(k0, len, f, buf, R, dst);
+    });
+    {
+      const DF vals[4] = {to_df(l_ts), to_df(l_tt), to_df(l_rs), to_df(l_rt)};
+      DF o[4];
+      cl_sum<4>(vals, busy, s_df, s_part[1], C, o);
+      if (threadIdx.x == 0) {
+        const S ts = sc_from(o[0], S{}), t2 = sc_from(o[1], S{}), rs = sc_from(o[2], S{}), rtv = sc_from(o[3], S{});
+        if (!sc_finite(ts) || !sc_finite(t2) || !sc_finite(rs) || !sc_finite(rtv)) {
+          s_ctl = 1;
+          status = 2;
+        } else {
+          S omega, beta;
+          sc_zero(omega);
+          sc_zero(beta);
+          if (sc_pos(t2)) omega = sc_div(ts, t2);
+          const S rho_new = sc_fnma(omega, rtv, rs);
+          if (sc_nonzero(omega)) beta = sc_mul(sc_div(rho_new, rho), sc_div(alpha, omega));
+          s_sc[0] = beta;
+          s_sc[1] = alpha;
+          s_sc[2] = omega;
+          rho = rho_new;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_ctl) break;
+  }
+  // x_{it-1} to the solution vector; every CTA waits until no CTA reads its shared memory
+  V* const xg = (V*)d.kx;
+#pragma unroll
+  for (int q = 0; q < RPT; q++) {
+    const int i = threadIdx.x + q * kClThreads;
+    if (i < nr) xg[c0 + i] = ox[q];
+  }
+  if (me == 0 && threadIdx.x == 0) {
+    d.ctr->krylov_iters = it - 1;
+    d.ctr->krylov_status = status;
+    d.ctr->krylov_solver = 1;
+    d.ctr->krylov_relres = bb > 0.0 ? sqrt(sc_double(rr_last) / (bb * dscale)) : 0.0;
+  }
+  cl_sync();
 }
 
 template <typename T, bool L>
@@ -1073,16 +1634,63 @@ int krylov_grid(int fp32, int sms) {
   return a < b ? a : b;
 }
 
-// The solver's blocks fill every SM, so two solves must never be resident at once: launches
-// from different streams (models served concurrently) are chained through one event per device,
-// each waiting for the previous one to finish.
+namespace {
+template <typename T, bool L>
+int cluster_fits(int ctas) {
+  auto fn = k_bicgstab_cl<T, L>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem) != cudaSuccess) return 0;
+  if (ctas > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = ctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kClThreads);
+  cfg.dynamicSmemBytes = kClSmem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <typename T, bool L>
+ClusterShape cluster_shape_t(int max_ctas) {
+  for (int c = kClMaxCtas; c >= 2; c >>= 1) {
+    if (c > max_ctas) continue;
+    if (cluster_fits<T, L>(c) >= 1) {
+      const int per = ClShape<T>::kRows - (L ? kLineBlockRows : 0);
+      return ClusterShape{c, c * per};
+    }
+  }
+  cudaGetLastError();
+  return ClusterShape{0, -1};
+}
+}  // namespace
+
+ClusterShape krylov_cluster_shape(int fp32, int lines, int max_ctas) {
+  if (max_ctas <= 0) return ClusterShape{0, -1};
+  if (fp32) return lines ? cluster_shape_t<float, true>(max_ctas) : cluster_shape_t<float, false>(max_ctas);
+  return lines ? cluster_shape_t<double, true>(max_ctas) : cluster_shape_t<double, false>(max_ctas);
+}
+
+// The grid solver's blocks fill every SM, so two of its solves must never be resident at once:
+// launches from different streams (models served concurrently) are chained through one event per
+// device, each waiting for the previous one to finish.  Cluster solves occupy C SMs and run
+// concurrently with anything.
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_coop_mu;
 cudaEvent_t g_coop_ev[kMaxDevices] = {};
 }  // namespace
 
-cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, LaunchCfg c) {
+cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, ClusterShape cl,
+                            LaunchCfg c) {
   // barrier counter and timeout flag start from zero in every launch
   cudaError_t e = cudaMemsetAsync(&d.ctr->bar_count, 0, 3 * sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
@@ -1091,14 +1699,35 @@ cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int 
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   Dev dd = d;
-  void* args[] = {&dd, &rtol, &maxit};
+  int cap = cl.ctas > 0 ? cl.cap : -1;
+  if (cl.ctas > 0) {
+    void* cfn = fp32 ? (lines ? (void*)k_bicgstab_cl<float, true> : (void*)k_bicgstab_cl<float, false>)
+                     : (lines ? (void*)k_bicgstab_cl<double, true> : (void*)k_bicgstab_cl<double, false>);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl.ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cl.ctas);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = kClSmem;
+    cfg.stream = c.stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void* cargs[] = {&dd, &rtol, &maxit, &cap};
+    count_launches(1);
+    e = cudaLaunchKernelExC(&cfg, cfn, cargs);
+    if (e != cudaSuccess) return e;
+  }
+  void* args[] = {&dd, &rtol, &maxit, &cap};
   count_launches(1);
   void* fn = fp32 ? (lines ? (void*)k_bicgstab<float, true> : (void*)k_bicgstab<float, false>)
                   : (lines ? (void*)k_bicgstab<double, true> : (void*)k_bicgstab<double, false>);
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  e = cudaStreamIsCapturing(c.stream, &cap);
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(c.stream, &cap_st);
   if (e != cudaSuccess) return e;
-  if (cap != cudaStreamCaptureStatusNone)  // captured into a model's graph: ordered by its own stream
+  if (cap_st != cudaStreamCaptureStatusNone)  // captured into a model's graph: ordered by its own stream
     return cudaLaunchCooperativeKernel(fn, grid, kKryBlk, args, kKrySmem, c.stream);
   std::lock_guard<std::mutex> lk(g_coop_mu);
   if (!g_coop_ev[dev]) {

@@ -76,6 +76,8 @@ struct lns_model {
   std::vector<void*> owned;
   double avg_degree = 0.0;
   int kgrid[2] = {0, 0};  // cooperative BiCGStab grid (FP64, FP32)
+  lns::ClusterShape kcl[2][2] = {};  // cluster BiCGStab [fp32][lines] for the current krylov_cluster
+  int kcl_max = -2;                  // krylov_cluster the shapes were computed for
   // timestep state
   bool step_open = false;
   double dt = 0.0;
@@ -272,6 +274,17 @@ lns_status bits_to_host(lns_model* m, uint32_t* host, const uint32_t* src) {
   return LNS_OK;
 }
 
+// Shape of the cluster solver for the model's krylov_cluster option (queried once per value).
+lns::ClusterShape cluster_shape(lns_model* m, int fp32, int lines) {
+  const int want = m->o.krylov_cluster < 0 ? 16 : m->o.krylov_cluster;
+  if (want != m->kcl_max) {
+    for (int f = 0; f < 2; f++)
+      for (int l = 0; l < 2; l++) m->kcl[f][l] = lns::krylov_cluster_shape(f, l, want);
+    m->kcl_max = want;
+  }
+  return m->kcl[fp32 ? 1 : 0][lines ? 1 : 0];
+}
+
 // Solve the local system on the set currently in d.va at the current state: compaction,
 // assembly, line factors, BiCGStab.  Leaves the Krylov solution in d.kx.
 lns_status local_solve(lns_model* m, int debug) {
@@ -293,7 +306,8 @@ lns_status local_solve(lns_model* m, int debug) {
     TRY(ev_end(m, &pe, 0.0, 0.0));
   }
   TRY(ev_begin(m, KC_KRYLOV, &pe));
-  CK(lns::launch_bicgstab(d, fp32, lines, m->o.krylov_rtol, m->o.krylov_maxit, m->kgrid[fp32 ? 1 : 0], c));
+  CK(lns::launch_bicgstab(d, fp32, lines, m->o.krylov_rtol, m->o.krylov_maxit, m->kgrid[fp32 ? 1 : 0],
+                          cluster_shape(m, fp32, lines), c));
   TRY(ev_end(m, &pe, 0.0, 0.0));
   return LNS_OK;
 }
@@ -530,6 +544,7 @@ lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
     st->max_dp = maxdp;
     st->max_dsw = bits2d(h.max_dsw_bits);
     st->cnv = cnv;
+    st->krylov_solver = h.krylov_solver;
     st->step_done = 0;
   }
   return krylov_outcome(m);
@@ -766,6 +781,8 @@ lns_status validate_options(const lns_options* o) {
   if (!(o->krylov_rtol > 0.0) || !(o->eps_p >= 0.0)) return fail(LNS_EINVAL, "krylov_rtol > 0 and eps_p >= 0 required");
   if (o->precond != LNS_PRECOND_BJAC && o->precond != LNS_PRECOND_BJAC_CELL)
     return fail(LNS_EINVAL, "unknown preconditioner");
+  if (o->krylov_cluster > 16 || (o->krylov_cluster > 0 && (o->krylov_cluster & (o->krylov_cluster - 1))))
+    return fail(LNS_EINVAL, "krylov_cluster must be < 0, 0, or a power of two <= 16");
   return LNS_OK;
 }
 
@@ -853,6 +870,7 @@ lns_status lns_options_default(lns_options* o) {
   o->p_scale = 0.0;
   o->profile = 0;
   o->fp64_fallback = 1;
+  o->krylov_cluster = -1;
   return LNS_OK;
 }
 
@@ -880,6 +898,7 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
     return cleanup_fail(fail(LNS_ECUDA, "cannot query SM count"));
   m->kgrid[0] = lns::krylov_grid(0, m->sms);
   m->kgrid[1] = lns::krylov_grid(1, m->sms);
+  cluster_shape(m, 0, 0);  // function attributes and occupancy queries stay outside stream capture
   Dev& d = m->d;
   d.n = n;
   d.n_adj = na;
@@ -1048,6 +1067,7 @@ lns_status lns_set_options(lns_model* m, const lns_options* o) {
   if (m->step_open && o->mode != m->o.mode) return fail(LNS_ESTATE, "cannot change mode inside an open timestep");
   m->o = *o;
   drop_graph(m);  // captured with the old options
+  cluster_shape(m, 0, 0);
   return LNS_OK;
 }
 
@@ -1397,6 +1417,7 @@ lns_status lns_solve_local(lns_model* m, double dt, const uint32_t* va_bits, dou
     out->max_dp = bits2d(h.max_dp_bits);
     out->max_dsw = bits2d(h.max_dsw_bits);
     out->cnv = bits2d(h.cnv_bits);
+    out->krylov_solver = h.krylov_solver;
   }
   return krylov_outcome(m);
 }

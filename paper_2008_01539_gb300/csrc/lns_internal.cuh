@@ -56,6 +56,8 @@ struct IterCounters {
   unsigned bar_pad;
   int bar_timeout;     // set when a barrier wait gave up (the kernel then stops)
   int solve_failed;    // the update kernel found the Krylov solve failed and applied nothing
+  int krylov_solver;   // which solver ran the last solve: 1 cluster, 2 grid
+  int pad_i;
   double pad[1];
 };
 
@@ -144,7 +146,14 @@ cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c);
 
 // k_krylov.cu
 cudaError_t launch_residual_flags(const Dev& d, double tol_cnv, LaunchCfg c);
-cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, LaunchCfg c);
+// Cluster solver shape: ctas per cluster (0: none) and the largest n_A it takes (-1: none).
+struct ClusterShape {
+  int ctas, cap;
+};
+cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, ClusterShape cl,
+                            LaunchCfg c);
 int krylov_grid(int fp32, int sms);
+// The largest cluster (<= max_ctas, a power of two) the device co-schedules for the cluster solver.
+ClusterShape krylov_cluster_shape(int fp32, int lines, int max_ctas);
 
 }  // namespace lns

@@ -51,7 +51,7 @@ class lns_options(C.Structure):
                 ("max_dd_outer", C.c_int32), ("sat_chop", C.c_double), ("krylov_fp32", C.c_int32),
                 ("precond", C.c_int32), ("krylov_rtol", C.c_double), ("krylov_maxit", C.c_int32),
                 ("krylov_fail_rtol", C.c_double), ("p_scale", C.c_double), ("profile", C.c_int32),
-                ("fp64_fallback", C.c_int32)]
+                ("fp64_fallback", C.c_int32), ("krylov_cluster", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -65,7 +65,8 @@ class lns_allocator(C.Structure):
 class lns_iter_stats(C.Structure):
     _fields_ = [("n_active", C.c_int32), ("is_expand", C.c_int32), ("converged", C.c_int32),
                 ("step_done", C.c_int32), ("krylov_iters", C.c_int32), ("krylov_status", C.c_int32),
-                ("fp64_retry", C.c_int32), ("max_dp", C.c_double), ("max_dsw", C.c_double), ("cnv", C.c_double), ("krylov_relres", C.c_double)]
+                ("fp64_retry", C.c_int32), ("max_dp", C.c_double), ("max_dsw", C.c_double), ("cnv", C.c_double),
+                ("krylov_relres", C.c_double), ("krylov_solver", C.c_int32)]
 
 
 class lns_step_stats(C.Structure):
@@ -235,6 +236,7 @@ class Options:
     p_scale: float = 0.0
     profile: int = 0
     fp64_fallback: int = 1
+    krylov_cluster: int = -1
 
     def c(self) -> lns_options:
         return lns_options(*[getattr(self, f.name) for f in dataclasses.fields(self)])
