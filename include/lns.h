@@ -216,6 +216,27 @@ typedef struct {
  * t_span, dt_min = t_span / 1024, dt_max = t_span, grow 2, cut 0.5, easy_iters 4. */
 lns_status lns_advance(lns_model* model, double t_span, const lns_dt_control* ctl, lns_advance_stats* out);
 
+/* Batched ensembles: many independent models (e.g. DFN realizations of uneven size) advanced
+ * together.  The paper advances one model (Section 4.3); this runs its method on every member at
+ * once.  Each member keeps its own state, active sets, convergence test and time-step controller
+ * (lns_advance's rule with ctl, applied per member: a member whose step fails is cut and retried
+ * while the others go on), so every member ends exactly as lns_advance(member, t_span, ctl) alone
+ * would leave it, bit for bit.  A round advances every live member by one Newton iteration: the
+ * work before the solve (compaction, assembly, line factors) of all members, then each member's
+ * solve and update; the members' work runs on their own streams and overlaps on the device (a
+ * system small enough for the cluster solver occupies up to 16 SMs; larger ones take the grid
+ * solver, one at a time).  Give every member a stream of its own (lns_set_stream) for overlap.
+ * Members: standard Newton or Algorithm 1, no timestep open, each model at most once.  out
+ * [n_members] gets each member's statistics (status per member); the call returns the first
+ * member's failure status, if any, after all members are done. */
+typedef struct {
+  int32_t rounds;         /* batch Newton rounds */
+  int64_t cluster_solves; /* solves run by the cluster solver */
+  int64_t grid_solves;    /* solves run by the grid solver */
+} lns_batch_stats;
+lns_status lns_batch_advance(lns_model* const* members, int32_t n_members, double t_span, const lns_dt_control* ctl,
+                             lns_advance_stats* out, lns_batch_stats* stats);
+
 /* One Newton iteration of Algorithm 1 (or standard Newton): opens a timestep of size dt
  * if none is open, runs lines 4-21 once, and closes the timestep once the loop condition
  * (is_expand or not converged) is false.  Not available in LNS_MODE_DD or LNS_MODE_RESIDUAL. */

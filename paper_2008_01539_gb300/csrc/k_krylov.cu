@@ -1689,6 +1689,37 @@ std::mutex g_coop_mu;
 cudaEvent_t g_coop_ev[kMaxDevices] = {};
 }  // namespace
 
+// One solver only (the host has read n_A): which = 1 the cluster solver (n_A <= cl.cap), 2 the grid
+// solver.  Same kernels and arguments as launch_bicgstab's, so the results are the same bits.
+cudaError_t launch_bicgstab_which(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, ClusterShape cl,
+                                  int which, LaunchCfg c) {
+  if (which == 1 && cl.ctas > 0) {
+    ClusterShape only = cl;
+    cudaError_t e = cudaMemsetAsync(&d.ctr->bar_count, 0, 3 * sizeof(unsigned), c.stream);
+    if (e != cudaSuccess) return e;
+    Dev dd = d;
+    int cap = cl.cap;
+    void* cfn = fp32 ? (lines ? (void*)k_bicgstab_cl<float, true> : (void*)k_bicgstab_cl<float, false>)
+                     : (lines ? (void*)k_bicgstab_cl<double, true> : (void*)k_bicgstab_cl<double, false>);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = only.ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(only.ctas);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = kClSmem;
+    cfg.stream = c.stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void* cargs[] = {&dd, &rtol, &maxit, &cap};
+    count_launches(1);
+    return cudaLaunchKernelExC(&cfg, cfn, cargs);
+  }
+  return launch_bicgstab(d, fp32, lines, rtol, maxit, grid, ClusterShape{0, -1}, c);
+}
+
 cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, ClusterShape cl,
                             LaunchCfg c) {
   // barrier counter and timeout flag start from zero in every launch

@@ -78,6 +78,12 @@ struct lns_model {
   int kgrid[2] = {0, 0};  // cooperative BiCGStab grid (FP64, FP32)
   lns::ClusterShape kcl[2][2] = {};  // cluster BiCGStab [fp32][lines] for the current krylov_cluster
   int kcl_max = -2;                  // krylov_cluster the shapes were computed for
+  int fault_h = 0;                   // host copy of the injected solver fault (lns_debug_fault)
+  // batched advance (lns_batch_advance): the iteration split around the solve, each half captured
+  cudaGraph_t bg[2] = {nullptr, nullptr};
+  cudaGraphExec_t bx[2] = {nullptr, nullptr};
+  int64_t bx_kernels[2] = {0, 0};
+  bool bgraph_ok = true;
   // timestep state
   bool step_open = false;
   double dt = 0.0;
@@ -128,6 +134,12 @@ void drop_graph(lns_model* m) {
   if (m->graph) cudaGraphDestroy(m->graph);
   m->gexec = nullptr;
   m->graph = nullptr;
+  for (int k = 0; k < 2; k++) {
+    if (m->bx[k]) cudaGraphExecDestroy(m->bx[k]);
+    if (m->bg[k]) cudaGraphDestroy(m->bg[k]);
+    m->bx[k] = nullptr;
+    m->bg[k] = nullptr;
+  }
   for (auto& pe : m->graph_pending) {
     m->ev_pool.push_back(pe.a);
     m->ev_pool.push_back(pe.b);
@@ -495,21 +507,12 @@ lns_status with_fp64_krylov(lns_model* m, F body) {
   return r;
 }
 
-// One pass of Algorithm 1 lines 4-21 (or of standard Newton).
-lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
+// Host side of one pass of Algorithm 1 lines 4-21 (or of standard Newton), after its device work
+// has completed and the counter block is on the host: an FP32 solve that failed is redone in FP64,
+// then the model's iteration state and the caller's statistics are updated.
+lns_status finish_iteration(lns_model* m, lns_iter_stats* st) {
   Dev& d = m->d;
   const bool local = m->o.mode == LNS_MODE_LOCAL;
-  if (m->o.krylov_fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
-  const bool graph = m->graph_ok && m->o.profile != 1 && m->o.m_layers <= 8;
-  if (graph) TRY(ensure_graph(m));
-  if (graph && m->gexec) {
-    CK(cudaGraphLaunch(m->gexec, m->stream));
-    lns::count_launches((int)m->graph_kernels);
-    m->pending = m->graph_pending;
-  } else {
-    TRY(enqueue_iteration(m));
-  }
-  CK(cudaStreamSynchronize(m->stream));
   annotate_pending(m);
   TRY(ev_flush(m));
   const IterCounters& h = *d.ctr_h;
@@ -548,6 +551,40 @@ lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
     st->step_done = 0;
   }
   return krylov_outcome(m);
+}
+
+// One pass of Algorithm 1 lines 4-21 (or of standard Newton).
+lns_status alg1_iteration(lns_model* m, lns_iter_stats* st) {
+  Dev& d = m->d;
+  if (m->o.krylov_fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
+  const bool graph = m->graph_ok && m->o.profile != 1 && m->o.m_layers <= 8;
+  if (graph) TRY(ensure_graph(m));
+  if (graph && m->gexec) {
+    CK(cudaGraphLaunch(m->gexec, m->stream));
+    lns::count_launches((int)m->graph_kernels);
+    m->pending = m->graph_pending;
+  } else {
+    TRY(enqueue_iteration(m));
+  }
+  CK(cudaStreamSynchronize(m->stream));
+  return finish_iteration(m, st);
+}
+
+// After an iteration: close the timestep when the loop condition of Algorithm 1 (or standard
+// Newton's convergence) says so, or fail it at max_newton (lns_newton_iter's rule).
+lns_status after_iteration(lns_model* m, lns_iter_stats* st) {
+  const bool done = m->o.mode == LNS_MODE_FULL ? m->converged : (!m->is_expand && m->converged);
+  if (done) {
+    TRY(close_step(m));
+    TRY(sync(m));
+    if (st) st->step_done = 1;
+  } else if (m->cur.iterations >= m->o.max_newton) {
+    TRY(close_step(m));
+    TRY(sync(m));
+    if (st) st->step_done = 1;
+    return fail(LNS_ENOCONV, "Newton loop reached max_newton");
+  }
+  return LNS_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -765,6 +802,77 @@ lns_status dd_timestep(lns_model* m, double dt, lns_step_stats* out) {
   m->cur.status = st;
   if (out) *out = m->cur;
   return st;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched advance: one Newton iteration of a member split around its solve, so that the host can
+// read n_A of every member between the halves and launch only the solver that takes it (the same
+// rule the device applies in a single model's iteration: n_A <= the cluster capacity).  Each half
+// is captured once per member as a CUDA graph.
+// ---------------------------------------------------------------------------------------
+lns_status enqueue_pre(lns_model* m) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  TRY(reset_iter(m));
+  CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, c));
+  const int lines = m->o.precond == LNS_PRECOND_BJAC;
+  CK(lns::launch_assemble(d, eff_p_scale(m), m->o.krylov_fp32, lines, 0, c));
+  if (lines) CK(lns::launch_line_setup(d, m->o.krylov_fp32, c));
+  CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+  return LNS_OK;
+}
+
+lns_status enqueue_post(lns_model* m) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  const bool local = m->o.mode == LNS_MODE_LOCAL;
+  CK(lns::launch_flag(d, local ? d.vb : nullptr, 1, 0, 0, m->o.eps_p, m->o.eps_sw, eff_p_scale(m), m->o.sat_chop,
+                      m->o.krylov_fp32, d.kx, m->o.krylov_fail_rtol, c));
+  if (local) {
+    TRY(dilate(m, m->o.m_layers));
+    CK(lns::launch_alg1_combine(d, m->o.tol_dp, m->o.tol_cnv, -1, c));
+  }
+  CK(cudaMemcpyAsync(d.ctr_h, d.ctr, sizeof(IterCounters), cudaMemcpyDeviceToHost, m->stream));
+  return LNS_OK;
+}
+
+// Run half k (0 before the solve, 1 after it) of a member's iteration: its graph, captured on first
+// use, or direct launches (m_layers > 8: the expansion reads frontier sizes on the host).
+lns_status run_half(lns_model* m, int k) {
+  auto body = [&]() { return k == 0 ? enqueue_pre(m) : enqueue_post(m); };
+  if (!(m->bgraph_ok && m->o.m_layers <= 8)) return body();
+  if (!m->bx[k]) {
+    const int64_t before = lns::g_launches.load(std::memory_order_relaxed);
+    if (cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      m->bgraph_ok = false;
+      return body();
+    }
+    lns_status r = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(m->stream, &g);
+    if (r != LNS_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&m->bx[k], g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      m->bx[k] = nullptr;
+      cudaGetLastError();
+      m->bgraph_ok = false;
+      lns::count_launches((int)-(lns::g_launches.load(std::memory_order_relaxed) - before));
+      return body();
+    }
+    m->bg[k] = g;
+    m->bx_kernels[k] = lns::g_launches.load(std::memory_order_relaxed) - before;
+    lns::count_launches((int)-m->bx_kernels[k]);  // nothing ran during the capture
+  }
+  CK(cudaGraphLaunch(m->bx[k], m->stream));
+  lns::count_launches((int)m->bx_kernels[k]);
+  return LNS_OK;
+}
+
+// The solver the device would pick for this member's system (n_A read by the host).
+int pick_solver(lns_model* m) {
+  const int fp32 = m->o.krylov_fp32, lines = m->o.precond == LNS_PRECOND_BJAC;
+  const lns::ClusterShape cl = cluster_shape(m, fp32, lines);
+  return (cl.ctas > 0 && m->d.ctr_h->n_active <= cl.cap && m->fault_h != 1) ? 1 : 2;
 }
 
 lns_status check_model(const lns_model* m) {
@@ -1147,6 +1255,7 @@ lns_status lns_debug_fault(lns_model* m, int32_t code) {
   TRY(check_model(m));
   if (code < 0 || code > 3) return fail(LNS_EINVAL, "fault code must be 0..3");
   CK(cudaMemcpyAsync(m->d.fault, &code, sizeof(int), cudaMemcpyHostToDevice, m->stream));
+  m->fault_h = code;
   return sync(m);
 }
 
@@ -1218,20 +1327,9 @@ lns_status lns_newton_iter(lns_model* m, double dt, lns_iter_stats* out) {
     if (out) *out = st;
     return s;
   }
-  const bool done = m->o.mode == LNS_MODE_FULL ? m->converged : (!m->is_expand && m->converged);
-  if (done) {
-    TRY(close_step(m));
-    TRY(sync(m));
-    st.step_done = 1;
-  } else if (m->cur.iterations >= m->o.max_newton) {
-    TRY(close_step(m));
-    TRY(sync(m));
-    st.step_done = 1;
-    if (out) *out = st;
-    return fail(LNS_ENOCONV, "Newton loop reached max_newton");
-  }
+  s = after_iteration(m, &st);
   if (out) *out = st;
-  return LNS_OK;
+  return s;
 }
 
 lns_status lns_advance(lns_model* m, double t_span, const lns_dt_control* ctl, lns_advance_stats* out) {
@@ -1292,6 +1390,142 @@ lns_status lns_advance(lns_model* m, double t_span, const lns_dt_control* ctl, l
   a.dt_next = dt;
   if (out) *out = a;
   return s;
+}
+
+lns_status lns_batch_advance(lns_model* const* members, int32_t n_members, double t_span, const lns_dt_control* ctl,
+                             lns_advance_stats* out, lns_batch_stats* bst) {
+  if (bst) std::memset(bst, 0, sizeof(*bst));
+  if (n_members < 0 || (n_members > 0 && (!members || !out)))
+    return fail(LNS_EINVAL, "members and out must be non-NULL");
+  if (!(t_span > 0.0) || !std::isfinite(t_span)) return fail(LNS_EINVAL, "t_span must be positive and finite");
+  lns_dt_control c{t_span, t_span / 1024.0, t_span, 2.0, 0.5, 4};
+  if (ctl) c = *ctl;
+  if (!(c.dt_init > 0.0) || !(c.dt_min > 0.0) || !(c.dt_max >= c.dt_min) || !(c.grow >= 1.0) || !(c.cut > 0.0) ||
+      !(c.cut < 1.0) || !std::isfinite(c.dt_init) || !std::isfinite(c.dt_max) || !std::isfinite(c.grow))
+    return fail(LNS_EINVAL, "bad time-step controller");
+  std::vector<lns_model*> ms(members, members + n_members);
+  for (int i = 0; i < n_members; i++) {
+    TRY(check_model(ms[i]));
+    for (int j = 0; j < i; j++)
+      if (ms[j] == ms[i]) return fail(LNS_EINVAL, "a model appears twice in the batch");
+    if (ms[i]->o.mode != LNS_MODE_LOCAL && ms[i]->o.mode != LNS_MODE_FULL)
+      return fail(LNS_EINVAL, "batched advance runs standard Newton or Algorithm 1 only");
+    if (ms[i]->step_open) return fail(LNS_ESTATE, "a member has a timestep open");
+  }
+  struct Member {
+    lns_model* m;
+    double t, dt, h;
+    int had_prev;
+    bool live, open;
+    lns_advance_stats a;
+  };
+  std::vector<Member> st(n_members);
+  for (int i = 0; i < n_members; i++) {
+    lns_model* m = ms[i];
+    Dev& d = m->d;
+    std::memset(&out[i], 0, sizeof(out[i]));
+    st[i] = Member{m, 0.0, std::min(c.dt_init, c.dt_max), 0.0, 0, true, false, lns_advance_stats{}};
+    if (d.n == 0) {  // nothing to solve: the plain controller
+      lns_status s = lns_advance(m, t_span, &c, &out[i]);
+      if (s != LNS_OK) return s;
+      st[i].live = false;
+      continue;
+    }
+    const size_t n = (size_t)d.n;
+    if (!m->ck_state) TRY(dalloc_t(m, 2 * n, &m->ck_state));
+    if (!m->ck_prev) TRY(dalloc_t(m, (size_t)std::max(d.W, 1), &m->ck_prev));
+    if (m->o.krylov_fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
+  }
+  // the end of a step attempt (lns_advance's controller)
+  auto end_step = [&](Member& b, lns_status s) -> lns_status {
+    lns_model* m = b.m;
+    Dev& d = m->d;
+    const size_t n = (size_t)d.n;
+    b.a.iterations += m->cur.iterations;
+    b.a.krylov_iters += m->cur.krylov_iters;
+    b.a.cell_updates += m->cur.cell_updates;
+    b.open = false;
+    if (s == LNS_OK) {
+      b.t = (b.h == t_span - b.t) ? t_span : b.t + b.h;
+      b.a.steps += 1;
+      if (m->cur.iterations <= c.easy_iters) b.dt = std::min(b.dt * c.grow, c.dt_max);
+      if (b.t >= t_span) b.live = false;
+      return LNS_OK;
+    }
+    if (s != LNS_ENOCONV && s != LNS_EKRYLOV) {
+      b.a.status = s;
+      b.live = false;
+      return LNS_OK;
+    }
+    CK(cudaMemcpyAsync(d.p, m->ck_state, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.sw, m->ck_state + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaMemcpyAsync(d.prev, m->ck_prev, sizeof(uint32_t) * (size_t)d.W, cudaMemcpyDeviceToDevice, m->stream));
+    m->has_prev = b.had_prev;
+    b.a.cuts += 1;
+    b.dt = b.h * c.cut;
+    if (b.dt < c.dt_min) {
+      b.a.status = LNS_ENOCONV;
+      b.live = false;
+    }
+    return LNS_OK;
+  };
+  for (;;) {
+    std::vector<Member*> live;
+    for (auto& b : st)
+      if (b.live) live.push_back(&b);
+    if (live.empty()) break;
+    if (bst) bst->rounds += 1;
+    for (Member* b : live) {  // open a step where none is open (checkpoint first, as lns_advance)
+      if (b->open) continue;
+      lns_model* m = b->m;
+      Dev& d = m->d;
+      const size_t n = (size_t)d.n;
+      b->h = std::min(b->dt, t_span - b->t);
+      CK(cudaMemcpyAsync(m->ck_state, d.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+      CK(cudaMemcpyAsync(m->ck_state + n, d.sw, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+      CK(cudaMemcpyAsync(m->ck_prev, d.prev, sizeof(uint32_t) * (size_t)d.W, cudaMemcpyDeviceToDevice, m->stream));
+      b->had_prev = m->has_prev;
+      TRY(open_step(m, b->h));
+      b->open = true;
+    }
+    for (Member* b : live) TRY(run_half(b->m, 0));
+    for (Member* b : live) CK(cudaStreamSynchronize(b->m->stream));
+    for (Member* b : live) {
+      lns_model* m = b->m;
+      const int which = pick_solver(m);
+      if (bst) (which == 1 ? bst->cluster_solves : bst->grid_solves) += 1;
+      CK(lns::launch_bicgstab_which(m->d, m->o.krylov_fp32, m->o.precond == LNS_PRECOND_BJAC, m->o.krylov_rtol,
+                                    m->o.krylov_maxit, m->kgrid[m->o.krylov_fp32 ? 1 : 0],
+                                    cluster_shape(m, m->o.krylov_fp32, m->o.precond == LNS_PRECOND_BJAC), which,
+                                    cfg(m)));
+      TRY(run_half(m, 1));
+    }
+    for (Member* b : live) CK(cudaStreamSynchronize(b->m->stream));
+    for (Member* b : live) {
+      lns_model* m = b->m;
+      m->pending.clear();
+      lns_status s = finish_iteration(m, nullptr);
+      if (s != LNS_OK) {
+        m->step_open = false;
+        TRY(end_step(*b, s));
+        continue;
+      }
+      s = after_iteration(m, nullptr);
+      if (s != LNS_OK || !m->step_open) TRY(end_step(*b, s));
+    }
+  }
+  lns_status first_bad = LNS_OK;
+  for (int i = 0; i < n_members; i++) {
+    Member& b = st[i];
+    if (b.m->d.n == 0) continue;
+    TRY(sync(b.m));
+    b.a.t_done = b.t;
+    b.a.dt_next = b.dt;
+    out[i] = b.a;
+    if (b.a.status != LNS_OK && first_bad == LNS_OK) first_bad = (lns_status)b.a.status;
+  }
+  if (first_bad != LNS_OK) return fail(first_bad, "a member of the batch did not complete (see its status)");
+  return LNS_OK;
 }
 
 lns_status lns_timestep(lns_model* m, double dt, lns_step_stats* out) {

@@ -152,6 +152,8 @@ struct ClusterShape {
 };
 cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, ClusterShape cl,
                             LaunchCfg c);
+cudaError_t launch_bicgstab_which(const Dev& d, int fp32, int lines, double rtol, int maxit, int grid, ClusterShape cl,
+                                  int which, LaunchCfg c);
 int krylov_grid(int fp32, int sms);
 // The largest cluster (<= max_ctas, a power of two) the device co-schedules for the cluster solver.
 ClusterShape krylov_cluster_shape(int fp32, int lines, int max_ctas);

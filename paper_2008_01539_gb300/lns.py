@@ -87,6 +87,10 @@ class lns_advance_stats(C.Structure):
                 ("dt_next", C.c_double)]
 
 
+class lns_batch_stats(C.Structure):
+    _fields_ = [("rounds", C.c_int32), ("cluster_solves", C.c_int64), ("grid_solves", C.c_int64)]
+
+
 class lns_server_options(C.Structure):
     _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
 
@@ -121,7 +125,7 @@ EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_
            "lns_launch_count", "lns_last_error", "lns_active_set_noalloc",
            "lns_server_create", "lns_server_destroy", "lns_server_add_model", "lns_server_submit",
            "lns_server_poll", "lns_server_drain", "lns_server_get_state", "lns_server_get_stats", "lns_server_now",
-           "lns_server_cancel", "lns_debug_fault", "lns_advance", "lns_compact"]
+           "lns_server_cancel", "lns_debug_fault", "lns_advance", "lns_compact", "lns_batch_advance"]
 
 
 def library_path() -> str:
@@ -153,6 +157,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "lns_solve_local": [vp, f64, vp, vp, vp, P(lns_iter_stats)],
         "lns_assemble": [vp, f64, vp, vp, vp, vp],
         "lns_compact": [vp, vp, vp, vp, P(i32)],
+        "lns_batch_advance": [vp, i32, f64, P(lns_dt_control), vp, P(lns_batch_stats)],
         "lns_get_state": [vp, vp, vp],
         "lns_set_state": [vp, vp, vp, vp, vp],
         "lns_get_state_device": [vp, vp, vp],
@@ -207,6 +212,22 @@ def lns_active_set_noalloc(n_cells: int, row_ptr: int, nbr: int, always_bits: in
                                          dsw or None, float(eps_p), float(eps_sw), int(m_layers), int(bool(converged)),
                                          va_bits or None, vb_bits or None, C.byref(ie), stream or None))
     return int(ie.value)
+
+
+def lns_batch_advance(models, t_span: float, dt_init: Optional[float] = None, dt_min: Optional[float] = None,
+                      dt_max: Optional[float] = None, grow: float = 2.0, cut: float = 0.5, easy_iters: int = 4,
+                      allow_noconv: bool = False) -> Tuple[List[Dict], Dict]:
+    """Advance every Model in `models` by t_span seconds together (lns_batch_advance), each with its
+    own time-step controller; returns the members' statistics and the batch's."""
+    ctl = lns_dt_control(float(dt_init if dt_init is not None else t_span),
+                         float(dt_min if dt_min is not None else t_span / 1024.0),
+                         float(dt_max if dt_max is not None else t_span), float(grow), float(cut), int(easy_iters))
+    hs = (C.c_void_p * max(len(models), 1))(*[m.h for m in models])
+    outs = (lns_advance_stats * max(len(models), 1))()
+    bst = lns_batch_stats()
+    rc = load().lns_batch_advance(hs, len(models), float(t_span), C.byref(ctl), outs, C.byref(bst))
+    _check(rc, allow=(LNS_ENOCONV,) if allow_noconv else ())
+    return [_as_dict(outs[i]) for i in range(len(models))], _as_dict(bst)
 
 
 def _check(rc: int, allow=()) -> int:
