@@ -126,6 +126,9 @@ typedef struct {
                            * vectors in distributed shared memory) are solved there, larger ones by
                            * the grid solver over every SM: the largest cluster in CTAs (2, 4, 8 or
                            * 16); 0: the grid solver only; < 0: the default (16).  Default -1. */
+  int32_t autotune;       /* 1: the first timestep of a model whose size class has no cached tuning
+                           * runs lns_autotune first (a one-time cost per device, precision,
+                           * preconditioner and size class); 0: the cache or the defaults.  Default 1. */
 } lns_options;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
@@ -220,12 +223,14 @@ lns_status lns_advance(lns_model* model, double t_span, const lns_dt_control* ct
  * together.  The paper advances one model (Section 4.3); this runs its method on every member at
  * once.  Each member keeps its own state, active sets, convergence test and time-step controller
  * (lns_advance's rule with ctl, applied per member: a member whose step fails is cut and retried
- * while the others go on), so every member ends exactly as lns_advance(member, t_span, ctl) alone
- * would leave it, bit for bit.  A round advances every live member by one Newton iteration: the
- * work before the solve (compaction, assembly, line factors) of all members, then each member's
- * solve and update; the members' work runs on their own streams and overlaps on the device (a
- * system small enough for the cluster solver occupies up to 16 SMs; larger ones take the grid
- * solver, one at a time).  Give every member a stream of its own (lns_set_stream) for overlap.
+ * while the others go on).  A round advances every live member by one Newton iteration: the work
+ * before the solve (compaction, assembly, line factors) of all members, then each member's solve
+ * and update; the members' work runs on their own streams and overlaps on the device.  Every
+ * system the cluster solver can hold goes to it (it occupies up to 16 SMs, so the members' solves
+ * run side by side), larger ones to the grid solver, one at a time; so each member ends exactly,
+ * bit for bit, as lns_advance(member, t_span, ctl) leaves it alone with the tuning's
+ * cluster_max_rows < 0 (every system that fits in the cluster).  Give every member a stream of its
+ * own (lns_set_stream) for overlap.
  * Members: standard Newton or Algorithm 1, no timestep open, each model at most once.  out
  * [n_members] gets each member's statistics (status per member); the call returns the first
  * member's failure status, if any, after all members are done. */
@@ -309,6 +314,47 @@ lns_status lns_reset(lns_model* model);
 /* The previous timestep's support set (the next step's initial active set before the
  * always-active cells are added). */
 lns_status lns_get_support(const lns_model* model, uint32_t* bits);
+
+/* ---------------------------------------------------------------------------------------
+ * Autotuning.  The paper has no counterpart (its method is independent of the hardware); these
+ * choices only change how the kernels are laid out over the GPU, never what they compute:
+ *   - cluster_max_rows: local systems of at most this many rows are solved by the thread-block
+ *     cluster solver, larger ones by the grid solver (clamped to the cluster solver's capacity;
+ *     < 0: its capacity; 0: never).  The two solvers reach the same Krylov tolerance with a
+ *     different reduction order, so this choice moves results by rounding only;
+ *   - asm_block, asm_blocks_per_sm: block size (64, 128 or 256 threads, two lanes per row) and
+ *     blocks per SM of the assembly (0: defaults 64 and 4);
+ *   - set_blocks_per_sm: blocks per SM of the update/flag and frontier-expansion kernels
+ *     (0: default 4).
+ * Launch shapes leave every result bit-identical (each row is computed by its own lanes and every
+ * set operation is order-independent).
+ *
+ * lns_autotune measures on the model's own data and device: it builds active sets of growing size
+ * (the always-active cells, then 1, 2, 4, ... more rings of neighbours), assembles each system, and
+ * times both solvers and each launch shape with CUDA events; cluster_max_rows is the largest size
+ * up to which the cluster solver was faster at every measured size.  It applies the choice to the
+ * model, stores it in a process-wide cache keyed by device, Krylov precision, preconditioner and
+ * model size class (the bit length of n_cells), and returns it.  Models created later (or given new
+ * options) in the same class take the cached choice unless lns_set_tuning set one.  The model's
+ * state is not changed; no timestep may be open.  Work runs on the model's stream. */
+typedef struct {
+  int32_t cluster_max_rows;
+  int32_t asm_block;
+  int32_t asm_blocks_per_sm;
+  int32_t set_blocks_per_sm;
+  int32_t measured;       /* 1: chosen by lns_autotune (here or from the cache), 0: defaults or caller's */
+} lns_tuning;
+lns_status lns_autotune(lns_model* model, lns_tuning* out);
+lns_status lns_get_tuning(const lns_model* model, lns_tuning* out);
+lns_status lns_set_tuning(lns_model* model, const lns_tuning* tuning);
+/* The autotuner's solver rule on its measurements (exported so it can be checked without a GPU):
+ * sizes ascending; t_cluster[k] < 0 where the system did not fit the cluster solver.  Returns the
+ * largest sizes[k] such that the cluster solver was faster at sizes[0..k], else 0. */
+int32_t lns_tune_pick(int32_t n, const int32_t* sizes, const double* t_cluster, const double* t_grid);
+/* The cache (exported for the same reason): lookup returns 1 and fills *out when an entry exists. */
+int32_t lns_tune_cache_lookup(int32_t device, int32_t krylov_fp32, int32_t precond, int32_t n_cells, lns_tuning* out);
+void lns_tune_cache_store(int32_t device, int32_t krylov_fp32, int32_t precond, int32_t n_cells, const lns_tuning* t);
+void lns_tune_cache_clear(void);
 
 /* Kernel timing (options.profile = 1 or 2): up to cap entries, *count gets the number. */
 lns_status lns_kernel_times(const lns_model* model, lns_kernel_time* out, int32_t cap, int32_t* count);

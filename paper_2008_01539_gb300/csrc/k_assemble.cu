@@ -91,9 +91,9 @@ __device__ __forceinline__ PhaseProps phase_props(const FluidK& F, double p, dou
 // other row coming from its partner by shuffle.  Splitting the phases halves the chain of
 // dependent FP64 instructions a warp issues per row (one FP64 warp instruction per ~64 cycles at
 // most on this GPU), and the rows spread over all SMs.
-template <typename T>
-__global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double p_scale, double inv_p_scale, int lines,
-                                                     int debug) {
+template <typename T, int BLK>
+__global__ void __launch_bounds__(BLK) k_assemble(Dev d, FluidK F, double p_scale, double inv_p_scale, int lines,
+                                                 int debug) {
   const int nA = d.ctr->n_active;
   const double dt = d.stepp[0], inv_dt = d.stepp[1];
   const double g = F.f.gravity;
@@ -221,13 +221,13 @@ __global__ void __launch_bounds__(kAsmBlk) k_assemble(Dev d, FluidK F, double p_
     }
   }
   // CNV maximum over the block, one atomic per block
-  __shared__ double sh[kAsmBlk / 32];
+  __shared__ double sh[BLK / 32];
   for (int o = 16; o > 0; o >>= 1) cnv_max = fmax(cnv_max, __shfl_xor_sync(0xffffffffu, cnv_max, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = cnv_max;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
-    for (int w = 0; w < kAsmBlk / 32; w++) m = fmax(m, sh[w]);
+    for (int w = 0; w < BLK / 32; w++) m = fmax(m, sh[w]);
     atomicMax(&d.ctr->cnv_bits, (unsigned long long)__double_as_longlong(m));
   }
 }
@@ -460,12 +460,26 @@ cudaError_t launch_assemble(const Dev& d, double p_scale, int fp32, int lines, i
   F.inv_span = 1.0 / (1.0 - d.fl.swc - d.fl.sor);
   F.inv_mu[0] = 1.0 / d.fl.mu_o;
   F.inv_mu[1] = 1.0 / d.fl.mu_w;
-  const int grid = 4 * c.sms;
+  // launch shape (results do not depend on it: every row is computed by its own lane pair)
+  const int blk = c.asm_block == 128 || c.asm_block == 256 ? c.asm_block : kAsmBlk;
+  const int grid = (c.asm_mult >= 1 && c.asm_mult <= 16 ? c.asm_mult : 4) * c.sms;
   count_launches(1);
-  if (fp32)
-    k_assemble<float><<<grid, kAsmBlk, 0, c.stream>>>(d, F, p_scale, 1.0 / p_scale, lines, debug);
-  else
-    k_assemble<double><<<grid, kAsmBlk, 0, c.stream>>>(d, F, p_scale, 1.0 / p_scale, lines, debug);
+  const double ips = 1.0 / p_scale;
+  if (fp32) {
+    if (blk == 256)
+      k_assemble<float, 256><<<grid, 256, 0, c.stream>>>(d, F, p_scale, ips, lines, debug);
+    else if (blk == 128)
+      k_assemble<float, 128><<<grid, 128, 0, c.stream>>>(d, F, p_scale, ips, lines, debug);
+    else
+      k_assemble<float, kAsmBlk><<<grid, kAsmBlk, 0, c.stream>>>(d, F, p_scale, ips, lines, debug);
+  } else {
+    if (blk == 256)
+      k_assemble<double, 256><<<grid, 256, 0, c.stream>>>(d, F, p_scale, ips, lines, debug);
+    else if (blk == 128)
+      k_assemble<double, 128><<<grid, 128, 0, c.stream>>>(d, F, p_scale, ips, lines, debug);
+    else
+      k_assemble<double, kAsmBlk><<<grid, kAsmBlk, 0, c.stream>>>(d, F, p_scale, ips, lines, debug);
+  }
   return cudaGetLastError();
 }
 

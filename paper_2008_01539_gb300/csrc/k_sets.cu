@@ -340,6 +340,9 @@ inline int words_grid(int W) { return (W + kBlk - 1) / kBlk; }
 
 }  // namespace
 
+// grid of the per-iteration list kernels (update/flag, frontier expansion, halo): blocks per SM x SMs
+static int set_grid(const LaunchCfg& c) { return (c.set_mult >= 1 && c.set_mult <= 16 ? c.set_mult : 4) * c.sms; }
+
 cudaError_t launch_compact(const Dev& d, const uint32_t* bits, int* list, int* inv, int* count_out, LaunchCfg c) {
   int nb = words_grid(d.W);
   if (nb == 0) return cudaMemsetAsync(count_out, 0, sizeof(int), c.stream);
@@ -362,7 +365,7 @@ cudaError_t launch_outer_halo(const Dev& d, const uint32_t* set, const int* list
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t) * (size_t)d.W, c.stream);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  k_outer_halo<<<4 * c.sms, kBlk, 0, c.stream>>>(d.row_ptr, d.nbr, set, list, count, out);
+  k_outer_halo<<<set_grid(c), kBlk, 0, c.stream>>>(d.row_ptr, d.nbr, set, list, count, out);
   return cudaGetLastError();
 }
 
@@ -371,10 +374,10 @@ cudaError_t launch_flag(const Dev& d, const uint32_t* vb, int apply, int record_
                         LaunchCfg c) {
   count_launches(1);
   if (fp32)
-    k_flag<float><<<4 * c.sms, kBlk, 0, c.stream>>>(d, vb, apply, record_stamp, solve_id, eps_p, eps_sw, p_scale,
+    k_flag<float><<<set_grid(c), kBlk, 0, c.stream>>>(d, vb, apply, record_stamp, solve_id, eps_p, eps_sw, p_scale,
                                                     sat_chop, (const float*)x, fail_rtol);
   else
-    k_flag<double><<<4 * c.sms, kBlk, 0, c.stream>>>(d, vb, apply, record_stamp, solve_id, eps_p, eps_sw, p_scale,
+    k_flag<double><<<set_grid(c), kBlk, 0, c.stream>>>(d, vb, apply, record_stamp, solve_id, eps_p, eps_sw, p_scale,
                                                      sat_chop, (const double*)x, fail_rtol);
   return cudaGetLastError();
 }
@@ -389,7 +392,7 @@ cudaError_t launch_dilate(const Dev& d, uint32_t* reach, int layers, LaunchCfg c
     cudaError_t e = cudaMemsetAsync(cout, 0, sizeof(int), c.stream);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_dilate_round<<<4 * c.sms, kBlk, 0, c.stream>>>(d.row_ptr, d.nbr, fin, cin, fout, cout, reach);
+    k_dilate_round<<<set_grid(c), kBlk, 0, c.stream>>>(d.row_ptr, d.nbr, fin, cin, fout, cout, reach);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -398,7 +401,7 @@ cudaError_t launch_dilate(const Dev& d, uint32_t* reach, int layers, LaunchCfg c
 
 cudaError_t launch_seed_frontier(const Dev& d, const int* list, int count_host, uint32_t* reach, LaunchCfg c) {
   count_launches(1);
-  k_seed<<<4 * c.sms, kBlk, 0, c.stream>>>(list, count_host, reach, d.fr0, &d.ctr->n_frontier[0]);
+  k_seed<<<set_grid(c), kBlk, 0, c.stream>>>(list, count_host, reach, d.fr0, &d.ctr->n_frontier[0]);
   return cudaGetLastError();
 }
 

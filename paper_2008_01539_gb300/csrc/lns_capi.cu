@@ -14,6 +14,9 @@
 #include <vector>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -79,6 +82,8 @@ struct lns_model {
   lns::ClusterShape kcl[2][2] = {};  // cluster BiCGStab [fp32][lines] for the current krylov_cluster
   int kcl_max = -2;                  // krylov_cluster the shapes were computed for
   int fault_h = 0;                   // host copy of the injected solver fault (lns_debug_fault)
+  lns_tuning tune{};                 // launch shapes and solver choice (lns_autotune / lns_set_tuning)
+  bool tune_explicit = false;        // set by the caller: cached tunings do not replace it
   // batched advance (lns_batch_advance): the iteration split around the solve, each half captured
   cudaGraph_t bg[2] = {nullptr, nullptr};
   cudaGraphExec_t bx[2] = {nullptr, nullptr};
@@ -114,7 +119,13 @@ struct lns_model {
 
 namespace {
 
-LaunchCfg cfg(const lns_model* m) { return LaunchCfg{m->sms, m->stream}; }
+LaunchCfg cfg(const lns_model* m) {
+  LaunchCfg c{m->sms, m->stream};
+  c.asm_block = m->tune.asm_block;
+  c.asm_mult = m->tune.asm_blocks_per_sm;
+  c.set_mult = m->tune.set_blocks_per_sm;
+  return c;
+}
 
 // dt and 1/dt of the next solves to the device (only when dt changes; the previous upload of the
 // pinned pair has completed: every solve ends with a stream synchronization)
@@ -294,7 +305,12 @@ lns::ClusterShape cluster_shape(lns_model* m, int fp32, int lines) {
       for (int l = 0; l < 2; l++) m->kcl[f][l] = lns::krylov_cluster_shape(f, l, want);
     m->kcl_max = want;
   }
-  return m->kcl[fp32 ? 1 : 0][lines ? 1 : 0];
+  lns::ClusterShape cl = m->kcl[fp32 ? 1 : 0][lines ? 1 : 0];
+  if (cl.ctas > 0 && m->tune.cluster_max_rows >= 0) {  // the autotuner's threshold (< 0: capacity)
+    if (m->tune.cluster_max_rows == 0) return lns::ClusterShape{0, -1};
+    cl.cap = std::min(cl.cap, m->tune.cluster_max_rows);
+  }
+  return cl;
 }
 
 // Solve the local system on the set currently in d.va at the current state: compaction,
@@ -868,11 +884,68 @@ lns_status run_half(lns_model* m, int k) {
   return LNS_OK;
 }
 
-// The solver the device would pick for this member's system (n_A read by the host).
-int pick_solver(lns_model* m) {
+// The solver of a batch member's system (n_A read by the host): the cluster solver whenever the
+// system fits it.  The autotuner's threshold compares the two solvers' latency on a model alone;
+// in a batch the members' cluster solves run concurrently on different SMs, which the grid solver
+// (all SMs, one solve at a time) cannot.
+lns::ClusterShape batch_shape(lns_model* m) {
   const int fp32 = m->o.krylov_fp32, lines = m->o.precond == LNS_PRECOND_BJAC;
-  const lns::ClusterShape cl = cluster_shape(m, fp32, lines);
+  (void)cluster_shape(m, fp32, lines);  // the capacity for the current krylov_cluster
+  return m->kcl[fp32 ? 1 : 0][lines ? 1 : 0];
+}
+
+int pick_solver(lns_model* m) {
+  const lns::ClusterShape cl = batch_shape(m);
   return (cl.ctas > 0 && m->d.ctr_h->n_active <= cl.cap && m->fault_h != 1) ? 1 : 2;
+}
+
+// ---------------------------------------------------------------------------------------
+// Autotuner: defaults, process-wide cache, measurement.
+// ---------------------------------------------------------------------------------------
+lns_tuning default_tuning() {
+  lns_tuning t{};
+  t.cluster_max_rows = -1;
+  t.asm_block = 0;
+  t.asm_blocks_per_sm = 0;
+  t.set_blocks_per_sm = 0;
+  t.measured = 0;
+  return t;
+}
+
+int size_class(int n) {
+  int b = 0;
+  while (n > 0) {
+    b++;
+    n >>= 1;
+  }
+  return b;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, lns_tuning>& tune_cache() {
+  static std::map<std::tuple<int, int, int, int>, lns_tuning> c;
+  return c;
+}
+
+// the cached tuning of the model's class, unless the caller set one
+void apply_cached_tuning(lns_model* m);
+// lns_autotune on first use when the options ask for it and nothing decided the tuning yet
+lns_status maybe_autotune(lns_model* m);
+void apply_cached_tuning(lns_model* m) {
+  if (m->tune_explicit) return;
+  lns_tuning t;
+  if (lns_tune_cache_lookup(m->device, m->o.krylov_fp32, m->o.precond, m->d.n, &t))
+    m->tune = t;
+  else
+    m->tune = default_tuning();
+}
+
+lns_status maybe_autotune(lns_model* m) {
+  if (!m->o.autotune || m->tune.measured || m->tune_explicit || m->fault_h != 0 || m->o.profile != 0 || m->d.n == 0)
+    return LNS_OK;
+  apply_cached_tuning(m);  // another model of this class may have measured it meanwhile
+  if (m->tune.measured) return LNS_OK;
+  return lns_autotune(m, nullptr);
 }
 
 lns_status check_model(const lns_model* m) {
@@ -979,6 +1052,7 @@ lns_status lns_options_default(lns_options* o) {
   o->profile = 0;
   o->fp64_fallback = 1;
   o->krylov_cluster = -1;
+  o->autotune = 1;
   return LNS_OK;
 }
 
@@ -1007,6 +1081,7 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
   m->kgrid[0] = lns::krylov_grid(0, m->sms);
   m->kgrid[1] = lns::krylov_grid(1, m->sms);
   cluster_shape(m, 0, 0);  // function attributes and occupancy queries stay outside stream capture
+  m->tune = default_tuning();
   Dev& d = m->d;
   d.n = n;
   d.n_adj = na;
@@ -1139,6 +1214,7 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
   e = e ? e : up(d.sw0, desc->sw0, sizeof(double) * (size_t)n);
   if (n == 0 && e == cudaSuccess) e = cudaMemsetAsync(d.row_ptr, 0, sizeof(int), m->stream);
   if (e != cudaSuccess) return cleanup_fail(fail(LNS_ECUDA, std::string("upload: ") + cudaGetErrorString(e)));
+  apply_cached_tuning(m);
   *out = m;
   lns_status r = lns_reset(m);
   if (r != LNS_OK) {
@@ -1176,6 +1252,7 @@ lns_status lns_set_options(lns_model* m, const lns_options* o) {
   m->o = *o;
   drop_graph(m);  // captured with the old options
   cluster_shape(m, 0, 0);
+  apply_cached_tuning(m);
   return LNS_OK;
 }
 
@@ -1319,7 +1396,10 @@ lns_status lns_newton_iter(lns_model* m, double dt, lns_iter_stats* out) {
   if (m->o.mode == LNS_MODE_DD || m->o.mode == LNS_MODE_RESIDUAL)
     return fail(LNS_ESTATE, "lns_newton_iter is not available in LNS_MODE_DD or LNS_MODE_RESIDUAL");
   if (m->d.n == 0) return fail(LNS_EINVAL, "empty model");
-  if (!m->step_open) TRY(open_step(m, dt));
+  if (!m->step_open) {
+    TRY(maybe_autotune(m));
+    TRY(open_step(m, dt));
+  }
   lns_iter_stats st{};
   lns_status s = alg1_iteration(m, &st);
   if (s != LNS_OK) {
@@ -1435,6 +1515,7 @@ lns_status lns_batch_advance(lns_model* const* members, int32_t n_members, doubl
     if (!m->ck_state) TRY(dalloc_t(m, 2 * n, &m->ck_state));
     if (!m->ck_prev) TRY(dalloc_t(m, (size_t)std::max(d.W, 1), &m->ck_prev));
     if (m->o.krylov_fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
+    TRY(maybe_autotune(m));
   }
   // the end of a step attempt (lns_advance's controller)
   auto end_step = [&](Member& b, lns_status s) -> lns_status {
@@ -1495,8 +1576,7 @@ lns_status lns_batch_advance(lns_model* const* members, int32_t n_members, doubl
       const int which = pick_solver(m);
       if (bst) (which == 1 ? bst->cluster_solves : bst->grid_solves) += 1;
       CK(lns::launch_bicgstab_which(m->d, m->o.krylov_fp32, m->o.precond == LNS_PRECOND_BJAC, m->o.krylov_rtol,
-                                    m->o.krylov_maxit, m->kgrid[m->o.krylov_fp32 ? 1 : 0],
-                                    cluster_shape(m, m->o.krylov_fp32, m->o.precond == LNS_PRECOND_BJAC), which,
+                                    m->o.krylov_maxit, m->kgrid[m->o.krylov_fp32 ? 1 : 0], batch_shape(m), which,
                                     cfg(m)));
       TRY(run_half(m, 1));
     }
@@ -1528,6 +1608,193 @@ lns_status lns_batch_advance(lns_model* const* members, int32_t n_members, doubl
   return LNS_OK;
 }
 
+int32_t lns_tune_pick(int32_t n, const int32_t* sizes, const double* t_cluster, const double* t_grid) {
+  int32_t best = 0;
+  for (int32_t k = 0; k < n && sizes && t_cluster && t_grid; k++) {
+    if (!(t_cluster[k] >= 0.0) || !(t_cluster[k] < t_grid[k])) break;
+    best = sizes[k];
+  }
+  return best;
+}
+
+int32_t lns_tune_cache_lookup(int32_t device, int32_t krylov_fp32, int32_t precond, int32_t n_cells, lns_tuning* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = tune_cache().find(std::make_tuple(device, krylov_fp32 ? 1 : 0, precond, size_class(n_cells)));
+  if (it == tune_cache().end()) return 0;
+  if (out) *out = it->second;
+  return 1;
+}
+
+void lns_tune_cache_store(int32_t device, int32_t krylov_fp32, int32_t precond, int32_t n_cells, const lns_tuning* t) {
+  if (!t) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_cache()[std::make_tuple(device, krylov_fp32 ? 1 : 0, precond, size_class(n_cells))] = *t;
+}
+
+void lns_tune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_cache().clear();
+}
+
+lns_status lns_get_tuning(const lns_model* m, lns_tuning* out) {
+  TRY(check_model(m));
+  if (!out) return fail(LNS_EINVAL, "out is NULL");
+  *out = m->tune;
+  return LNS_OK;
+}
+
+lns_status lns_set_tuning(lns_model* m, const lns_tuning* t) {
+  TRY(check_model(m));
+  if (!t) {  // back to the cache or the defaults
+    m->tune_explicit = false;
+    apply_cached_tuning(m);
+    drop_graph(m);
+    return LNS_OK;
+  }
+  if ((t->asm_block != 0 && t->asm_block != 64 && t->asm_block != 128 && t->asm_block != 256) ||
+      t->asm_blocks_per_sm < 0 || t->asm_blocks_per_sm > 16 || t->set_blocks_per_sm < 0 || t->set_blocks_per_sm > 16)
+    return fail(LNS_EINVAL, "asm_block must be 0, 64, 128 or 256 and blocks per SM 0..16");
+  m->tune = *t;
+  m->tune_explicit = true;
+  drop_graph(m);  // captured with the old launch shapes
+  return LNS_OK;
+}
+
+lns_status lns_autotune(lns_model* m, lns_tuning* out) {
+  TRY(check_model(m));
+  if (m->step_open) return fail(LNS_ESTATE, "a timestep is open");
+  Dev& d = m->d;
+  lns_tuning best = default_tuning();
+  if (d.n == 0) {
+    m->tune = best;
+    if (out) *out = best;
+    return LNS_OK;
+  }
+  const int fp32 = m->o.krylov_fp32, lines = m->o.precond == LNS_PRECOND_BJAC;
+  if (fp32 && !d.raw) TRY(dalloc_t(m, (size_t)std::max(d.n_adj, 1) * 4, &d.raw));
+  drop_graph(m);
+  const lns_tuning saved = m->tune;
+  m->tune = default_tuning();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto timed = [&](auto body, int reps, double* us) -> lns_status {
+    double best_us = 1e30;
+    for (int r = 0; r < reps; r++) {
+      CK(cudaEventRecord(e0, m->stream));
+      TRY(body());
+      CK(cudaEventRecord(e1, m->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      best_us = std::min(best_us, 1e3 * (double)ms);
+    }
+    *us = best_us;
+    return LNS_OK;
+  };
+  const int asm_blk[3] = {64, 128, 256}, mults[3] = {2, 4, 8};
+  double t_asm[3][3] = {}, t_set[3] = {};
+  std::vector<int32_t> sizes;
+  std::vector<double> tcl, tgr;
+  const lns::ClusterShape cap_shape = cluster_shape(m, fp32, lines);  // its capacity (no threshold yet)
+  TRY(set_dt(m, 10.0 * 86400.0));  // a mid-range step of the workloads (0.01-30 days)
+  lns_status st = [&]() -> lns_status {
+    // the always-active cells (every active set of the model contains them), or the model's initial
+    // set when it has none; then 1, 2, 4, ... more rings of neighbours at each step
+    if (d.n_always > 0)
+      CK(lns::launch_words_op(d, lns::kCopy, d.va, d.always, nullptr, cfg(m)));
+    else
+      TRY(initial_set(m, d.va));
+    for (int k = 0; k < 8; k++) {
+      TRY(reset_iter(m));
+      CK(lns::launch_compact(d, d.va, d.act, d.inv, &d.ctr->n_active, cfg(m)));
+      TRY(read_counters(m));
+      const int nA = d.ctr_h->n_active;
+      if (nA == 0) break;
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+          LaunchCfg c = cfg(m);
+          c.asm_block = asm_blk[a];
+          c.asm_mult = mults[b];
+          double us = 0;
+          TRY(timed([&]() -> lns_status {
+                CK(lns::launch_assemble(d, eff_p_scale(m), fp32, lines, 0, c));
+                return LNS_OK;
+              }, 3, &us));
+          t_asm[a][b] += us;
+        }
+      CK(lns::launch_assemble(d, eff_p_scale(m), fp32, lines, 0, cfg(m)));
+      if (lines) CK(lns::launch_line_setup(d, fp32, cfg(m)));
+      const lns::ClusterShape cl = cap_shape;
+      double tc = -1.0, tg = 0.0;
+      if (cl.ctas > 0 && nA <= cl.cap)
+        TRY(timed([&]() -> lns_status {
+              CK(lns::launch_bicgstab_which(d, fp32, lines, m->o.krylov_rtol, m->o.krylov_maxit, m->kgrid[fp32 ? 1 : 0],
+                                            cl, 1, cfg(m)));
+              return LNS_OK;
+            }, 3, &tc));
+      TRY(timed([&]() -> lns_status {
+            CK(lns::launch_bicgstab_which(d, fp32, lines, m->o.krylov_rtol, m->o.krylov_maxit, m->kgrid[fp32 ? 1 : 0], cl,
+                                          2, cfg(m)));
+            return LNS_OK;
+          }, 3, &tg));
+      sizes.push_back(nA);
+      tcl.push_back(tc);
+      tgr.push_back(tg);
+      for (int b = 0; b < 3; b++) {  // update/flag kernel (no state change; seeds the frontier with the
+                                     // moved boundary cells, at most n_A) and a two-ring expansion
+        LaunchCfg c = cfg(m);
+        c.set_mult = mults[b];
+        double us = 0;
+        TRY(timed([&]() -> lns_status {
+              CK(cudaMemsetAsync(d.reach, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+              CK(cudaMemsetAsync(&d.ctr->n_frontier[0], 0, 2 * sizeof(int), m->stream));
+              CK(lns::launch_flag(d, d.vb, 0, 0, 0, m->o.eps_p, m->o.eps_sw, eff_p_scale(m), m->o.sat_chop, fp32, d.kx,
+                                  -1.0, c));
+              CK(lns::launch_dilate(d, d.reach, 2, c));
+              return LNS_OK;
+            }, 3, &us));
+        t_set[b] += us;
+      }
+      if (nA >= d.n || (cl.ctas > 0 && nA > cl.cap) || (cl.ctas == 0 && k >= 2)) break;
+      // next set: this one and its neighbours
+      CK(cudaMemsetAsync(d.reach, 0, sizeof(uint32_t) * (size_t)d.W, m->stream));
+      CK(cudaMemsetAsync(d.ctr, 0, sizeof(IterCounters), m->stream));
+      CK(lns::launch_seed_frontier(d, d.act, nA, d.reach, cfg(m)));
+      CK(lns::launch_dilate(d, d.reach, 1 << k, cfg(m)));
+      CK(lns::launch_words_op(d, lns::kCopy, d.va, d.reach, nullptr, cfg(m)));
+    }
+    return LNS_OK;
+  }();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LNS_OK) {
+    m->tune = saved;
+    return st;
+  }
+  int ba = 0, bb = 1;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++)
+      if (t_asm[a][b] < t_asm[ba][bb]) {
+        ba = a;
+        bb = b;
+      }
+  int bs = 1;
+  for (int b = 0; b < 3; b++)
+    if (t_set[b] < t_set[bs]) bs = b;
+  best.cluster_max_rows = lns_tune_pick((int32_t)sizes.size(), sizes.data(), tcl.data(), tgr.data());
+  best.asm_block = asm_blk[ba];
+  best.asm_blocks_per_sm = mults[bb];
+  best.set_blocks_per_sm = mults[bs];
+  best.measured = 1;
+  m->tune = best;
+  m->tune_explicit = false;
+  lns_tune_cache_store(m->device, fp32, m->o.precond, d.n, &best);
+  TRY(sync(m));
+  if (out) *out = best;
+  return LNS_OK;
+}
+
 lns_status lns_timestep(lns_model* m, double dt, lns_step_stats* out) {
   TRY(check_model(m));
   NvtxRange range("lns_timestep");
@@ -1535,8 +1802,9 @@ lns_status lns_timestep(lns_model* m, double dt, lns_step_stats* out) {
     if (out) std::memset(out, 0, sizeof(*out));
     return LNS_OK;
   }
-  if (m->o.mode == LNS_MODE_DD) return dd_timestep(m, dt, out);
   if (m->step_open) return fail(LNS_ESTATE, "a timestep opened by lns_newton_iter is still open");
+  TRY(maybe_autotune(m));
+  if (m->o.mode == LNS_MODE_DD) return dd_timestep(m, dt, out);
   if (m->o.mode == LNS_MODE_RESIDUAL) return residual_timestep(m, dt, out);
   TRY(open_step(m, dt));
   lns_status s = LNS_OK;

@@ -115,6 +115,10 @@ lns_status validate_opts(const lns_options* o);
 struct LaunchCfg {
   int sms;
   cudaStream_t stream;
+  // launch shapes chosen by the autotuner (0: the defaults); results do not depend on them
+  int asm_block = 0;  // assembly threads per block (64, 128, 256)
+  int asm_mult = 0;   // assembly blocks per SM
+  int set_mult = 0;   // blocks per SM of the update/flag and frontier-expansion kernels
 };
 
 // k_sets.cu

@@ -51,7 +51,7 @@ class lns_options(C.Structure):
                 ("max_dd_outer", C.c_int32), ("sat_chop", C.c_double), ("krylov_fp32", C.c_int32),
                 ("precond", C.c_int32), ("krylov_rtol", C.c_double), ("krylov_maxit", C.c_int32),
                 ("krylov_fail_rtol", C.c_double), ("p_scale", C.c_double), ("profile", C.c_int32),
-                ("fp64_fallback", C.c_int32), ("krylov_cluster", C.c_int32)]
+                ("fp64_fallback", C.c_int32), ("krylov_cluster", C.c_int32), ("autotune", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -91,6 +91,11 @@ class lns_batch_stats(C.Structure):
     _fields_ = [("rounds", C.c_int32), ("cluster_solves", C.c_int64), ("grid_solves", C.c_int64)]
 
 
+class lns_tuning(C.Structure):
+    _fields_ = [("cluster_max_rows", C.c_int32), ("asm_block", C.c_int32), ("asm_blocks_per_sm", C.c_int32),
+                ("set_blocks_per_sm", C.c_int32), ("measured", C.c_int32)]
+
+
 class lns_server_options(C.Structure):
     _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
 
@@ -125,7 +130,9 @@ EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_
            "lns_launch_count", "lns_last_error", "lns_active_set_noalloc",
            "lns_server_create", "lns_server_destroy", "lns_server_add_model", "lns_server_submit",
            "lns_server_poll", "lns_server_drain", "lns_server_get_state", "lns_server_get_stats", "lns_server_now",
-           "lns_server_cancel", "lns_debug_fault", "lns_advance", "lns_compact", "lns_batch_advance"]
+           "lns_server_cancel", "lns_debug_fault", "lns_advance", "lns_compact", "lns_batch_advance",
+           "lns_autotune", "lns_get_tuning", "lns_set_tuning", "lns_tune_pick", "lns_tune_cache_lookup",
+           "lns_tune_cache_store", "lns_tune_cache_clear"]
 
 
 def library_path() -> str:
@@ -158,6 +165,9 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "lns_assemble": [vp, f64, vp, vp, vp, vp],
         "lns_compact": [vp, vp, vp, vp, P(i32)],
         "lns_batch_advance": [vp, i32, f64, P(lns_dt_control), vp, P(lns_batch_stats)],
+        "lns_autotune": [vp, P(lns_tuning)],
+        "lns_get_tuning": [vp, P(lns_tuning)],
+        "lns_set_tuning": [vp, P(lns_tuning)],
         "lns_get_state": [vp, vp, vp],
         "lns_set_state": [vp, vp, vp, vp, vp],
         "lns_get_state_device": [vp, vp, vp],
@@ -190,6 +200,14 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     L.lns_launch_count.restype = C.c_int64
     L.lns_server_now.argtypes = [vp]
     L.lns_server_now.restype = C.c_double
+    L.lns_tune_pick.argtypes = [i32, vp, vp, vp]
+    L.lns_tune_pick.restype = C.c_int32
+    L.lns_tune_cache_lookup.argtypes = [i32, i32, i32, i32, P(lns_tuning)]
+    L.lns_tune_cache_lookup.restype = C.c_int32
+    L.lns_tune_cache_store.argtypes = [i32, i32, i32, i32, P(lns_tuning)]
+    L.lns_tune_cache_store.restype = None
+    L.lns_tune_cache_clear.argtypes = []
+    L.lns_tune_cache_clear.restype = None
     L.lns_active_set_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, f64, f64, i32, i32, vp, vp, P(i32), vp]
     L.lns_active_set_noalloc.restype = C.c_int
     _lib = L
@@ -230,6 +248,30 @@ def lns_batch_advance(models, t_span: float, dt_init: Optional[float] = None, dt
     return [_as_dict(outs[i]) for i in range(len(models))], _as_dict(bst)
 
 
+def lns_tune_pick(sizes, t_cluster, t_grid) -> int:
+    """The autotuner's solver rule (host only): largest size up to which the cluster solver won."""
+    a = np.ascontiguousarray(sizes, np.int32)
+    b = np.ascontiguousarray(t_cluster, np.float64)
+    c = np.ascontiguousarray(t_grid, np.float64)
+    return int(load().lns_tune_pick(int(a.shape[0]), a.ctypes.data, b.ctypes.data, c.ctypes.data))
+
+
+def lns_tune_cache(device: int, krylov_fp32: int, precond: int, n_cells: int) -> Optional[Dict]:
+    t = lns_tuning()
+    if load().lns_tune_cache_lookup(int(device), int(krylov_fp32), int(precond), int(n_cells), C.byref(t)):
+        return _as_dict(t)
+    return None
+
+
+def lns_tune_cache_store(device: int, krylov_fp32: int, precond: int, n_cells: int, **kw) -> None:
+    t = lns_tuning(**{k: int(v) for k, v in kw.items()})
+    load().lns_tune_cache_store(int(device), int(krylov_fp32), int(precond), int(n_cells), C.byref(t))
+
+
+def lns_tune_cache_clear() -> None:
+    load().lns_tune_cache_clear()
+
+
 def _check(rc: int, allow=()) -> int:
     if rc != LNS_OK and rc not in allow:
         msg = load().lns_last_error().decode(errors="replace")
@@ -258,6 +300,7 @@ class Options:
     profile: int = 0
     fp64_fallback: int = 1
     krylov_cluster: int = -1
+    autotune: int = 1
 
     def c(self) -> lns_options:
         return lns_options(*[getattr(self, f.name) for f in dataclasses.fields(self)])
@@ -491,6 +534,30 @@ class Model:
 
     def lns_reset_kernel_times(self) -> None:
         _check(load().lns_reset_kernel_times(self.h))
+
+    # ---- autotuning ----
+    def lns_autotune(self) -> Dict:
+        """Measure launch shapes and the cluster/grid solver threshold on this model (lns_autotune)."""
+        t = lns_tuning()
+        _check(load().lns_autotune(self.h, C.byref(t)))
+        return _as_dict(t)
+
+    def lns_get_tuning(self) -> Dict:
+        t = lns_tuning()
+        _check(load().lns_get_tuning(self.h, C.byref(t)))
+        return _as_dict(t)
+
+    def lns_set_tuning(self, tuning: Optional[Dict] = None, **kw) -> None:
+        """Set the tuning (keys of lns_tuning; missing keys keep their current value); None: back to
+        the cached or default tuning."""
+        if tuning is None and not kw:
+            _check(load().lns_set_tuning(self.h, None))
+            return
+        cur = self.lns_get_tuning()
+        cur.update(tuning or {})
+        cur.update(kw)
+        t = lns_tuning(**{k: int(v) for k, v in cur.items()})
+        _check(load().lns_set_tuning(self.h, C.byref(t)))
 
     def lns_debug_fault(self, code: int) -> None:
         """Inject a solver fault for failure tests (1: a barrier wait runs out, 2: breakdown; 0: none)."""

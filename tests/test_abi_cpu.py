@@ -56,7 +56,7 @@ def test_last_error_and_defaults_without_gpu(lib):
 def test_struct_layouts_match_c():
     structs = ["lns_fluid", "lns_model_desc", "lns_options", "lns_allocator", "lns_iter_stats", "lns_step_stats",
                "lns_kernel_time", "lns_server_options", "lns_completion", "lns_server_stats", "lns_dt_control",
-               "lns_advance_stats", "lns_batch_stats"]
+               "lns_advance_stats", "lns_batch_stats", "lns_tuning"]
     src = "#include <stdio.h>\n#include <stddef.h>\n#include \"lns.h\"\nint main(void){\n"
     for s in structs:
         src += f'  printf("{s} %zu\\n", sizeof({s}));\n'

@@ -1,9 +1,10 @@
 """Batched ensembles (lns_batch_advance): independent realizations advanced together, each with its
 own active sets, convergence and time-step controller.
 
-- Every member ends bit for bit as lns_advance leaves it alone (state and statistics: steps, cuts,
-  Newton and Krylov iterations, cell updates), in both Krylov precisions, with members of uneven
-  size whose solves go to both solvers and whose steps are cut independently.
+- Every member ends bit for bit as lns_advance leaves it alone with every system that fits in the
+  cluster solver sent there (state and statistics: steps, cuts, Newton and Krylov iterations, cell
+  updates), in both Krylov precisions, with members of uneven size whose solves go to both solvers
+  and whose steps are cut independently.
 - Small members at a tight tolerance match the oracle's own controller run per member (same
   accepted and cut steps, fields within 1e-7).
 """
@@ -32,6 +33,8 @@ def _batch(cases, opts, **adv):
 
     streams = [torch.cuda.Stream() for _ in cases]
     models = [lns.Model(c, opts, stream=s) for c, s in zip(cases, streams)]
+    for m in models:
+        m.lns_set_tuning(cluster_max_rows=-1)
     outs, bst = lns.lns_batch_advance(models, allow_noconv=True, **adv)
     torch.cuda.synchronize()
     states = [m.lns_get_state() for m in models]
@@ -51,6 +54,7 @@ def test_members_bit_identical_to_solo_advance(fp32):
     keys = ("status", "steps", "cuts", "iterations", "krylov_iters", "cell_updates", "t_done", "dt_next")
     for c, o, (pb, swb) in zip(cases, outs, states):
         g = lns.Model(c, opts)
+        g.lns_set_tuning(cluster_max_rows=-1)  # every system that fits goes to the cluster, as in the batch
         a = g.lns_advance(allow_noconv=True, **adv)
         ps, sws = g.lns_get_state()
         g.close()

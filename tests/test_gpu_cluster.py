@@ -48,6 +48,7 @@ def _check(case, va, fp32, cluster, precond=lns.LNS_PRECOND_BJAC, expect=None, s
     def solve(cl):
         g = lns.Model(case, lns.Options(krylov_fp32=fp32, krylov_rtol=1e-6 if fp32 else 1e-12, krylov_maxit=5000,
                                         krylov_cluster=cl, precond=precond))
+        g.lns_set_tuning(cluster_max_rows=-1)  # every system that fits goes to the cluster solver
         g.lns_set_state(p, sw, pn, swn)
         out = g.lns_solve_local(dt, va)
         g.close()
@@ -145,6 +146,7 @@ def test_whole_case_cluster_equals_oracle_small(fp32):
     ref = O.Sim(case, O.Options(mode=1, **tight))
     g = lns.Model(case, lns.Options(mode=1, krylov_fp32=fp32, krylov_rtol=1e-5 if fp32 else 1e-12,
                                     krylov_maxit=5000, krylov_cluster=16, **tight))
+    g.lns_set_tuning(cluster_max_rows=-1)
     for dt in case.dt_schedule:
         a = g.lns_timestep(dt)
         b = ref.timestep(dt)
