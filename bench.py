@@ -59,12 +59,13 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="run only the headline case (for profiler launch lists)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
-    ap.add_argument("--serve-seconds", type=float, default=15.0,
-                    help="measured window of the serving run (Poisson arrivals); 0 skips it")
-    ap.add_argument("--serve-warmup", type=float, default=4.0, help="serving warm-up before the window (s)")
-    ap.add_argument("--serve-models", type=int, default=32, help="resident models of the serving run")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="each measured window of the serving run (Poisson arrivals); 0 skips it")
+    ap.add_argument("--serve-runs", type=int, default=3, help="measured serving windows (their spread is reported)")
+    ap.add_argument("--serve-warmup", type=float, default=10.0, help="serving warm-up before the windows (s)")
+    ap.add_argument("--serve-models", type=int, default=64, help="resident models of the serving run")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="request arrival rate (1/s)")
-    ap.add_argument("--serve-workers", type=int, default=4, help="requests run at once")
+    ap.add_argument("--serve-workers", type=int, default=8, help="requests run at once")
     ap.add_argument("--ensemble", type=int, default=256,
                     help="realizations in the batched-ensemble run (N ~ U{150..500} grids; 0 skips it)")
     ap.add_argument("--large-3d", type=int, default=1,
@@ -501,32 +502,26 @@ def ensemble_run(args, opts, stream):
     return out
 
 
-def serving_run(args, opts):
-    """Requests 'advance model k by dt' with Poisson arrivals over resident models of log-uniform
-    size; latency = completion - submission on the server clock."""
+def _serve_window(srv, ids, rng, rate, seconds, warmup):
+    """Poisson arrivals of 'advance model k by dt' requests for warmup + seconds; the requests
+    submitted after the warm-up are measured (latency = completion - submission, server clock)."""
     import numpy as np
 
     from paper_2008_01539_gb300 import casegen as cg
-    from paper_2008_01539_gb300 import lns
 
-    rng = np.random.default_rng(4)
-    sizes = np.exp(rng.uniform(np.log(1e4), np.log(1e6), args.serve_models)).astype(int)
-    t0 = time.perf_counter()
-    srv = lns.Server(workers=args.serve_workers, hbm_budget_bytes=150 << 30)
-    ids = [srv.add_model(cg.serving_model(k, int(c)), opts) for k, c in enumerate(sizes)]
-    t_setup = time.perf_counter() - t0
-    total = args.serve_warmup + args.serve_seconds
     start = srv.now()
-    t_next, rid, sub, done = start, 0, {}, []
+    total = warmup + seconds
+    t_next, sub, done = start, 0, []
+    rid0 = _serve_window.rid
     while True:
         now = srv.now()
         while t_next <= now and t_next - start < total:
             mid = int(rng.integers(len(ids)))
             dt = float(np.exp(rng.uniform(np.log(0.1), np.log(30.0)))) * cg.DAY
-            srv.submit(ids[mid], dt, rid)
-            sub[rid] = (t_next - start, ids[mid])
-            rid += 1
-            t_next += float(rng.exponential(1.0 / args.serve_rate))
+            srv.submit(ids[mid], dt, _serve_window.rid)
+            _serve_window.rid += 1
+            sub += 1
+            t_next += float(rng.exponential(1.0 / rate))
         done += srv.poll(512, 0.0)
         if t_next - start >= total:
             break
@@ -537,29 +532,68 @@ def serving_run(args, opts):
         if not got:
             break
         done += got
-    st = srv.stats()
-    srv.close()
-    meas = [c for c in done if c["t_submit"] - start >= args.serve_warmup]
+    done = [c for c in done if c["request_id"] >= rid0]
+    meas = [c for c in done if c["t_submit"] - start >= warmup]
     ok = [c for c in meas if c["status"] == 0]
     lat = np.array([c["t_done"] - c["t_submit"] for c in ok])
     t_first = min(c["t_submit"] for c in meas) if meas else 0.0
     t_last = max(c["t_done"] for c in meas) if meas else 1.0
     upd = sum(c["stats"]["cell_updates"] for c in ok)
+    return {"requests": len(meas), "failed": len(meas) - len(ok),
+            "p50_latency_ms": float(np.percentile(lat, 50)) * 1e3 if len(lat) else None,
+            "p99_latency_ms": float(np.percentile(lat, 99)) * 1e3 if len(lat) else None,
+            "mean_latency_ms": float(lat.mean()) * 1e3 if len(lat) else None,
+            "value": upd / max(t_last - t_first, 1e-9),
+            "timestep_cuts": int(sum(c["stats"]["dd_outer"] for c in ok))}
+
+
+_serve_window.rid = 0
+
+
+def serving_run(args, opts):
+    """Requests 'advance model k by dt' with Poisson arrivals over resident models of log-uniform
+    size, half of them 2D (N x N matrix + DFN) and half 3D (N x N x 10 layers + fracture planes and
+    panels); one warm-up window, then args.serve_runs measured windows on the same server."""
+    import numpy as np
+
+    from paper_2008_01539_gb300 import casegen as cg
+    from paper_2008_01539_gb300 import lns
+
+    rng = np.random.default_rng(4)
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(1e6), args.serve_models)).astype(int)
+    t0 = time.perf_counter()
+    cases = [(cg.serving_model if k % 2 == 0 else cg.serving_model_3d)(k, int(c)) for k, c in enumerate(sizes)]
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    srv = lns.Server(workers=args.serve_workers, hbm_budget_bytes=150 << 30)
+    ids = [srv.add_model(c, opts) for c in cases]
+    t_setup = time.perf_counter() - t0
+    _serve_window(srv, ids, rng, args.serve_rate, 0.0, args.serve_warmup)  # warm-up: models admitted
+    runs = [_serve_window(srv, ids, rng, args.serve_rate, args.serve_seconds, 0.0) for _ in range(args.serve_runs)]
+    st = srv.stats()
+    srv.close()
+
+    def spread(key):
+        v = [r[key] for r in runs if r[key] is not None]
+        return {"median": float(np.median(v)), "min": float(min(v)), "max": float(max(v))} if v else None
+
     return {
-        "workload": f"{len(ids)} resident models (N x N matrix + DFN, {int(sizes.min())}-{int(sizes.max())} cells, "
-                    f"log-uniform), Poisson arrivals at {args.serve_rate:.0f}/s, dt log-uniform 0.1-30 d, model "
-                    f"uniform, {args.serve_workers} workers, HBM budget 150 GB",
-        "window_s": args.serve_seconds, "warmup_s": args.serve_warmup,
-        "requests": len(meas), "failed": len(meas) - len(ok),
-        "failed_by_status": {str(k): sum(1 for c in meas if c["status"] == k) for k in sorted({c["status"] for c in meas})
-                             if k != 0},
-        "p50_latency_ms": float(np.percentile(lat, 50)) * 1e3 if len(lat) else None,
-        "p99_latency_ms": float(np.percentile(lat, 99)) * 1e3 if len(lat) else None,
-        "mean_latency_ms": float(lat.mean()) * 1e3 if len(lat) else None,
-        "value": upd / max(t_last - t_first, 1e-9), "unit": UNIT,
-        "timestep_cuts": int(sum(c["stats"]["dd_outer"] for c in ok)),
+        "workload": f"{len(ids)} resident models ({sum(1 for k in range(len(ids)) if k % 2 == 0)} 2D N x N matrix + "
+                    f"DFN, {sum(1 for k in range(len(ids)) if k % 2)} 3D N x N x 10 + fracture planes and panels; "
+                    f"{int(min(c.n for c in cases))}-{int(max(c.n for c in cases))} cells, log-uniform), Poisson "
+                    f"arrivals at {args.serve_rate:.0f}/s, dt log-uniform 0.1-30 d, model uniform, "
+                    f"{args.serve_workers} workers, HBM budget 150 GB; each request through the time-step "
+                    f"controller (cut down to dt/65536)",
+        "window_s": args.serve_seconds, "windows": len(runs), "warmup_s": args.serve_warmup,
+        "requests": sum(r["requests"] for r in runs), "failed": sum(r["failed"] for r in runs),
+        "p50_latency_ms": spread("p50_latency_ms"), "p99_latency_ms": spread("p99_latency_ms"),
+        "mean_latency_ms": spread("mean_latency_ms"),
+        "value": float(np.median([r["value"] for r in runs])), "unit": UNIT,
+        "per_window": runs,
+        "timestep_cuts": sum(r["timestep_cuts"] for r in runs),
         "resident_models": st["resident_models"], "resident_gb": st["resident_bytes"] / 2 ** 30,
-        "evictions": st["evictions"], "total_cells": int(sizes.sum()), "setup_s": t_setup}
+        "evictions": st["evictions"], "total_cells": int(sum(c.n for c in cases)), "generate_s": t_gen,
+        "setup_s": t_setup}
 
 
 def write_traffic(args):

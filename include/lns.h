@@ -365,7 +365,7 @@ lns_status lns_reset_kernel_times(lns_model* model);
  * framework's pool or a fixed budget, or they run where cudaMalloc (which may synchronize the
  * whole device) would stall other work -- and therefore cannot create a model.
  *
- * Computes exactly what lns_active_set computes (Algorithm 1, lines 8-20), on the caller's arrays:
+ * Computes exactly what lns_active_set computes, on the caller's arrays:
  *   row_ptr [n_cells+1], nbr [row_ptr[n_cells]]: the connection graph as in lns_model_desc;
  *   always_bits: bitset of always-active cells, or NULL for none;
  *   dp, dsw [n_cells]: the update (dsw may be NULL: zero); entries outside V_A are ignored;
@@ -376,11 +376,13 @@ lns_status lns_reset_kernel_times(lns_model* model);
  * The call allocates nothing: its working storage (frontier lists, bitsets, counters; about
  * 8.4 MB for the limit below) is one file-scope __device__ array that every GPU loading the
  * library keeps until the process exits.  Limits: n_cells <= LNS_NOALLOC_MAX_CELLS and
- * m_layers <= LNS_NOALLOC_MAX_LAYERS; larger values return LNS_EINVAL.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the array and each clears
- * what it needs, so calls that overlap on the GPU (two streams or two threads on one device)
- * race: serialize them. */
+ * m_layers <= LNS_NOALLOC_MAX_LAYERS; larger values return LNS_EINVAL.  The call reads its result
+ * flag back and waits for its stream, so it must never be made while a stream is being captured
+ * (it then returns LNS_EINVAL).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of the process, so do
+ * not use this call on a device after resetting it (cudaDeviceReset) in the same process.  All
+ * calls share the array and each clears what it needs, so calls that overlap on the GPU (two
+ * streams or two threads on one device) race: serialize them. */
 #define LNS_NOALLOC_MAX_CELLS (1 << 20)
 #define LNS_NOALLOC_MAX_LAYERS 1024
 lns_status lns_active_set_noalloc(int32_t n_cells, const int32_t* row_ptr, const int32_t* nbr,
@@ -399,15 +401,20 @@ lns_status lns_active_set_noalloc(int32_t n_cells, const int32_t* row_ptr, const
  * are created when first needed and admitted against hbm_budget_bytes (0: no limit) -- when a
  * model does not fit, idle models are evicted least recently used first, their state and support
  * saved to the host and restored exactly on their next request; a model that does not fit even
- * then waits for the running requests, and runs alone if it exceeds the budget by itself.  A timestep that does not
- * converge is retried from its starting state as two half steps (up to 4 levels).  Results are the
- * same as those of lns_timestep on a model alone (the kernels are deterministic).
+ * then waits for the running requests, and runs alone if it exceeds the budget by itself.  A request
+ * runs lns_advance over its interval (first step dt; a step that does not converge is undone and
+ * halved, steps grow back after easy ones, down to dt * dt_min_fraction); a request that fails
+ * even there leaves its model unchanged.  Served models send every system that fits to the cluster
+ * solver (their tuning's cluster_max_rows < 0), so solves of different models run side by side.
+ * Results are the same as those of lns_advance on a model alone with that tuning (the kernels are
+ * deterministic).
  * --------------------------------------------------------------------------------------- */
 typedef struct lns_server lns_server; /* opaque */
 
 typedef struct {
   int32_t workers;           /* requests run at once (1..64) */
   int64_t hbm_budget_bytes;  /* device bytes the resident models may hold; 0: no limit */
+  double dt_min_fraction;    /* a request's steps may be cut down to dt * this; 0: 2^-16 */
 } lns_server_options;
 
 typedef struct {
@@ -416,7 +423,7 @@ typedef struct {
   int32_t status;            /* lns_status of the request */
   double dt;
   double t_submit, t_start, t_done;  /* seconds on the server clock (lns_server_now) */
-  lns_step_stats stats;      /* summed over the half steps of any cut; dd_outer = cuts */
+  lns_step_stats stats;      /* summed over the request's steps (failed ones included); dd_outer = cuts */
 } lns_completion;
 
 typedef struct {

@@ -630,3 +630,19 @@ def small_dfn3d(nx: int = 10, ny: int = 8, nz: int = 3, n_nf: int = 3, seed: int
     return dfn3d_case(nx, ny, nz, dx, dz, n_nf, seed, hf=hf, wells=[(0, (ny - 2) // 2, nz // 2, 1500.0 * PSI)],
                       nf_len=(3 * dx, 6 * dx), nf_layers=(1, nz), dts=doubling_schedule(n_steps),
                       name=f"small3d_{nx}x{ny}x{nz}")
+
+
+def serving_model_3d(index: int, cells: int, dx: float = 5.0, dz: float = 2.0, nz: int = 10) -> Case:
+    """A 3D resident model of about ``cells`` cells for the serving workload, built like the
+    200x200x20 case: an N x N x nz layered matrix (N = round(sqrt(cells / nz))), two hydraulic-
+    fracture stages (vertical planes over the middle layers) with a producer at 1500 psi in each,
+    and N / 2 natural-fracture panels (seed = ``index``)."""
+    nn = max(12, int(round(math.sqrt(cells / nz))))
+    yc = nn * dx / 2
+    half = max(3, nn // 8)
+    k0, k1 = nz // 4, nz - nz // 4
+    hf = [((nn // 2 + o) * dx + dx / 2, yc - half * dx, yc + half * dx, k0, k1, 2 * half) for o in (-3, 3)]
+    wells = [(s, half, (k1 - k0) // 2, 1500.0 * PSI) for s in range(2)]
+    return dfn3d_case(nn, nn, nz, dx, dz, max(4, nn // 2), 30_000 + index, hf=hf, wells=wells,
+                      nf_layers=(2, max(2, nz - 2)), dts=np.array([DAY]), name=f"serve3d{index}_{nn}x{nn}x{nz}")
+

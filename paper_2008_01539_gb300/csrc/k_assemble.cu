@@ -14,10 +14,13 @@
 // (p_scale dp, dSw).  All residual, flux and accumulation arithmetic is FP64; the scaled
 // blocks and right-hand side are stored in T (FP64, or FP32 for the inexact-Newton path).
 //
-// Mapping: one thread per active row (each cell's properties evaluated once per use, no
-// redundant FP64 work: FP64 issues at a small fraction of the FP32 rate on this GPU).  The
-// boundary set V_B of the solved set (rows with an inactive neighbour) falls out of the
-// column scan and is written here too.
+// Mapping: a pass over the active rows evaluates each row's phase properties once (k_cell_props,
+// two lanes per row); the assembly then takes a lane pair per active row, one lane per phase, and
+// reads the properties of the row and of its active neighbours from that pass -- only an inactive
+// neighbour (a Dirichlet value) is evaluated in place.  FP64 issues at a small fraction of the FP32
+// rate on this GPU, so the FP64 instruction chain of a row is what bounds the kernel.  The boundary
+// set V_B of the solved set (rows with an inactive neighbour) falls out of the column scan and is
+// written here too.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,6 +86,36 @@ __device__ __forceinline__ PhaseProps phase_props(const FluidK& F, double p, dou
   return q;
 }
 
+// Phase properties of every active row, once per iteration: lane pair per row, lane l = phase l.
+// The assembly reads them for the row itself and for each active neighbour, instead of evaluating
+// them again per connection (a cell's properties would otherwise be computed 1 + degree times).
+__global__ void __launch_bounds__(128) k_cell_props(Dev d, FluidK F) {
+  const int nA = d.ctr->n_active;
+  const int l = threadIdx.x & 1;
+  const int pairs = (gridDim.x * blockDim.x) >> 1;
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 1; k < nA; k += pairs) {
+    const int i = d.act[k];
+    const PhaseProps q = phase_props(F, d.p[i], d.sw[i], l);
+    double4* o = (double4*)(d.cprops + 16 * (size_t)k + 8 * l);
+    o[0] = make_double4(q.b, q.rho, q.mob, q.db);
+    o[1] = make_double4(q.drho, q.dmob_dp, q.dmob_ds, 0.0);
+  }
+}
+
+__device__ __forceinline__ PhaseProps load_props(const double* cprops, int k, int l) {
+  const double4* o = (const double4*)(cprops + 16 * (size_t)k + 8 * l);
+  const double4 a = o[0], b = o[1];
+  PhaseProps q;
+  q.b = a.x;
+  q.rho = a.y;
+  q.mob = a.z;
+  q.db = a.w;
+  q.drho = b.x;
+  q.dmob_dp = b.y;
+  q.dmob_ds = b.z;
+  return q;
+}
+
 // Two lanes per active row, one per phase (l = lane parity: 0 oil, 1 water): each lane evaluates
 // its phase's accumulation, fluxes and well terms (FP64), the pair
 // exchanges its residual and diagonal rows, and both lanes form D^{-1}.  Pass 1 writes each
@@ -109,7 +142,7 @@ __global__ void __launch_bounds__(BLK) k_assemble(Dev d, FluidK F, double p_scal
     const int i = d.act[k];
     const int e0 = d.row_ptr[i], e1 = d.row_ptr[i + 1];
     const double p_i = d.p[i], sw_i = d.sw[i], z_i = d.depth[i], pvr = d.pv_ref[i];
-    const PhaseProps qi = phase_props(F, p_i, sw_i, l);
+    const PhaseProps qi = load_props(d.cprops, k, l);
     const double pv = pvr * (1.0 + f.c_r * (p_i - f.p_ref)), dpv = pvr * f.c_r;
     double R, Dp, Ds;  // residual of phase l and row l of the diagonal block (d/dp_i, d/dSw_i)
     {  // accumulation
@@ -126,46 +159,75 @@ __global__ void __launch_bounds__(BLK) k_assemble(Dev d, FluidK F, double p_scal
     // cell is active too (it is then the previous / next compact row)
     const int lid_i = lines ? d.line_id[i] : -1;
     int eprev = -1, enext = -1;
-    for (int e = e0; e < e1; e++) {
-      const int j = d.nbr[e];
-      const double T_e = d.trans[e];
-      const double p_j = d.p[j];
-      const PhaseProps qj = phase_props(F, p_j, d.sw[j], l);
-      const double dz = z_i - d.depth[j];
-      const double rho_avg = 0.5 * (qi.rho + qj.rho);
-      const double dphi = (p_i - p_j) - (g * rho_avg) * dz;
-      const bool up_i = dphi > 0.0 || (dphi == 0.0 && i < j);
-      const double tm = T_e * (up_i ? qi.mob : qj.mob);
-      R += tm * dphi;
-      const double hgdz = g * dz * 0.5;
-      double o0 = tm * (-1.0 - hgdz * qj.drho), o1 = 0.0;
-      const double dl0 = tm * (1.0 - hgdz * qi.drho);
-      double dl0u = 0.0, dl1 = 0.0;
-      if (up_i) {
-        dl0u = T_e * qi.dmob_dp * dphi;
-        dl1 = T_e * qi.dmob_ds * dphi;
-      } else {
-        o0 += T_e * qj.dmob_dp * dphi;
-        o1 = T_e * qj.dmob_ds * dphi;
+    // connections in batches of kNb: every load of a batch (neighbour, its state, its set bit and
+    // compact row, then its properties) is issued before any is used, so a batch costs about two
+    // dependent L2 round trips instead of two per connection; the flux sums run in CSR order
+    constexpr int kNb = 8;
+    for (int eb = e0; eb < e1; eb += kNb) {
+      int jj[kNb], kj[kNb];
+      double T_e[kNb], p_j[kNb], z_j[kNb], sw_j[kNb];
+      bool in[kNb];
+#pragma unroll
+      for (int q = 0; q < kNb; q++) {
+        jj[q] = eb + q < e1 ? d.nbr[eb + q] : i;
+        T_e[q] = eb + q < e1 ? d.trans[eb + q] : 0.0;
       }
-      Dp += dl0 + dl0u;
-      Ds += dl1;
-      const bool in = bit(d.va, j);
-      edge |= !in;
-      if (l == 0) d.colA[e] = in ? d.inv[j] : -1;
-      if (lid_i >= 0 && in && (j == i - 1 || j == i + 1) && d.line_id[j] == lid_i) {
-        if (j < i)
-          eprev = e;
-        else
-          enext = e;
+#pragma unroll
+      for (int q = 0; q < kNb; q++) {
+        p_j[q] = d.p[jj[q]];
+        z_j[q] = d.depth[jj[q]];
+        sw_j[q] = d.sw[jj[q]];
+        in[q] = bit(d.va, jj[q]);
       }
-      if (debug) {
-        d.dbg_off[4 * (size_t)e + 2 * l] = o0;
-        d.dbg_off[4 * (size_t)e + 2 * l + 1] = o1;
-      }
-      if (in) {  // raw row in FP64 until it is scaled
-        raw[4 * (size_t)e + 2 * l] = o0;
-        raw[4 * (size_t)e + 2 * l + 1] = o1;
+#pragma unroll
+      for (int q = 0; q < kNb; q++) kj[q] = in[q] ? d.inv[jj[q]] : -1;
+      PhaseProps qn[kNb];
+#pragma unroll
+      for (int q = 0; q < kNb; q++)
+        if (in[q]) qn[q] = load_props(d.cprops, kj[q], l);
+#pragma unroll
+      for (int q = 0; q < kNb; q++) {
+        const int e = eb + q;
+        if (e >= e1) break;
+        const int j = jj[q];
+        // an active neighbour's properties were computed once this iteration; an inactive one
+        // (frozen at its current state, a Dirichlet value) is evaluated here
+        const PhaseProps qj = in[q] ? qn[q] : phase_props(F, p_j[q], sw_j[q], l);
+        const double dz = z_i - z_j[q];
+        const double rho_avg = 0.5 * (qi.rho + qj.rho);
+        const double dphi = (p_i - p_j[q]) - (g * rho_avg) * dz;
+        const bool up_i = dphi > 0.0 || (dphi == 0.0 && i < j);
+        const double tm = T_e[q] * (up_i ? qi.mob : qj.mob);
+        R += tm * dphi;
+        const double hgdz = g * dz * 0.5;
+        double o0 = tm * (-1.0 - hgdz * qj.drho), o1 = 0.0;
+        const double dl0 = tm * (1.0 - hgdz * qi.drho);
+        double dl0u = 0.0, dl1 = 0.0;
+        if (up_i) {
+          dl0u = T_e[q] * qi.dmob_dp * dphi;
+          dl1 = T_e[q] * qi.dmob_ds * dphi;
+        } else {
+          o0 += T_e[q] * qj.dmob_dp * dphi;
+          o1 = T_e[q] * qj.dmob_ds * dphi;
+        }
+        Dp += dl0 + dl0u;
+        Ds += dl1;
+        edge |= !in[q];
+        if (l == 0) d.colA[e] = kj[q];
+        if (lid_i >= 0 && in[q] && (j == i - 1 || j == i + 1) && d.line_id[j] == lid_i) {
+          if (j < i)
+            eprev = e;
+          else
+            enext = e;
+        }
+        if (debug) {
+          d.dbg_off[4 * (size_t)e + 2 * l] = o0;
+          d.dbg_off[4 * (size_t)e + 2 * l + 1] = o1;
+        }
+        if (in[q]) {  // raw row in FP64 until it is scaled
+          raw[4 * (size_t)e + 2 * l] = o0;
+          raw[4 * (size_t)e + 2 * l + 1] = o1;
+        }
       }
     }
     if (edge && l == 0) atomicOr(&d.vb[i >> 5], 1u << (i & 31));
@@ -463,7 +525,8 @@ cudaError_t launch_assemble(const Dev& d, double p_scale, int fp32, int lines, i
   // launch shape (results do not depend on it: every row is computed by its own lane pair)
   const int blk = c.asm_block == 128 || c.asm_block == 256 ? c.asm_block : kAsmBlk;
   const int grid = (c.asm_mult >= 1 && c.asm_mult <= 16 ? c.asm_mult : 4) * c.sms;
-  count_launches(1);
+  count_launches(2);
+  k_cell_props<<<grid / 2 > 0 ? grid / 2 : 1, 128, 0, c.stream>>>(d, F);
   const double ips = 1.0 / p_scale;
   if (fp32) {
     if (blk == 256)

@@ -1130,6 +1130,7 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
   AL(d.tmp2, W);
   AL(d.act, N);
   AL(d.inv, N);
+  AL(d.cprops, N * 16);
   AL(d.fr0, N);
   AL(d.fr1, N);
   AL(d.blk_sums, (W + 255) / 256 + 1);

@@ -6,7 +6,8 @@
 //   state        : p, sw (iterate u^nu), pn, swn (time level u^n), p0, sw0 (initial), f64[n]
 //   sets         : va, vb, supp, reach, step union, previous-step support  (bitsets[W])
 //   compaction   : act[n] ascending active cells, inv[n] cell -> compact row (valid where
-//                  va is set), frontier lists fr0/fr1[n]
+//                  va is set), frontier lists fr0/fr1[n]; cprops[n][2][8] phase properties of
+//                  the active rows (f64)
 //   system       : blocks[E2] 2x2 off-diagonal blocks stored at the CSR entry of their
 //                  row (f64 or f32), colA[E2] compact column or -1, rhs[2n]; the diagonal
 //                  blocks are scaled to the identity and not stored
@@ -75,6 +76,10 @@ struct Dev {
   uint32_t *va, *vb, *supp, *reach, *uni, *prev, *tmp0, *tmp1, *tmp2;
   // compaction
   int *act, *inv, *fr0, *fr1, *blk_sums;
+  // per compact row and phase, FP64 properties of the current iterate (8 doubles: b, rho,
+  // lambda b, db/dp, drho/dp, d(lambda b)/dp, d(lambda b)/dSw, unused), written once per iteration
+  // before the assembly reads them for the row itself and for its active neighbours
+  double* cprops;
   // system
   void* blocks;  // E2 * 4 * sizeof(T)
   double* raw;   // E2 * 4: unscaled FP64 blocks (FP32 path only; the FP64 path scales in place)

@@ -189,10 +189,17 @@ extern "C" lns_status lns_active_set_noalloc(int32_t n_cells, const int32_t* row
   }
   if (!row_ptr || !nbr || !dp || !va_bits || !vb_bits)
     return fail(LNS_EINVAL, "row_ptr, nbr, dp, va_bits and vb_bits must be device pointers (non-NULL)");
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  {  // the call waits for its stream, which a stream capture forbids
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(stream, &cap);
+    if (ce != cudaSuccess) return fail(LNS_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(LNS_EINVAL, "lns_active_set_noalloc waits for its stream and cannot be called during a capture");
+  }
   Scratch s;
   lns_status st = scratch_for_current_device(&s);
   if (st != LNS_OK) return st;
-  cudaStream_t stream = (cudaStream_t)cuda_stream;
   const int W = (n_cells + 31) / 32;
   const int grid = (W + kBlk - 1) / kBlk;
   cudaError_t e = cudaMemsetAsync(s.ctr, 0, sizeof(int) * kCtrInts, stream);

@@ -13,9 +13,11 @@
 // idle resident models are evicted, least recently used first, after saving their state and
 // support set to the host (restored exactly when the model comes back).
 //
-// A timestep that fails to converge (LNS_ENOCONV, LNS_EKRYLOV) is retried from the saved state
-// as two half steps, up to kMaxSplits levels: a simple time-step cut.  A request that fails at
-// every level leaves its model as it was.
+// A request runs lns_advance over its interval: a step that fails to converge (LNS_ENOCONV,
+// LNS_EKRYLOV) is undone and retried with half the step, and steps grow back after easy ones, down
+// to a smallest step of dt * dt_min_fraction.  A request that fails even there leaves its model as
+// it was.  The models' solves that fit the thread-block-cluster solver (up to 16 SMs) run side by
+// side on the workers' streams; larger ones take the grid solver over every SM, one at a time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +36,7 @@
 
 namespace {
 
-constexpr int kMaxSplits = 4;
+constexpr double kDefaultMinFraction = 1.0 / 65536.0;
 
 struct Counting {  // allocator context of one model: bytes it holds on the device
   size_t bytes = 0;
@@ -70,9 +72,9 @@ struct ServedModel {
   bool saved = false, saved_support = false;
   std::vector<double> p_saved, sw_saved;
   std::vector<uint32_t> supp_saved;
-  // checkpoints of the time-step cut, one per cut level (device [2n]: p, sw; host support bits)
-  double* ck[kMaxSplits + 1] = {};
-  std::vector<uint32_t> ck_supp[kMaxSplits + 1];
+  // checkpoint of the request's starting state (device [2n]: p, sw; host support bits)
+  double* ck = nullptr;
+  std::vector<uint32_t> ck_supp;
 };
 
 struct Request {
@@ -101,6 +103,7 @@ struct lns_server {
   size_t resident_bytes = 0;
   lns_server_stats st{};
   int device = 0;
+  double min_fraction = kDefaultMinFraction;
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -132,11 +135,10 @@ lns_status evict(lns_server* s, ServedModel& sm, cudaStream_t stream) {
   if (r != LNS_OK) return r;
   sm.saved = true;
   sm.saved_support = sm.has_support;
-  for (auto& c : sm.ck)
-    if (c) {
-      cudaFreeAsync(c, stream);
-      c = nullptr;
-    }
+  if (sm.ck) {
+    cudaFreeAsync(sm.ck, stream);
+    sm.ck = nullptr;
+  }
   lns_model_destroy(sm.m);
   cudaStreamSynchronize(stream);
   sm.m = nullptr;
@@ -166,6 +168,14 @@ lns_status admit(ServedModel& sm, cudaStream_t stream) {
   lns_allocator a{sm.counting.get(), counting_alloc, counting_free};
   lns_status r = lns_model_create(&sm.desc, &sm.opts, &a, stream, &sm.m);
   if (r != LNS_OK) return r;
+  {  // solves of different models run side by side when they fit the cluster solver; the launch
+     // shapes are the model class's cached ones, if measured
+    lns_tuning t{};
+    lns_get_tuning(sm.m, &t);
+    t.cluster_max_rows = -1;
+    r = lns_set_tuning(sm.m, &t);
+    if (r != LNS_OK) return r;
+  }
   if (sm.saved) {
     r = lns_set_state(sm.m, sm.p_saved.data(), sm.sw_saved.data(), nullptr, nullptr);
     if (r == LNS_OK && sm.saved_support) r = lns_set_support(sm.m, sm.supp_saved.data());
@@ -175,48 +185,32 @@ lns_status admit(ServedModel& sm, cudaStream_t stream) {
   return LNS_OK;
 }
 
-// One timestep with the time-step cut: on a convergence failure, restore the state saved before
-// the step and advance by two halves instead (each half may be cut again, kMaxSplits levels in
-// all).  A step that fails at every level leaves the model as it was before the step.
-lns_status advance(ServedModel& sm, double dt, int depth, lns_step_stats* acc, cudaStream_t stream) {
+// One request: lns_advance over dt with the cut/grow controller (first step dt, smallest
+// dt * min_fraction).  A request that fails leaves the model as it was before it.
+lns_status advance(ServedModel& sm, double dt, double min_fraction, lns_step_stats* acc, cudaStream_t stream) {
   const int n = sm.desc.n_cells;
-  double*& ck = sm.ck[depth];
-  std::vector<uint32_t>& ck_supp = sm.ck_supp[depth];
-  if (!ck && cudaMallocAsync((void**)&ck, sizeof(double) * 2 * (size_t)std::max(n, 1), stream) != cudaSuccess) {
-    ck = nullptr;
+  if (!sm.ck && cudaMallocAsync((void**)&sm.ck, sizeof(double) * 2 * (size_t)std::max(n, 1), stream) != cudaSuccess) {
+    sm.ck = nullptr;
     return fail(LNS_ENOMEM, "checkpoint allocation failed");
   }
-  ck_supp.resize((n + 31) / 32);
-  lns_status r = lns_get_state_device(sm.m, ck, ck + n);
-  if (r == LNS_OK) r = lns_get_support(sm.m, ck_supp.data());
+  sm.ck_supp.resize((n + 31) / 32);
+  lns_status r = lns_get_state_device(sm.m, sm.ck, sm.ck + n);
+  if (r == LNS_OK) r = lns_get_support(sm.m, sm.ck_supp.data());
   if (r != LNS_OK) return r;
   const bool had_support = sm.has_support;
-  auto restore = [&]() -> lns_status {
-    lns_status q = lns_set_state_device(sm.m, ck, ck + n);
-    if (q == LNS_OK) q = lns_set_support(sm.m, had_support ? ck_supp.data() : nullptr);
-    sm.has_support = had_support;
-    return q;
-  };
-  lns_step_stats st{};
-  r = lns_timestep(sm.m, dt, &st);
-  sm.has_support = true;
-  acc->iterations += st.iterations;
-  acc->krylov_iters += st.krylov_iters;
-  acc->fp64_retries += st.fp64_retries;
-  acc->cell_updates += st.cell_updates;
-  acc->last_max_dp = st.last_max_dp;
-  acc->last_cnv = st.last_cnv;
-  if (r != LNS_ENOCONV && r != LNS_EKRYLOV) return r;
-  lns_status q = restore();
-  if (q != LNS_OK || depth >= kMaxSplits) return q != LNS_OK ? q : r;
-  acc->dd_outer += 1;  // counts the cuts
-  r = advance(sm, 0.5 * dt, depth + 1, acc, stream);
-  if (r == LNS_OK) r = advance(sm, 0.5 * dt, depth + 1, acc, stream);
-  if (r != LNS_OK) {
-    q = restore();
-    if (q != LNS_OK) return q;
-  }
-  return r;
+  const lns_dt_control ctl{dt, dt * min_fraction, dt, 2.0, 0.5, 4};
+  lns_advance_stats a{};
+  r = lns_advance(sm.m, dt, &ctl, &a);
+  if (a.steps > 0) sm.has_support = true;
+  acc->iterations += a.iterations;
+  acc->krylov_iters += (int32_t)a.krylov_iters;
+  acc->cell_updates += a.cell_updates;
+  acc->dd_outer += a.cuts;  // counts the cuts
+  if (r == LNS_OK) return r;
+  lns_status q = lns_set_state_device(sm.m, sm.ck, sm.ck + n);
+  if (q == LNS_OK) q = lns_set_support(sm.m, had_support ? sm.ck_supp.data() : nullptr);
+  sm.has_support = had_support;
+  return q != LNS_OK ? q : r;
 }
 
 void worker_loop(lns_server* s, cudaStream_t stream) {
@@ -264,7 +258,7 @@ void worker_loop(lns_server* s, cudaStream_t stream) {
     } else {
       r = lns_set_stream(sm.m, stream);
     }
-    if (r == LNS_OK) r = advance(sm, rq.dt, 0, &acc, stream);
+    if (r == LNS_OK) r = advance(sm, rq.dt, s->min_fraction, &acc, stream);
     acc.status = r;
     const double t_done = s->now();
 
@@ -319,8 +313,10 @@ lns_status lns_server_create(const lns_server_options* o, lns_server** out) {
   if (!o || !out) return fail(LNS_EINVAL, "options and out must be non-NULL");
   if (o->workers < 1 || o->workers > 64) return fail(LNS_EINVAL, "workers must be in [1, 64]");
   if (o->hbm_budget_bytes < 0) return fail(LNS_EINVAL, "hbm_budget_bytes must be >= 0");
+  if (o->dt_min_fraction < 0.0 || o->dt_min_fraction >= 1.0) return fail(LNS_EINVAL, "dt_min_fraction must be in [0, 1)");
   lns_server* s = new lns_server();
   s->o = *o;
+  if (o->dt_min_fraction > 0.0) s->min_fraction = o->dt_min_fraction;
   s->t0 = std::chrono::steady_clock::now();
   cudaGetDevice(&s->device);
   for (int w = 0; w < o->workers; w++) {
@@ -349,11 +345,10 @@ lns_status lns_server_destroy(lns_server* s) {
   // models are freed on the stream of their last request (still alive), then the streams go
   for (auto& p : s->models) {
     if (!p->m) continue;
-    for (auto& c : p->ck)
-      if (c) {
-        cudaFreeAsync(c, s->streams[0]);
-        c = nullptr;
-      }
+    if (p->ck) {
+      cudaFreeAsync(p->ck, s->streams[0]);
+      p->ck = nullptr;
+    }
     lns_set_stream(p->m, s->streams[0]);
     lns_model_destroy(p->m);
     p->m = nullptr;

@@ -97,7 +97,7 @@ class lns_tuning(C.Structure):
 
 
 class lns_server_options(C.Structure):
-    _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+    _fields_ = [("workers", C.c_int32), ("hbm_budget_bytes", C.c_int64), ("dt_min_fraction", C.c_double)]
 
 
 class lns_completion(C.Structure):
@@ -569,13 +569,13 @@ class Server:
     requests from any thread; poll for completions with their timestamps (seconds on the
     server clock) and step statistics."""
 
-    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0):
+    def __init__(self, workers: int = 4, hbm_budget_bytes: int = 0, dt_min_fraction: float = 0.0):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("liblns needs a CUDA GPU")
         h = C.c_void_p()
-        o = lns_server_options(int(workers), int(hbm_budget_bytes))
+        o = lns_server_options(int(workers), int(hbm_budget_bytes), float(dt_min_fraction))
         _check(load().lns_server_create(C.byref(o), C.byref(h)))
         self.h = h
         self.n = []

@@ -133,12 +133,14 @@ def test_cancelled_request_leaves_its_model_unchanged():
     srv.drain()
     done = {c["request_id"]: c for c in srv.poll(16, 1.0)}
     assert set(done) == {0, 1, 2}
+    ref = lns.Model(cases[1], opts)
+    ref.lns_set_tuning(cluster_max_rows=-1)  # as served models: every system that fits in the cluster
     if cancelled:
         assert done[1]["status"] == lns.LNS_ESTATE
-        ref = _run(cases[1], opts, [2.0 * cg.DAY])
+        _run(cases[1], opts, [2.0 * cg.DAY], ref)
     else:  # the worker had already taken it
         assert done[1]["status"] == 0
-        ref = _run(cases[1], opts, [1.0 * cg.DAY, 2.0 * cg.DAY])
+        _run(cases[1], opts, [1.0 * cg.DAY, 2.0 * cg.DAY], ref)
     assert np.array_equal(srv.get_state(ids[1])[0], ref.lns_get_state()[0])
     assert not srv.cancel(0)  # finished requests cannot be cancelled
     srv.close()
