@@ -249,7 +249,10 @@ lns_status ev_flush(lns_model* m) {
 
 // Algorithmic traffic models (bytes and flops per launch) from the row count; sT = 8 or 4.
 double bytes_assemble(double nA, double deg, double sT) { return nA * (52.0 + 2 * sT + deg * (20.0 + 4 * sT)); }
-double flops_assemble(double nA, double deg) { return nA * (90.0 + deg * 60.0); }
+// FP64 instructions (per thread) of the assembly and its property pass per active row: the count
+// ncu reports on the 400x400 DFN case (291 per row at mean degree 4.0), split as 2 lanes x
+// (70 + 19 per connection)
+double flops_assemble(double nA, double deg) { return nA * 2.0 * (70.0 + 19.0 * deg); }
 double bytes_krylov_iter(double nA, double deg, double sT) {
   return nA * (2.0 * (12.0 + deg * (4.0 + 6.0 * sT) + 2.0 * sT) + 34.0 * sT);
 }
