@@ -62,7 +62,8 @@ class _Model(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("eps_p", C.c_double), ("eps_sw", C.c_double),
                 ("m_layers", C.c_int32), ("tol_dp", C.c_double), ("tol_cnv", C.c_double),
-                ("max_newton", C.c_int32), ("sat_chop", C.c_double), ("max_dd_outer", C.c_int32)]
+                ("max_newton", C.c_int32), ("sat_chop", C.c_double), ("max_dd_outer", C.c_int32),
+                ("dd_local_newton", C.c_int32), ("dd_local_shrink", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -150,7 +151,9 @@ def source_text() -> str:
 class Options:
     """Solver options.  mode: 0 standard Newton, 1 Algorithm 1, 2 Algorithm 2, 3 residual-based
     active sets (unconverged cells inflated by m_layers; the Lu-Beckner estimate the paper cites).
-    Cutoffs and tolerances in SI (Pa); eps_p = 0.3 psi as in the paper's runs."""
+    Cutoffs and tolerances in SI (Pa); eps_p = 0.3 psi as in the paper's runs.  Algorithm 2
+    variants: dd_local_newton steps per subdomain visit (to local convergence), dd_local_shrink
+    (later steps of a visit solve only the previous step's support within the subdomain)."""
     mode: int = 1
     eps_p: float = 0.3 * 6894.757293168
     eps_sw: float = 0.0
@@ -160,10 +163,13 @@ class Options:
     max_newton: int = 25
     sat_chop: float = 0.2
     max_dd_outer: int = 25
+    dd_local_newton: int = 1
+    dd_local_shrink: int = 0
 
     def _c(self) -> _Opts:
         return _Opts(self.mode, self.eps_p, self.eps_sw, self.m_layers, self.tol_dp, self.tol_cnv,
-                     self.max_newton, self.sat_chop, self.max_dd_outer)
+                     self.max_newton, self.sat_chop, self.max_dd_outer, self.dd_local_newton,
+                     self.dd_local_shrink)
 
 
 def _ptr(a: np.ndarray) -> int:

@@ -779,6 +779,45 @@ static int32_t count_set(int32_t n, const uint8_t* s) {
   return c;
 }
 
+/* Algorithm 2, a subdomain visit beyond its first local solve (the variants the paper names after
+ * Algorithm 2 and in Section 6: solving a subproblem further, and exploiting the solution's locality
+ * inside a subdomain).  The visit's first step has been taken on V_A^k (converged: its convergence
+ * test).  Further steps, up to dd_local_newton in all, stop once a step converges; each solves
+ * V_A^k, or with dd_local_shrink only the support of the previous step's update within V_A^k plus
+ * the subdomain's always-active cells (none left: the visit ends).  Every step stamps its
+ * non-negligible updates with the visit's solve id and can set own_big.  Returns 0, -1 (singular
+ * local system) or -4 (iteration limit). */
+static int dd_refine(const orc_model* m, const orc_opts* o, double* p, double* sw, const double* pn,
+                     const double* swn, double dt, const uint8_t* vak, int converged, int32_t solve_id,
+                     int32_t* big_stamp, int32_t* own_big, double* dp, double* dsw, uint8_t* set, int32_t* it,
+                     int32_t it_cap, orc_step_stats* st, int32_t* trace, int32_t trace_cap, uint8_t* union_out,
+                     double* cnv_max, double* dp_max) {
+  int32_t n = m->n;
+  for (int32_t j = 2; j <= o->dd_local_newton && !converged; j++) {
+    if (o->dd_local_shrink) {
+      for (int32_t i = 0; i < n; i++) set[i] = (uint8_t)(vak[i] && (is_big(o, dp[i], dsw[i]) || m->always[i]));
+    } else {
+      memcpy(set, vak, n);
+    }
+    int32_t na = count_set(n, set);
+    if (na == 0) break;
+    if (*it >= it_cap) return -4;
+    if (orc_local_solve(m, o, p, sw, pn, swn, dt, set, dp, dsw, cnv_max, dp_max) != 0) return -1;
+    apply_update(n, set, p, sw, dp, dsw);
+    or_into(n, union_out, set);
+    for (int32_t i = 0; i < n; i++)
+      if (set[i] && is_big(o, dp[i], dsw[i])) {
+        *own_big = 1;
+        big_stamp[i] = solve_id;
+      }
+    if (trace && *it < trace_cap) trace[*it] = na;
+    st->cell_updates += na;
+    (*it)++;
+    converged = *dp_max < o->tol_dp && *cnv_max < o->tol_cnv;
+  }
+  return 0;
+}
+
 int orc_timestep(const orc_model* m, const orc_opts* o, double* p, double* sw, uint8_t* prev_supp,
                  int32_t* has_prev, double dt, orc_step_stats* st, int32_t* trace, int32_t trace_cap,
                  uint8_t* union_out) {
@@ -891,6 +930,7 @@ int orc_timestep(const orc_model* m, const orc_opts* o, double* p, double* sw, u
     int32_t* own_big = (int32_t*)calloc(cap + 1, sizeof(int32_t));
     int32_t* big_stamp = (int32_t*)calloc(nn, sizeof(int32_t)); /* solve id of the last non-negligible update */
     uint8_t* vt = (uint8_t*)malloc(nn);
+    uint8_t* scratch = (uint8_t*)malloc(nn); /* the solved set of a visit's further steps */
     int32_t solve_id = 0;
     VA[0] = (uint8_t*)malloc(nn);
     VB[0] = (uint8_t*)malloc(nn);
@@ -927,8 +967,17 @@ int orc_timestep(const orc_model* m, const orc_opts* o, double* p, double* sw, u
       VA[k + 1] = (uint8_t*)malloc(nn);
       VB[k + 1] = (uint8_t*)malloc(nn);
       VD[k + 1] = (uint8_t*)malloc(nn);
+      const int conv1 = dp_max < o->tol_dp && cnv_max < o->tol_cnv;
       orc_dd_expand(m, o, VB[k], dp, dsw, vt, VA[k + 1], VB[k + 1], VD[k + 1], &is_expand);
+      /* the visit's further steps (variants; none with dd_local_newton = 1) */
+      int rc = dd_refine(m, o, p, sw, pn, swn, dt, VA[k], conv1, solve_id, big_stamp, &own_big[k], dp, dsw, scratch,
+                         &it, o->max_newton * (o->max_dd_outer + 1), st, trace, trace_cap, union_out, &cnv_max,
+                         &dp_max);
       k++;
+      if (rc != 0) {
+        status = rc;
+        break;
+      }
     }
     int32_t N = k;
     st->n_subdomains = N;
@@ -971,7 +1020,12 @@ int orc_timestep(const orc_model* m, const orc_opts* o, double* p, double* sw, u
         if (trace && it < trace_cap) trace[it] = na;
         st->cell_updates += na;
         it++;
-        if (!(dp_max < o->tol_dp && cnv_max < o->tol_cnv)) all_ok = 0;
+        const int conv1 = dp_max < o->tol_dp && cnv_max < o->tol_cnv;
+        if (!conv1) all_ok = 0; /* the pass converges when every visited subdomain was already converged */
+        int rc = dd_refine(m, o, p, sw, pn, swn, dt, VA[s], conv1, solve_id, big_stamp, &own_big[s], dp, dsw,
+                           scratch, &it, o->max_newton * (o->max_dd_outer + 1), st, trace, trace_cap, union_out,
+                           &cnv_max, &dp_max);
+        if (rc != 0) status = rc;
       }
       nu++;
       converged = all_ok;
@@ -989,6 +1043,7 @@ int orc_timestep(const orc_model* m, const orc_opts* o, double* p, double* sw, u
     free(own_big);
     free(big_stamp);
     free(vt);
+    free(scratch);
   }
   /* support of the timestep's update: the next step's initial active set (Section 5.2) */
   for (int32_t i = 0; i < n; i++) prev_supp[i] = (uint8_t)is_big(o, p[i] - pn[i], sw[i] - swn[i]);

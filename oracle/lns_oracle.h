@@ -70,6 +70,12 @@ typedef struct {
   int32_t max_newton;
   double sat_chop;     /* |dSw| limit per update (<= 0: none) */
   int32_t max_dd_outer;
+  /* Algorithm 2 variants (the paper's Section 4.4 closing remarks and Section 6): a subdomain
+   * visit takes up to dd_local_newton Newton steps on its subdomain, stopping at local convergence
+   * (1: the plain one-step visit); with dd_local_shrink, each step after the first solves only the
+   * support of the previous step's update within the subdomain, plus its always-active cells. */
+  int32_t dd_local_newton;
+  int32_t dd_local_shrink;
 } orc_opts;
 
 typedef struct {
