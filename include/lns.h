@@ -129,6 +129,15 @@ typedef struct {
   int32_t autotune;       /* 1: the first timestep of a model whose size class has no cached tuning
                            * runs lns_autotune first (a one-time cost per device, precision,
                            * preconditioner and size class); 0: the cache or the defaults.  Default 1. */
+  /* Algorithm 2 variants (Section 4.4 after Algorithm 2, and Section 6: solving a subproblem
+   * further, exploiting the solution's locality inside a subdomain).  A subdomain visit takes up to
+   * dd_local_newton Newton steps on its subdomain (>= 1; default 1, the plain visit), stopping at the
+   * first step that passes the convergence test; the outer pass converges when every subdomain it
+   * visited passed the test at its first step.  With dd_local_shrink = 1 each step of a visit after
+   * the first solves only the support of the previous step's update within the subdomain plus the
+   * subdomain's always-active cells (an empty set ends the visit).  Default 0. */
+  int32_t dd_local_newton;
+  int32_t dd_local_shrink;
 } lns_options;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a

@@ -99,6 +99,7 @@ struct lns_model {
   // Algorithm 2 storage: per subdomain V_A^k, V_B^k, V_dB^k bitsets
   std::vector<uint32_t*> dd_va, dd_vb, dd_vdb;
   uint32_t* dd_vt = nullptr;
+  uint32_t* dd_set = nullptr;  // the solved set of a visit's further steps (Algorithm 2 variants)
   std::vector<uint32_t> stage;  // host staging of caller bitsets
   // dt of the current solve, in device memory (d.stepp) via a pinned staging pair
   double* dt_host = nullptr;
@@ -758,11 +759,41 @@ lns_status dd_expand_sets(lns_model* m, uint32_t* vt, uint32_t* va_next, uint32_
   return LNS_OK;
 }
 
+// Algorithm 2 variants: a subdomain visit's steps after its first (up to dd_local_newton in all),
+// stopping at the first that converges; with dd_local_shrink, each solves the support of the
+// previous step's update within the subdomain plus its always-active cells (empty: the visit ends).
+// Every step stamps with the visit's solve id and can set own_big.
+lns_status dd_refine(lns_model* m, uint32_t* va_k, int conv, int solve_id, int* own_big) {
+  Dev& d = m->d;
+  LaunchCfg c = cfg(m);
+  for (int j = 2; j <= m->o.dd_local_newton && !conv; j++) {
+    uint32_t* set = va_k;
+    if (m->o.dd_local_shrink) {
+      CK(lns::launch_words_op(d, lns::kAnd, m->dd_set, d.always, va_k, c));
+      CK(lns::launch_words_op(d, lns::kOr, m->dd_set, m->dd_set, d.supp, c));  // supp of the previous step
+      set = m->dd_set;
+    }
+    CK(cudaMemsetAsync(&d.ctr->n_frontier[1], 0, sizeof(int), m->stream));
+    CK(lns::launch_compact(d, set, d.fr1, nullptr, &d.ctr->n_frontier[1], c));
+    CK(cudaMemcpyAsync(&d.ctr_h->n_frontier[1], &d.ctr->n_frontier[1], sizeof(int), cudaMemcpyDeviceToHost,
+                       m->stream));
+    TRY(sync(m));
+    if (d.ctr_h->n_frontier[1] == 0) break;
+    if (m->cur.iterations >= m->o.max_newton * (m->o.max_dd_outer + 1))
+      return fail(LNS_ENOCONV, "Algorithm 2 reached its local-solve limit");
+    int ob = 0;
+    TRY(dd_solve(m, set, nullptr, solve_id, &ob, &conv));
+    if (ob) *own_big = 1;
+  }
+  return LNS_OK;
+}
+
 lns_status dd_timestep(lns_model* m, double dt, lns_step_stats* out) {
   Dev& d = m->d;
   LaunchCfg c = cfg(m);
   TRY(open_step(m, dt));
   if (!m->dd_vt) TRY(dalloc_t(m, (size_t)d.W, &m->dd_vt));
+  if (!m->dd_set) TRY(dalloc_t(m, (size_t)d.W, &m->dd_set));
   TRY(dd_ensure(m, 0));
   CK(lns::launch_words_op(d, lns::kCopy, m->dd_va[0], d.va, nullptr, c));
   CK(lns::launch_words_op(d, lns::kCopy, m->dd_vt, d.va, nullptr, c));
@@ -786,7 +817,12 @@ lns_status dd_timestep(lns_model* m, double dt, lns_step_stats* out) {
     last_solve.push_back(solve_id);
     own_big.push_back(ob);
     TRY(dd_expand_sets(m, m->dd_vt, m->dd_va[k + 1], m->dd_vb[k + 1], m->dd_vdb[k + 1], &is_expand));
+    const lns_status rr = dd_refine(m, m->dd_va[k], conv, solve_id, &own_big.back());
     k++;
+    if (rr != LNS_OK) {
+      st = rr;
+      break;
+    }
   }
   const int N = k;
   m->cur.n_subdomains = N;
@@ -805,12 +841,21 @@ lns_status dd_timestep(lns_model* m, double dt, lns_step_stats* out) {
       TRY(sync(m));
       const int halo = d.ctr_h->halo_flag;
       if (!(own_big[s] || halo)) continue;
+      if (m->cur.iterations >= m->o.max_newton * (m->o.max_dd_outer + 1)) {
+        st = fail(LNS_ENOCONV, "Algorithm 2 reached its local-solve limit");
+        break;
+      }
       int ob = 0, conv = 0;
       solve_id++;
       TRY(dd_solve(m, m->dd_va[s], nullptr, solve_id, &ob, &conv));
       last_solve[s] = solve_id;
       own_big[s] = ob;
-      if (!conv) all_ok = false;
+      if (!conv) all_ok = false;  // the pass converges when every visited subdomain was already converged
+      const lns_status rr = dd_refine(m, m->dd_va[s], conv, solve_id, &own_big[s]);
+      if (rr != LNS_OK) {
+        st = rr;
+        break;
+      }
     }
     nu++;
     converged = all_ok;
@@ -967,6 +1012,8 @@ lns_status validate_options(const lns_options* o) {
     return fail(LNS_EINVAL, "unknown preconditioner");
   if (o->krylov_cluster > 16 || (o->krylov_cluster > 0 && (o->krylov_cluster & (o->krylov_cluster - 1))))
     return fail(LNS_EINVAL, "krylov_cluster must be < 0, 0, or a power of two <= 16");
+  if (o->dd_local_newton < 1 || o->dd_local_shrink < 0 || o->dd_local_shrink > 1)
+    return fail(LNS_EINVAL, "dd_local_newton must be >= 1 and dd_local_shrink 0 or 1");
   return LNS_OK;
 }
 
@@ -1056,6 +1103,8 @@ lns_status lns_options_default(lns_options* o) {
   o->fp64_fallback = 1;
   o->krylov_cluster = -1;
   o->autotune = 1;
+  o->dd_local_newton = 1;
+  o->dd_local_shrink = 0;
   return LNS_OK;
 }
 

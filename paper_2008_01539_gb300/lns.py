@@ -51,7 +51,8 @@ class lns_options(C.Structure):
                 ("max_dd_outer", C.c_int32), ("sat_chop", C.c_double), ("krylov_fp32", C.c_int32),
                 ("precond", C.c_int32), ("krylov_rtol", C.c_double), ("krylov_maxit", C.c_int32),
                 ("krylov_fail_rtol", C.c_double), ("p_scale", C.c_double), ("profile", C.c_int32),
-                ("fp64_fallback", C.c_int32), ("krylov_cluster", C.c_int32), ("autotune", C.c_int32)]
+                ("fp64_fallback", C.c_int32), ("krylov_cluster", C.c_int32), ("autotune", C.c_int32),
+                ("dd_local_newton", C.c_int32), ("dd_local_shrink", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -301,6 +302,8 @@ class Options:
     fp64_fallback: int = 1
     krylov_cluster: int = -1
     autotune: int = 1
+    dd_local_newton: int = 1
+    dd_local_shrink: int = 0
 
     def c(self) -> lns_options:
         return lns_options(*[getattr(self, f.name) for f in dataclasses.fields(self)])
