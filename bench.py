@@ -407,7 +407,30 @@ def large_3d_run(opts, flush, stream):
                          for k in kt if k["launches"] > 0}}
         out[tag] = r
     out["fp32_krylov"]["error_vs_fp64_krylov_gpu"] = field_error(*states["fp32_krylov"], *states["fp64_krylov"])
+    if os.environ.get("RANK", "0") == "0":
+        out["cpu_baseline"] = oracle_ilu0_iteration(case)
     return out
+
+
+def oracle_ilu0_iteration(case):
+    """The oracle's per-Newton-iteration time on the 3D model: one Algorithm 1 iteration (the first
+    timestep's first, on its initial active set) with the block ILU(0)-preconditioned BiCGStab
+    linear step; the sparse LU is infeasible at this size."""
+    import numpy as np
+
+    import oracle as O
+
+    m = O.Model(case)
+    opts = O.Options(mode=1, linear=1, lin_rtol=1e-8)
+    va = O.initial_set(m, opts, np.zeros(case.n, np.uint8), False)
+    t0 = time.perf_counter()
+    O.local_solve(m, opts, case.p0, case.sw0, case.p0, case.sw0, float(case.dt_schedule[0]), va)
+    t = time.perf_counter() - t0
+    n_a = int(va.sum())
+    return {"value": n_a / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one Newton iteration of Algorithm 1 (the first timestep's first, n_A = {n_a} rows) with "
+                      f"the oracle's block ILU(0)-BiCGStab linear step (rtol 1e-8), single thread, {t:.1f} s; the "
+                      f"oracle's sparse LU is infeasible at a million cells"}
 
 
 ENSEMBLE_SPAN_DAYS = 30.0

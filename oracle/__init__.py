@@ -63,7 +63,8 @@ class _Opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("eps_p", C.c_double), ("eps_sw", C.c_double),
                 ("m_layers", C.c_int32), ("tol_dp", C.c_double), ("tol_cnv", C.c_double),
                 ("max_newton", C.c_int32), ("sat_chop", C.c_double), ("max_dd_outer", C.c_int32),
-                ("dd_local_newton", C.c_int32), ("dd_local_shrink", C.c_int32)]
+                ("dd_local_newton", C.c_int32), ("dd_local_shrink", C.c_int32),
+                ("linear", C.c_int32), ("lin_rtol", C.c_double), ("lin_maxit", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -81,6 +82,9 @@ def _configure(L):
     L.orc_cnv.argtypes = [C.POINTER(_Model), vp, vp, C.c_double, vp]
     L.orc_lu_solve.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, C.POINTER(C.c_int64)]
     L.orc_lu_solve.restype = C.c_int
+    L.orc_ilu0_bicgstab.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, C.c_double, C.c_int32,
+                                    C.POINTER(C.c_int32)]
+    L.orc_ilu0_bicgstab.restype = C.c_int
     L.orc_dilate.argtypes = [C.POINTER(_Model), vp, C.c_int32, vp]
     L.orc_boundary.argtypes = [C.POINTER(_Model), vp, vp]
     L.orc_outer_halo.argtypes = [C.POINTER(_Model), vp, vp]
@@ -165,11 +169,14 @@ class Options:
     max_dd_outer: int = 25
     dd_local_newton: int = 1
     dd_local_shrink: int = 0
+    linear: int = 0          # 0 block sparse LU, 1 block ILU(0)-preconditioned BiCGStab
+    lin_rtol: float = 1e-10
+    lin_maxit: int = 5000
 
     def _c(self) -> _Opts:
         return _Opts(self.mode, self.eps_p, self.eps_sw, self.m_layers, self.tol_dp, self.tol_cnv,
                      self.max_newton, self.sat_chop, self.max_dd_outer, self.dd_local_newton,
-                     self.dd_local_shrink)
+                     self.dd_local_shrink, self.linear, self.lin_rtol, self.lin_maxit)
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -252,6 +259,20 @@ def lu_solve(row_ptr, col, diag, off, rhs) -> Tuple[np.ndarray, int]:
     if rc != 0:
         raise ArithmeticError("singular block pivot in the oracle's sparse LU")
     return x, int(fill.value)
+
+
+def ilu0_bicgstab(row_ptr, col, diag, off, rhs, rtol: float = 1e-10, maxit: int = 5000):
+    """BiCGStab with a block ILU(0) preconditioner on the block system (as lu_solve).
+    Returns (x, status, iterations): status 0 converged, 1 maxit, 2 breakdown."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.int32)
+    col = np.ascontiguousarray(col, np.int32)
+    diag, off, rhs = _f64(diag), _f64(off), _f64(rhs)
+    nb = row_ptr.shape[0] - 1
+    x = np.zeros((nb, 2))
+    its = C.c_int32(0)
+    st = lib().orc_ilu0_bicgstab(nb, _ptr(row_ptr), _ptr(col), _ptr(diag), _ptr(off), _ptr(rhs), _ptr(x),
+                                 float(rtol), int(maxit), C.byref(its))
+    return x, int(st), int(its.value)
 
 
 def dilate(m: Model, seed, layers: int) -> np.ndarray:

@@ -669,6 +669,206 @@ void orc_dd_expand(const orc_model* m, const orc_opts* o, const uint8_t* vb_k, c
  * full residual and Jacobian are assembled and the active rows and columns taken out,
  * which is the definition; inactive cells act as Dirichlet values.
  * ---------------------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------------------
+ * Block ILU(0) and BiCGStab (the oracle's iterative linear step, for models too large for
+ * the sparse LU).  2x2 blocks; the factors overwrite copies of the matrix: row i's blocks left
+ * of the diagonal hold L_ik (unit block diagonal), the diagonal and the blocks right of it hold
+ * U.  Elimination in row order, no fill: A_ij -= L_ik U_kj only where (i, j) is in the pattern.
+ * ---------------------------------------------------------------------------------- */
+static int inv2(const double* a, double* out) {
+  double det = a[0] * a[3] - a[1] * a[2];
+  if (det == 0.0 || !isfinite(det)) return 1;
+  out[0] = a[3] / det;
+  out[1] = -a[1] / det;
+  out[2] = -a[2] / det;
+  out[3] = a[0] / det;
+  return 0;
+}
+
+static void mm2(const double* a, const double* b, double* c) { /* c = a b */
+  c[0] = a[0] * b[0] + a[1] * b[2];
+  c[1] = a[0] * b[1] + a[1] * b[3];
+  c[2] = a[2] * b[0] + a[3] * b[2];
+  c[3] = a[2] * b[1] + a[3] * b[3];
+}
+
+static void mv2(const double* a, const double* x, double* y) { /* y = a x */
+  y[0] = a[0] * x[0] + a[1] * x[1];
+  y[1] = a[2] * x[0] + a[3] * x[1];
+}
+
+typedef struct {
+  int32_t nb;
+  const int32_t *rp, *cl;
+  double *ld, *lo; /* factored diagonal (U_ii) and off-diagonal blocks */
+  double* dinv;    /* U_ii^{-1} */
+} ilu0;
+
+static int ilu0_factor(ilu0* f, const double* diag, const double* off) {
+  int32_t nb = f->nb;
+  memcpy(f->ld, diag, sizeof(double) * 4 * (size_t)nb);
+  memcpy(f->lo, off, sizeof(double) * 4 * (size_t)f->rp[nb]);
+  int32_t* pos = (int32_t*)malloc(sizeof(int32_t) * (nb > 0 ? nb : 1));
+  for (int32_t j = 0; j < nb; j++) pos[j] = -1;
+  int bad = 0;
+  for (int32_t i = 0; i < nb && !bad; i++) {
+    for (int32_t q = f->rp[i]; q < f->rp[i + 1]; q++) pos[f->cl[q]] = q;
+    for (int32_t q = f->rp[i]; q < f->rp[i + 1]; q++) {
+      int32_t k = f->cl[q];
+      if (k >= i) continue;                    /* row i's lower blocks, in column order */
+      double l[4];
+      mm2(f->lo + 4 * (int64_t)q, f->dinv + 4 * (int64_t)k, l); /* L_ik = A_ik U_kk^{-1} */
+      memcpy(f->lo + 4 * (int64_t)q, l, sizeof(l));
+      for (int32_t q2 = f->rp[k]; q2 < f->rp[k + 1]; q2++) {
+        int32_t j = f->cl[q2];
+        if (j <= k) continue;                  /* U_kj, j > k */
+        double t[4];
+        mm2(l, f->lo + 4 * (int64_t)q2, t);
+        double* dst = (j == i) ? f->ld + 4 * (int64_t)i : (pos[j] >= 0 ? f->lo + 4 * (int64_t)pos[j] : NULL);
+        if (!dst) continue;                    /* outside the pattern: dropped (no fill) */
+        for (int c = 0; c < 4; c++) dst[c] -= t[c];
+      }
+    }
+    if (inv2(f->ld + 4 * (int64_t)i, f->dinv + 4 * (int64_t)i)) bad = 1;
+    for (int32_t q = f->rp[i]; q < f->rp[i + 1]; q++) pos[f->cl[q]] = -1;
+  }
+  free(pos);
+  return bad;
+}
+
+/* z = (LU)^{-1} r */
+static void ilu0_apply(const ilu0* f, const double* r, double* z) {
+  int32_t nb = f->nb;
+  for (int32_t i = 0; i < nb; i++) { /* L y = r, unit block diagonal */
+    double y[2] = {r[2 * i], r[2 * i + 1]};
+    for (int32_t q = f->rp[i]; q < f->rp[i + 1]; q++) {
+      int32_t k = f->cl[q];
+      if (k >= i) continue;
+      double t[2];
+      mv2(f->lo + 4 * (int64_t)q, z + 2 * (int64_t)k, t);
+      y[0] -= t[0];
+      y[1] -= t[1];
+    }
+    z[2 * i] = y[0];
+    z[2 * i + 1] = y[1];
+  }
+  for (int32_t i = nb - 1; i >= 0; i--) { /* U x = y */
+    double y[2] = {z[2 * i], z[2 * i + 1]};
+    for (int32_t q = f->rp[i]; q < f->rp[i + 1]; q++) {
+      int32_t j = f->cl[q];
+      if (j <= i) continue;
+      double t[2];
+      mv2(f->lo + 4 * (int64_t)q, z + 2 * (int64_t)j, t);
+      y[0] -= t[0];
+      y[1] -= t[1];
+    }
+    mv2(f->dinv + 4 * (int64_t)i, y, z + 2 * (int64_t)i);
+  }
+}
+
+static void bmatvec(int32_t nb, const int32_t* rp, const int32_t* cl, const double* diag, const double* off,
+                    const double* x, double* y) {
+  for (int32_t i = 0; i < nb; i++) {
+    double a[2];
+    mv2(diag + 4 * (int64_t)i, x + 2 * (int64_t)i, a);
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+      double t[2];
+      mv2(off + 4 * (int64_t)q, x + 2 * (int64_t)cl[q], t);
+      a[0] += t[0];
+      a[1] += t[1];
+    }
+    y[2 * i] = a[0];
+    y[2 * i + 1] = a[1];
+  }
+}
+
+static double dot(int64_t n, const double* a, const double* b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+  return s;
+}
+
+int orc_ilu0_bicgstab(int32_t nb, const int32_t* row_ptr, const int32_t* col, const double* diag,
+                      const double* off, const double* rhs, double* x, double rtol, int32_t maxit, int32_t* iters) {
+  int64_t n2 = 2 * (int64_t)nb;
+  size_t v = sizeof(double) * (size_t)(n2 > 0 ? n2 : 1);
+  const size_t nd = sizeof(double) * 4 * (size_t)(nb > 0 ? nb : 1);
+  const size_t no = sizeof(double) * 4 * (size_t)(row_ptr[nb] > 0 ? row_ptr[nb] : 1);
+  ilu0 f = {nb, row_ptr, col, (double*)malloc(nd), (double*)malloc(no), (double*)malloc(nd)};
+  double *r = (double*)malloc(v), *rh = (double*)malloc(v), *pv = (double*)malloc(v), *vv = (double*)malloc(v);
+  double *ph = (double*)malloc(v), *sv = (double*)malloc(v), *sh = (double*)malloc(v), *tv = (double*)malloc(v);
+  int status = 1, it = 0;
+  for (int64_t i = 0; i < n2; i++) {
+    x[i] = 0.0;
+    r[i] = rhs[i];
+    rh[i] = rhs[i];
+    pv[i] = 0.0;
+    vv[i] = 0.0;
+  }
+  double bn = sqrt(dot(n2, rhs, rhs));
+  if (nb == 0 || bn == 0.0) {
+    status = 0;
+  } else if (ilu0_factor(&f, diag, off)) {
+    status = 2;
+  } else {
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    for (it = 1; it <= maxit; it++) {
+      double rho1 = dot(n2, rh, r);
+      if (rho1 == 0.0 || !isfinite(rho1)) {
+        status = 2;
+        break;
+      }
+      double beta = (rho1 / rho) * (alpha / omega);
+      for (int64_t i = 0; i < n2; i++) pv[i] = r[i] + beta * (pv[i] - omega * vv[i]);
+      ilu0_apply(&f, pv, ph);
+      bmatvec(nb, row_ptr, col, diag, off, ph, vv);
+      double rv = dot(n2, rh, vv);
+      if (rv == 0.0 || !isfinite(rv)) {
+        status = 2;
+        break;
+      }
+      alpha = rho1 / rv;
+      for (int64_t i = 0; i < n2; i++) sv[i] = r[i] - alpha * vv[i];
+      if (sqrt(dot(n2, sv, sv)) <= rtol * bn) {
+        for (int64_t i = 0; i < n2; i++) x[i] += alpha * ph[i];
+        status = 0;
+        break;
+      }
+      ilu0_apply(&f, sv, sh);
+      bmatvec(nb, row_ptr, col, diag, off, sh, tv);
+      double tt = dot(n2, tv, tv);
+      omega = tt > 0.0 ? dot(n2, tv, sv) / tt : 0.0;
+      for (int64_t i = 0; i < n2; i++) {
+        x[i] += alpha * ph[i] + omega * sh[i];
+        r[i] = sv[i] - omega * tv[i];
+      }
+      if (sqrt(dot(n2, r, r)) <= rtol * bn) {
+        status = 0;
+        break;
+      }
+      if (omega == 0.0) {
+        status = 2;
+        break;
+      }
+      rho = rho1;
+    }
+    if (it > maxit) it = maxit;
+  }
+  if (iters) *iters = it;
+  free(f.ld);
+  free(f.lo);
+  free(f.dinv);
+  free(r);
+  free(rh);
+  free(pv);
+  free(vv);
+  free(ph);
+  free(sv);
+  free(sh);
+  free(tv);
+  return status;
+}
+
 int orc_local_solve(const orc_model* m, const orc_opts* o, const double* p, const double* sw,
                     const double* pn, const double* swn, double dt, const uint8_t* va,
                     double* dp, double* dsw, double* cnv_max, double* dp_max) {
@@ -713,7 +913,14 @@ int orc_local_solve(const orc_model* m, const orc_opts* o, const double* p, cons
     if (cnv[i] > cmax) cmax = cnv[i];
   }
   rp[na] = (int32_t)q;
-  int status = orc_lu_solve(na, rp, cl, db, ob, rhs, x, NULL);
+  int status;
+  if (o->linear == 1) {
+    int32_t its = 0;
+    status = orc_ilu0_bicgstab(na, rp, cl, db, ob, rhs, x, o->lin_rtol > 0.0 ? o->lin_rtol : 1e-10,
+                               o->lin_maxit > 0 ? o->lin_maxit : 5000, &its);
+  } else {
+    status = orc_lu_solve(na, rp, cl, db, ob, rhs, x, NULL);
+  }
   for (int32_t i = 0; i < n; i++) {
     dp[i] = 0.0;
     dsw[i] = 0.0;

@@ -20,7 +20,8 @@
  *     (unconverged cells plus layers of neighbours), as mode 3.
  * The linear step is a hand-written block sparse LU (nested-dissection ordering,
  * symbolic factorization by elimination tree, row-by-row Doolittle elimination
- * with 2x2 block pivots).
+ * with 2x2 block pivots), or on request BiCGStab with a block ILU(0) preconditioner
+ * (for models too large for the LU; the CPU baseline of the million-cell case).
  *
  * Parity pins (tests/test_oracle_pins.py): closed-form erfc solution for 1D
  * slightly compressible flow into a constant-pressure fracture; cumulative mass
@@ -76,6 +77,11 @@ typedef struct {
    * support of the previous step's update within the subdomain, plus its always-active cells. */
   int32_t dd_local_newton;
   int32_t dd_local_shrink;
+  /* linear step: 0 the block sparse LU (default), 1 BiCGStab preconditioned by block ILU(0) in the
+   * natural (ascending cell) order, stopped at ||r|| <= lin_rtol ||b|| or lin_maxit iterations */
+  int32_t linear;
+  double lin_rtol;
+  int32_t lin_maxit;
 } orc_opts;
 
 typedef struct {
@@ -103,6 +109,11 @@ void orc_cnv(const orc_model* m, const double* p, const double* F, double dt, do
 /* Solve the block system A x = rhs (2x2 blocks, structurally symmetric pattern given by
  * row_ptr/col without the diagonal).  Returns 0, or -1 on a singular pivot. *fill gets
  * the number of stored off-diagonal blocks of L+U. */
+/* BiCGStab on the block system (diag, off as for orc_lu_solve), right-preconditioned by block
+ * ILU(0) (no fill beyond the pattern of the matrix; rows eliminated in index order).  Returns 0 on
+ * convergence, 1 at maxit, 2 on breakdown or a singular pivot; *iters gets the iterations. */
+int orc_ilu0_bicgstab(int32_t nb, const int32_t* row_ptr, const int32_t* col, const double* diag,
+                      const double* off, const double* rhs, double* x, double rtol, int32_t maxit, int32_t* iters);
 int orc_lu_solve(int32_t nb, const int32_t* row_ptr, const int32_t* col, const double* diag,
                  const double* off, const double* rhs, double* x, int64_t* fill);
 
