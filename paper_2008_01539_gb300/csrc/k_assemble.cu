@@ -509,6 +509,48 @@ __global__ void __launch_bounds__(32 * kLineWarps, 1) k_line_factor(Dev d) {
   }
 }
 
+// line_cum[l] = rows of the line blocks before block l of the ascending list, for l = 0 .. n_lines
+// (the grid solver weighs its row chunks by it).  One block: each thread sums a run of consecutive
+// blocks, an exclusive scan over the threads gives the runs' offsets, then each run is written.
+constexpr int kCumThreads = 1024;
+__global__ void __launch_bounds__(kCumThreads, 1) k_line_cum(Dev d) {
+  __shared__ int s_w[32];
+  __shared__ int s_tot;
+  const int nl = d.ctr->n_lines;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int per = (nl + kCumThreads - 1) / kCumThreads;
+  const int l0 = min(nl, (int)threadIdx.x * per), l1 = min(nl, l0 + per);
+  int sum = 0;
+#pragma unroll 4
+  for (int l = l0; l < l1; l++) sum += __ldg(&d.line_len[__ldg(&d.line_start[l])]);
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_w[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int v = s_w[lane];
+    int iv = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, iv, o);
+      if (lane >= o) iv += u;
+    }
+    s_w[lane] = iv - v;
+    if (lane == 31) s_tot = iv;
+  }
+  __syncthreads();
+  int run = s_w[w] + incl - sum;
+  for (int l = l0; l < l1; l++) {
+    d.line_cum[l] = run;
+    run += __ldg(&d.line_len[__ldg(&d.line_start[l])]);
+  }
+  if (threadIdx.x == 0) d.line_cum[nl] = s_tot;
+}
+
 }  // namespace
 
 cudaError_t launch_assemble(const Dev& d, double p_scale, int fp32, int lines, int debug, LaunchCfg c) {
@@ -568,7 +610,11 @@ cudaError_t launch_line_setup(const Dev& d, int fp32, LaunchCfg c) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // ascending line-block starts (compact rows < n_active <= n, so the n-bit bitset covers them)
-  return launch_compact(d, d.lblk, d.line_start, d.lscratch, &d.ctr->n_lines, c);
+  e = launch_compact(d, d.lblk, d.line_start, d.lscratch, &d.ctr->n_lines, c);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  k_line_cum<<<1, kCumThreads, 0, c.stream>>>(d);
+  return cudaGetLastError();
 }
 
 }  // namespace lns

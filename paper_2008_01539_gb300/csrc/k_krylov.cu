@@ -321,17 +321,21 @@ __device__ __forceinline__ typename V2<T>::t row_product(const int* col, const B
 }
 
 // ---- fracture-line solve -----------------------------------------------------------------
-// FP32 block-Thomas recurrences of one 32-row chunk for NR right-hand sides, as inclusive warp
-// scans of 2x2 affine maps, local to the chunk (zero carry-in):
-//   fwd: w_t = Dinv_t src_t + A_t w_{t-1};   bwd: z_t = w_t - G_t z_{t+1}.
-// On return lane t holds c_t and the composite map P_t such that the value of row t is
-// c_t + P_t * (the value entering the chunk).
+// FP32 block-Thomas recurrences of a fracture-line block for NR right-hand sides,
+//   fwd: w_t = Dinv_t src_t + A_t w_{t-1};   bwd: z_t = w_t - G_t z_{t+1},
+// as inclusive warp scans of 2x2 affine maps (one map per lane: a row, or the composite of the
+// lane's rows), local to a segment of seg lanes (zero carry-in).  On return lane t holds c_t and
+// the composite map P_t such that the value at lane t is c_t + P_t * (the value entering the
+// segment).
+// A lane with no partner at a level takes the identity map and a zero value from it, so every
+// lane runs the same instructions (no divergent branch per level).
 template <int NR>
 __device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float>& A, int lane, int seg = 32) {
   const int t = lane & (seg - 1);  // position in the segment of seg lanes (a power of two)
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     if (o >= seg) break;  // uniform
+    const bool in = t >= o;
     M2<float> Ap;
     Ap.a = __shfl_up_sync(0xffffffffu, A.a, o);
     Ap.b = __shfl_up_sync(0xffffffffu, A.b, o);
@@ -342,15 +346,15 @@ __device__ __forceinline__ void scan_fwd(float2 (&c)[NR], M2<float>& A, int lane
     for (int q = 0; q < NR; q++) {
       cp[q].x = __shfl_up_sync(0xffffffffu, c[q].x, o);
       cp[q].y = __shfl_up_sync(0xffffffffu, c[q].y, o);
+      cp[q] = in ? cp[q] : make_float2(0.f, 0.f);
     }
-    if (t >= o) {
+    Ap = in ? Ap : M2<float>{1.f, 0.f, 0.f, 1.f};
 #pragma unroll
-      for (int q = 0; q < NR; q++) {
-        c[q].x += A.a * cp[q].x + A.b * cp[q].y;
-        c[q].y += A.c * cp[q].x + A.d * cp[q].y;
-      }
-      A = mm(A, Ap);
+    for (int q = 0; q < NR; q++) {
+      c[q].x += A.a * cp[q].x + A.b * cp[q].y;
+      c[q].y += A.c * cp[q].x + A.d * cp[q].y;
     }
+    A = mm(A, Ap);
   }
 }
 
@@ -360,6 +364,7 @@ __device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float>& B, int lane
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     if (o >= seg) break;  // uniform
+    const bool in = t + o < seg;
     M2<float> Bp;
     Bp.a = __shfl_down_sync(0xffffffffu, B.a, o);
     Bp.b = __shfl_down_sync(0xffffffffu, B.b, o);
@@ -370,105 +375,136 @@ __device__ __forceinline__ void scan_bwd(float2 (&c)[NR], M2<float>& B, int lane
     for (int q = 0; q < NR; q++) {
       cp[q].x = __shfl_down_sync(0xffffffffu, c[q].x, o);
       cp[q].y = __shfl_down_sync(0xffffffffu, c[q].y, o);
+      cp[q] = in ? cp[q] : make_float2(0.f, 0.f);
     }
-    if (t + o < seg) {
+    Bp = in ? Bp : M2<float>{1.f, 0.f, 0.f, 1.f};
 #pragma unroll
-      for (int q = 0; q < NR; q++) {
-        c[q].x += B.a * cp[q].x + B.b * cp[q].y;
-        c[q].y += B.c * cp[q].x + B.d * cp[q].y;
-      }
-      B = mm(B, Bp);
+    for (int q = 0; q < NR; q++) {
+      c[q].x += B.a * cp[q].x + B.b * cp[q].y;
+      c[q].y += B.c * cp[q].x + B.d * cp[q].y;
     }
+    B = mm(B, Bp);
   }
 }
 
-// value of a row from its chunk-local scan and the value entering the chunk
-__device__ __forceinline__ float2 apply_carry(float2 c, const M2<float>& P, float2 carry) {
-  return make_float2(c.x + P.a * carry.x + P.b * carry.y, c.y + P.c * carry.x + P.d * carry.y);
-}
-
-// Factors of one line block: row t's D'^{-1}, A and G at fd[t*fs], fa[t*fs], fg[t*fs].
+// Factors of one line block: row t's D'^{-1}, A and G at fd[at(t)], fa[at(t)], fg[at(t)], with
+// at(t) = (o + t) fs + ((o + t) / 4) pad: the global arrays (fs 1, pad 0), or the rows staged in
+// shared memory at fac_slot (fs 3, pad 1).
 struct LineFac {
   const float4 *fd, *fa, *fg;
-  int fs;
+  int o, fs, pad;
+  __device__ __forceinline__ int at(int t) const {
+    const int i = o + t;
+    return i * fs + (i >> 2) * pad;
+  }
 };
+// Staged line factors: row i of a chunk at float4 slots fac_slot(i) + 0, 1, 2.  A pad slot after
+// every four rows puts the four consecutive rows each lane of a whole-warp line solve reads at a
+// stride of 13 slots, so the lanes of a quarter warp hit distinct banks.
+__device__ __forceinline__ int fac_slot(int i) { return 3 * i + (i >> 2); }
+constexpr size_t fac_slots(size_t rows) { return 3 * rows + rows / 4 + 1; }
 
-constexpr int kLineChunks = kLineBlockRows / 32;
+constexpr int kLineRpl = kLineBlockRows / 32;  // rows per lane of a whole-warp line solve
+
+// affine maps on a row value v -> M v + c: the map of row t after the map of the rows before it
+__device__ __forceinline__ float2 mv2(const M2<float>& M, float2 v) {
+  return make_float2(M.a * v.x + M.b * v.y, M.c * v.x + M.d * v.y);
+}
 
 // M^{-1} on one line block (len <= kLineBlockRows rows) for NR right-hand sides.  Input q of row
-// k0 + t is buf[q * bstride + t]; results are stored to dst[q][k0 + t].  The chunks of 32 rows
-// are scanned independently (their shuffle chains overlap), then the values entering each chunk
-// are passed along the chunks: only a 2x2 product per chunk and sweep stays sequential.
+// k0 + t is buf[q * bstride + t]; results are stored to dst[q][k0 + t].  Lane l holds the
+// kLineRpl consecutive rows starting at kLineRpl * l.  Each sweep composes its rows' affine maps
+// inside the lane, scans the 32 lane maps across the warp (one chain of five shuffle levels for
+// the whole block), and recomputes its rows from the value entering the lane.
 template <typename T, int NR>
 __device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, const float2* buf, int bstride,
                                            typename V2<T>::t* const (&dst)[NR]) {
+  constexpr int R = kLineRpl;
   const int lane = threadIdx.x & 31;
-  float2 w[kLineChunks][NR];
-  M2<float> P[kLineChunks];
+  float2 c[R][NR];
+  M2<float> A[R], B[R];
+  // every load of the lane's rows (both sweeps) is issued first; rows at or beyond len are zero
+  // maps and zero values, so they pass nothing to the rows of the block
 #pragma unroll
-  for (int c = 0; c < kLineChunks; c++) {
-    const int t = c * 32 + lane;
-    P[c] = {0.f, 0.f, 0.f, 0.f};
+  for (int j = 0; j < R; j++) {
+    const int t = R * lane + j;
+    A[j] = {0.f, 0.f, 0.f, 0.f};
+    B[j] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < NR; q++) w[c][q] = make_float2(0.f, 0.f);
-    if (c * 32 < len) {  // warp-uniform
-      if (t < len) {
-        const float4 Di = f.fd[(size_t)t * f.fs];
+    for (int q = 0; q < NR; q++) c[j][q] = make_float2(0.f, 0.f);
+    if (t < len) {
+      const int ft = f.at(t);
+      const float4 Di = f.fd[ft];
+      const float4 a4 = f.fa[ft];
+      const float4 g4 = f.fg[ft];
 #pragma unroll
-        for (int q = 0; q < NR; q++) {
-          const float2 u = buf[q * bstride + t];
-          w[c][q] = make_float2(Di.x * u.x + Di.y * u.y, Di.z * u.x + Di.w * u.y);
-        }
-        const float4 a4 = f.fa[(size_t)t * f.fs];
-        P[c] = {a4.x, a4.y, a4.z, a4.w};
-      }
-      scan_fwd<NR>(w[c], P[c], lane);
+      for (int q = 0; q < NR; q++) c[j][q] = mv2({Di.x, Di.y, Di.z, Di.w}, buf[q * bstride + t]);
+      A[j] = {a4.x, a4.y, a4.z, a4.w};
+      B[j] = {-g4.x, -g4.y, -g4.z, -g4.w};
     }
   }
-  float2 carry[NR];
+  // forward sweep w_t = Dinv_t src_t + A_t w_{t-1}: the lane's composite map, the warp scan, then
+  // the rows from the last row of the lane before
+  {
+    M2<float> M = A[0];
+    float2 cl[NR];
 #pragma unroll
-  for (int q = 0; q < NR; q++) carry[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < NR; q++) cl[q] = c[0][q];
 #pragma unroll
-  for (int c = 0; c < kLineChunks; c++)
-    if (c * 32 < len) {
-      const int last = min(31, len - 1 - c * 32);
+    for (int j = 1; j < R; j++) {
 #pragma unroll
       for (int q = 0; q < NR; q++) {
-        w[c][q] = apply_carry(w[c][q], P[c], carry[q]);
-        carry[q].x = __shfl_sync(0xffffffffu, w[c][q].x, last);
-        carry[q].y = __shfl_sync(0xffffffffu, w[c][q].y, last);
+        const float2 u = mv2(A[j], cl[q]);
+        cl[q] = make_float2(u.x + c[j][q].x, u.y + c[j][q].y);
       }
+      M = mm(A[j], M);
     }
-  // backward sweep: z_t = w_t - G_t z_{t+1}
+    scan_fwd<NR>(cl, M, lane);
 #pragma unroll
-  for (int c = 0; c < kLineChunks; c++) {
-    const int t = c * 32 + lane;
-    P[c] = {0.f, 0.f, 0.f, 0.f};
-    if (c * 32 < len) {
-      if (t < len) {
-        const float4 g4 = f.fg[(size_t)t * f.fs];
-        P[c] = {-g4.x, -g4.y, -g4.z, -g4.w};
-      } else {
+    for (int q = 0; q < NR; q++) {
+      float2 w;
+      w.x = __shfl_up_sync(0xffffffffu, cl[q].x, 1);
+      w.y = __shfl_up_sync(0xffffffffu, cl[q].y, 1);
+      if (lane == 0) w = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int q = 0; q < NR; q++) w[c][q] = make_float2(0.f, 0.f);
+      for (int j = 0; j < R; j++) {
+        const float2 u = mv2(A[j], w);
+        w = make_float2(u.x + c[j][q].x, u.y + c[j][q].y);
+        c[j][q] = w;
       }
-      scan_bwd<NR>(w[c], P[c], lane);
     }
   }
+  // backward sweep z_t = w_t - G_t z_{t+1}, mirrored
+  {
+    M2<float> M = B[R - 1];
+    float2 cl[NR];
 #pragma unroll
-  for (int q = 0; q < NR; q++) carry[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < NR; q++) cl[q] = c[R - 1][q];
 #pragma unroll
-  for (int c = kLineChunks - 1; c >= 0; c--)
-    if (c * 32 < len) {
-      const int t = c * 32 + lane;
+    for (int j = R - 2; j >= 0; j--) {
 #pragma unroll
       for (int q = 0; q < NR; q++) {
-        const float2 z = apply_carry(w[c][q], P[c], carry[q]);
+        const float2 u = mv2(B[j], cl[q]);
+        cl[q] = make_float2(u.x + c[j][q].x, u.y + c[j][q].y);
+      }
+      M = mm(B[j], M);
+    }
+    scan_bwd<NR>(cl, M, lane);
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+      float2 z;
+      z.x = __shfl_down_sync(0xffffffffu, cl[q].x, 1);
+      z.y = __shfl_down_sync(0xffffffffu, cl[q].y, 1);
+      if (lane == 31) z = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = R - 1; j >= 0; j--) {
+        const float2 u = mv2(B[j], z);
+        z = make_float2(u.x + c[j][q].x, u.y + c[j][q].y);
+        const int t = R * lane + j;
         if (t < len) dst[q][k0 + t] = mk<T>((T)z.x, (T)z.y);
-        carry[q].x = __shfl_sync(0xffffffffu, z.x, 0);
-        carry[q].y = __shfl_sync(0xffffffffu, z.y, 0);
       }
     }
+  }
 }
 
 // M^{-1} on short line blocks packed into segments of `seg` lanes (4, 8, 16 or 32; a line block of
@@ -497,9 +533,10 @@ __device__ __forceinline__ void line_solve_seg(int seg, int k0, int len, const L
 #pragma unroll
   for (int q = 0; q < NR; q++) w[q] = make_float2(0.f, 0.f);
   if (on) {  // every load of the row (both sweeps) is issued before the first scan
-    const float4 Di = f.fd[(size_t)t * f.fs];
-    const float4 a4 = f.fa[(size_t)t * f.fs];
-    g4 = f.fg[(size_t)t * f.fs];
+    const int ft = f.at(t);
+    const float4 Di = f.fd[ft];
+    const float4 a4 = f.fa[ft];
+    g4 = f.fg[ft];
 #pragma unroll
     for (int q = 0; q < NR; q++) {
       const float2 u = buf[q * bstride + t];
@@ -568,18 +605,18 @@ struct RowRef {
   int off, deg, line;
 };
 
-// Rows are split into one contiguous chunk per block, whose ends are moved forward so that no
-// fracture-line block straddles two chunks: a block solves its own line blocks after a block
+// Rows are split into one contiguous chunk per block, by cost (weighted_edge: a line row counts
+// more), whose ends are moved forward so that no fracture-line block straddles two chunks: a block solves its own line blocks after a block
 // barrier, from inputs its threads left in a block buffer.  Dynamic shared memory of a block:
 // the references of its first kRowsCached rows per thread, the line input buffer (two float2
 // per row), the line factors of its first kFacRows rows, the line-block table, and the pool of
 // staged matrix rows (columns and blocks).
 constexpr int kBufRows = 2048;   // chunk rows whose line inputs fit the shared buffer
 constexpr int kFacRows = 512;    // chunk rows whose line factors are staged
-constexpr int kLineList = 1024;  // line blocks of a chunk listed by length class (else one per warp)
+constexpr int kLineList = 1024;  // line blocks of a chunk listed in shared memory (else in d.lsort)
 constexpr size_t kSmRref = (size_t)kRowsCached * kKryBlk * sizeof(RowRef);
 constexpr size_t kSmBuf = (size_t)2 * kBufRows * sizeof(float2);
-constexpr size_t kSmFac = (size_t)kFacRows * 3 * sizeof(float4);
+constexpr size_t kSmFac = fac_slots(kFacRows) * sizeof(float4);
 constexpr size_t kSmLines = (size_t)kLineList * sizeof(int2);
 constexpr size_t kSmPool = kKrySmem - kSmRref - kSmBuf - kSmFac - kSmLines;
 
@@ -597,25 +634,49 @@ __device__ __forceinline__ int chunk_edge(const Dev& d, int k, int nA) {
   }
 }
 
-// First index l with line_start[l] >= k (line_start ascending, n entries), by one warp in steps
-// that narrow the range 32-fold; valid in all lanes.
-__device__ __forceinline__ int line_lower_bound(const int* ls, int n, int k) {
+// First index q in [0, n) with pred(q) true, pred false then true along q (n if none), by one warp
+// in steps that narrow the range 32-fold; valid in all lanes.
+template <typename Pred>
+__device__ __forceinline__ int warp_first(int n, Pred pred) {
   const int lane = threadIdx.x & 31;
   int lo = 0, hi = n;  // the answer lies in [lo, hi]
   while (hi - lo > 32) {
     const int step = (hi - lo + 31) / 32;
     const int q = lo + lane * step;
-    // samples at or beyond hi count as ">= k" (the answer is at most hi)
-    const bool ge = q >= hi || __ldg(&ls[q]) >= k;
-    const unsigned m = __ballot_sync(0xffffffffu, ge);
-    const int f = m ? __ffs(m) - 1 : 32;  // first sample with ls >= k
+    // samples at or beyond hi count as true (the answer is at most hi)
+    const unsigned m = __ballot_sync(0xffffffffu, q >= hi || pred(q));
+    const int f = m ? __ffs(m) - 1 : 32;  // first true sample
     const int nhi = f < 32 ? min(hi, lo + f * step) : hi;
-    if (f > 0) lo += (f - 1) * step;      // sample f-1 has ls < k
+    if (f > 0) lo += (f - 1) * step;      // sample f-1 is false
     hi = nhi;
   }
   const int q = lo + lane;
-  const unsigned m = __ballot_sync(0xffffffffu, q < hi && __ldg(&ls[q]) >= k);
+  const unsigned m = __ballot_sync(0xffffffffu, q < hi && pred(q));
   return m ? lo + __ffs(m) - 1 : hi;
+}
+
+// First index l with line_start[l] >= k (line_start ascending, n entries); valid in all lanes.
+__device__ __forceinline__ int line_lower_bound(const int* ls, int n, int k) {
+  return warp_first(n, [&](int q) { return __ldg(&ls[q]) >= k; });
+}
+
+// Where the grid solver's row chunk b of nb starts.  A fracture-line row costs more than another
+// row (its line solve follows its product), so the rows are split by cost: 2 units per row plus w
+// per line row (Dev::line_w).  The cost of rows [0, k) is 2 k + w LR(k), LR(k) the line rows among
+// them (line_cum at the line-block starts); chunk b starts where that cost reaches b / nb of the
+// total, and a start inside a line block moves to the nearer end of the block.  Nondecreasing in
+// b, 0 at b = 0 and n_A at b = nb.  One warp; valid in all lanes.
+__device__ __forceinline__ int weighted_edge(const Dev& d, int w, int b, int nb, int nA, int nl) {
+  const long long tot = 2LL * nA + (long long)w * __ldg(&d.line_cum[nl]);
+  const long long T = tot * b / nb;
+  // cost of the rows before line block l: 2 s_l + w line_cum[l], ascending in l
+  auto key = [&](int l) { return 2LL * __ldg(&d.line_start[l]) + (long long)w * __ldg(&d.line_cum[l]); };
+  const int f = warp_first(nl, [&](int l) { return key(l) > T; });
+  if (f == 0) return (int)min(T / 2, (long long)nA);  // before the first line block
+  const int s = __ldg(&d.line_start[f - 1]), len = __ldg(&d.line_len[s]);
+  const long long ks = key(f - 1), ke = ks + (2 + w) * (long long)len;
+  if (T < ke) return T - ks < ke - T ? s : s + len;
+  return (int)min(s + len + (T - ke) / 2, (long long)nA);
 }
 
 template <typename T, bool LINES>
@@ -670,6 +731,11 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   if (wib == 0) {
     const int rpb = (nA + nb - 1) / nb;
     int c0 = min(nA, (int)blockIdx.x * rpb), c1 = min(nA, c0 + rpb);
+    if (LINES && nlines > 0) {
+      const int w = d.line_w[sizeof(T) == 4 ? 1 : 0];
+      c0 = weighted_edge(d, w, blockIdx.x, nb, nA, nlines);
+      c1 = weighted_edge(d, w, blockIdx.x + 1, nb, nA, nlines);
+    }
     if (LINES) {
       c0 = chunk_edge(d, c0, nA);
       c1 = chunk_edge(d, c1, nA);
@@ -727,14 +793,16 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   if (LINES) {
     for (int k = kbeg; k < min(r1, r0 + kFacRows); k += kstep)
       if (__ldg(&d.line_row_flag[k])) {
-        float4* f = &s_fac[3 * (size_t)(k - r0)];
+        float4* f = &s_fac[fac_slot(k - r0)];
         f[0] = __ldg((const float4*)d.line_dinv + k);
         f[1] = __ldg((const float4*)d.line_a + k);
         f[2] = __ldg((const float4*)d.line_g + k);
       }
     // list the chunk's line blocks by length class (the order inside a class does not matter: each
-    // block is solved alone, the same way wherever it sits)
-    if (nlb <= kLineList) {
+    // block is solved alone, the same way wherever it sits), in shared memory or, for a chunk with
+    // more line blocks than that holds, in the chunk's own range of d.lsort
+    {
+      int2* const ltab = nlb <= kLineList ? s_lines : d.lsort + l0;
       for (int j = threadIdx.x; j < nlb; j += kstep)
         atomicAdd(&s_ccount[line_class(__ldg(&d.line_len[__ldg(&d.line_start[l0 + j])]))], 1);
       __syncthreads();
@@ -753,11 +821,12 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       for (int j = threadIdx.x; j < nlb; j += kstep) {
         const int k0 = __ldg(&d.line_start[l0 + j]);
         const int len = __ldg(&d.line_len[k0]);
-        s_lines[atomicAdd(&s_cfill[line_class(len)], 1)] = make_int2(k0, len);
+        ltab[atomicAdd(&s_cfill[line_class(len)], 1)] = make_int2(k0, len);
       }
     }
   }
   __syncthreads();
+  const int2* const ltab = nlb <= kLineList ? s_lines : d.lsort + l0;
 
   // fn(k, ref) over this thread's rows of the chunk (one call site: one copy of the row code); the
   // next row's reference is loaded before the current row is processed
@@ -784,32 +853,22 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       __syncthreads();
       auto fac = [&](const int2& kl) -> LineFac {
         const int o = kl.x - r0;
-        const float4* fb = &s_fac[3 * (size_t)o];
-        return o + kl.y <= kFacRows ? LineFac{fb, fb + 1, fb + 2, 3}
+        return o + kl.y <= kFacRows ? LineFac{s_fac, s_fac + 1, s_fac + 2, o, 3, 1}
                                     : LineFac{(const float4*)d.line_dinv + kl.x, (const float4*)d.line_a + kl.x,
-                                              (const float4*)d.line_g + kl.x, 1};
+                                              (const float4*)d.line_g + kl.x, 0, 1, 0};
       };
-      if (nlb <= kLineList) {
-        const int nit = s_citem[5];
+      const int nit = s_citem[5];
 #pragma unroll 1
-        for (int it = wib; it < nit; it += kWarps) {
-          int c = 0;
-          while (c < 4 && it >= s_citem[c + 1]) c++;
-          const int idx = it - s_citem[c];
-          if (c < 4) {
-            const int seg = 4 << c, li = idx * (8 >> c) + (lane >> (c + 2));
-            const int2 kl = li < s_ccount[c] ? s_lines[s_coff[c] + li] : make_int2(r0, 0);
-            solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), seg);
-          } else {
-            const int2 kl = s_lines[s_coff[4] + idx];
-            solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), 0);
-          }
-        }
-      } else {  // more line blocks than the list holds: one warp per block, in table order
-#pragma unroll 1
-        for (int j = wib; j < nlb; j += kWarps) {
-          const int k0 = __ldg(&d.line_start[l0 + j]);
-          const int2 kl = make_int2(k0, __ldg(&d.line_len[k0]));
+      for (int it = wib; it < nit; it += kWarps) {
+        int c = 0;
+        while (c < 4 && it >= s_citem[c + 1]) c++;
+        const int idx = it - s_citem[c];
+        if (c < 4) {
+          const int seg = 4 << c, li = idx * (8 >> c) + (lane >> (c + 2));
+          const int2 kl = li < s_ccount[c] ? ltab[s_coff[c] + li] : make_int2(r0, 0);
+          solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), seg);
+        } else {
+          const int2 kl = ltab[s_coff[4] + idx];
           solvefn(kl.x, kl.y, fac(kl), lbuf + (kl.x - r0), 0);
         }
       }
@@ -1216,7 +1275,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
   V* const szf = s_vec + 6 * R;
   float2* const lbuf = (float2*)(dsm + 7 * (size_t)R * sizeof(V));
   float4* const s_fac = (float4*)((unsigned char*)lbuf + 2 * (size_t)R * sizeof(float2));
-  Ref* const s_ref = (Ref*)((unsigned char*)s_fac + 3 * (size_t)R * sizeof(float4));
+  Ref* const s_ref = (Ref*)((unsigned char*)s_fac + fac_slots(R) * sizeof(float4));
   int2* const s_lines = (int2*)((unsigned char*)s_ref + (size_t)R * sizeof(Ref));
   unsigned char* const pool = (unsigned char*)s_lines + (size_t)kClLineList * sizeof(int2);
   const size_t pool_bytes = kClSmem - (size_t)(pool - dsm);
@@ -1288,9 +1347,10 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
   for (int i = threadIdx.x; i < nr; i += kClThreads) {
     s_ref[i] = stage(c0 + i);
     if (LINES && __ldg(&d.line_row_flag[c0 + i])) {
-      s_fac[3 * (size_t)i + 0] = __ldg((const float4*)d.line_dinv + c0 + i);
-      s_fac[3 * (size_t)i + 1] = __ldg((const float4*)d.line_a + c0 + i);
-      s_fac[3 * (size_t)i + 2] = __ldg((const float4*)d.line_g + c0 + i);
+      float4* f = &s_fac[fac_slot(i)];
+      f[0] = __ldg((const float4*)d.line_dinv + c0 + i);
+      f[1] = __ldg((const float4*)d.line_a + c0 + i);
+      f[2] = __ldg((const float4*)d.line_g + c0 + i);
     }
   }
   if (LINES && nlb <= kClLineList) {
@@ -1323,8 +1383,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
     if constexpr (LINES) {
       __syncthreads();
       auto fac = [&](int k0) -> LineFac {
-        const float4* fb = &s_fac[3 * (size_t)k0];
-        return LineFac{fb, fb + 1, fb + 2, 3};
+        return LineFac{s_fac, s_fac + 1, s_fac + 2, k0, 3, 1};
       };
       if (nlb <= kClLineList) {
         const int nit = s_citem[5];

@@ -1201,6 +1201,7 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
     d.line_g = t;
     AL(d.line_start, N);
     AL(d.line_len, N);
+    AL(d.line_cum, N + 1);
     AL(d.lscratch, N);
     AL(d.lblk, W);
     {
@@ -1209,6 +1210,8 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
       d.lnk = (int2*)t2;
       AL(t2, 2 * N);
       d.arow = (int2*)t2;
+      AL(t2, 2 * N);
+      d.lsort = (int2*)t2;
     }
     AL(d.line_row_flag, N);
     double** vecs[14] = {(double**)&d.kx,  (double**)&d.kr,   (double**)&d.krh,  (double**)&d.ky0, (double**)&d.ky1,
@@ -1245,6 +1248,23 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
       alist.push_back(i);
     }
   d.n_always = (int)alist.size();
+  {
+    // The grid solver splits its rows by cost, a fracture-line row counting line_w half rows more
+    // than another (its line solve follows its product).  Measured per BiCGStab iteration on GB300:
+    // long lines (mean >= 12 cells: the 2D fracture networks' segments, solved by whole warps) are
+    // best at 4 in FP32, short ones (the vertical columns of 3D fracture panels, packed several to a
+    // warp) at 1; an FP64 row's product costs about twice as much against the same FP32 line solve,
+    // so FP64 solves take half as much (rounded down).
+    std::vector<int> ids;
+    for (int i = 0; i < n; i++)
+      if (desc->line_id[i] >= 0) ids.push_back(desc->line_id[i]);
+    const size_t cells = ids.size();
+    std::sort(ids.begin(), ids.end());
+    const size_t lines = (size_t)(std::unique(ids.begin(), ids.end()) - ids.begin());
+    const bool long_lines = lines > 0 && cells >= 12 * lines;
+    d.line_w[1] = long_lines ? 4 : 1;
+    d.line_w[0] = long_lines ? 2 : 0;
+  }
   auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
     if (bytes == 0 || !src) return cudaSuccess;
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, m->stream);

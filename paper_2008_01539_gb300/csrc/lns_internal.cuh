@@ -92,8 +92,13 @@ struct Dev {
   void *line_dinv, *line_a, *line_g;
   // line_start: the marking pass's line starts (any order), then the ascending list of line-block
   // starts (after cutting); line_len[k]: rows of the line block starting at compact row k;
-  // lblk: bitset of line-block starts; lscratch: compaction scratch
-  int *line_start, *line_len, *line_row_flag, *lscratch;
+  // lblk: bitset of line-block starts; lscratch: compaction scratch; line_cum[l]: rows of the line
+  // blocks before block l of the ascending list (l = 0 .. n_lines)
+  int *line_start, *line_len, *line_row_flag, *lscratch, *line_cum;
+  int2* lsort;  // the grid solver's line blocks listed by length class, per chunk at its blocks' range
+  // extra cost of a fracture-line row in the grid solver's row split, in half rows, for FP64 [0] and
+  // FP32 [1] solves (chosen per model from its fracture lines' mean length)
+  int line_w[2];
   int2* lnk;  // per compact row: CSR entries of its couplings to the previous / next row of its line (-1)
   int2* arow;  // per compact row: first CSR entry, and degree | line flag << 24 (written by the assembly)
   uint32_t* lblk;
