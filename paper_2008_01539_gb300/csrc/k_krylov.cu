@@ -553,6 +553,12 @@ __device__ __forceinline__ void line_solve_seg(int seg, int k0, int len, const L
   }
 }
 
+// Systems of more rows than this (vectors and matrix of ~500 B a row in FP32: about the 126 MB L2)
+// prefetch each thread's next rows into L2 (see the grid solver's row loop).
+constexpr int kPrefetchRows = 200000;
+// L2 prefetch of the line holding a global address (no register result, no wait)
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // ---- grid barrier --------------------------------------------------------------------------
 // All blocks of the (cooperative, hence co-resident) launch add to one counter (zeroed before the
 // launch): block 0 adds 2^31 - (nb - 1), the others 1, so each barrier adds exactly 2^31 and the
@@ -660,9 +666,10 @@ __device__ __forceinline__ int line_lower_bound(const int* ls, int n, int k) {
   return warp_first(n, [&](int q) { return __ldg(&ls[q]) >= k; });
 }
 
-// Where the grid solver's row chunk b of nb starts.  A fracture-line row costs more than another
-// row (its line solve follows its product), so the rows are split by cost: 2 units per row plus w
-// per line row (Dev::line_w).  The cost of rows [0, k) is 2 k + w LR(k), LR(k) the line rows among
+// Where the grid solver's row chunk b of nb starts.  A fracture-line row costs a different amount
+// than another row (its line solve follows its product, its product is cheaper), so the rows are
+// split by cost: 2 units per row plus w per line row (Dev::line_w, -2 < w; w < 0 where line rows
+// are the cheaper ones).  The cost of rows [0, k) is 2 k + w LR(k), LR(k) the line rows among
 // them (line_cum at the line-block starts); chunk b starts where that cost reaches b / nb of the
 // total, and a start inside a line block moves to the nearer end of the block.  Nondecreasing in
 // b, 0 at b = 0 and n_A at b = nb.  One warp; valid in all lanes.
@@ -828,21 +835,40 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   __syncthreads();
   const int2* const ltab = nlb <= kLineList ? s_lines : d.lsort + l0;
 
-  // fn(k, ref) over this thread's rows of the chunk (one call site: one copy of the row code); the
-  // next row's reference is loaded before the current row is processed
+  // fn(k, ref) over this thread's rows of the chunk (one call site: one copy of the row code).  A
+  // software pipeline over the thread's rows: the reference of the row after next is loaded before
+  // the current row is processed, and on systems larger than L2 (kPrefetchRows) the next row's
+  // matrix entries (from its reference, loaded an iteration earlier) and the own vector entries of
+  // the row after next (pf) are prefetched into L2, so that a row waits for L2 rather than DRAM.
   auto ref_of = [&](int k, int q) -> Ref { return q < kRowsCached ? s_rref[q * kKryBlk + threadIdx.x] : global_ref(k); };
-  auto rows = [&](auto fn) {
+  auto prefetch_row = [&](const Ref& ref) {
+    if (ref.off < 0 && ref.deg > 0) {  // entries e0 .. e0 + deg - 1, all in bounds
+      const size_t e0 = (size_t)(-(ref.off + 1));
+      prefetch_l2(d.colA + e0);
+      const T* bl = &blocks[4 * e0];
+      prefetch_l2(bl);
+      prefetch_l2(bl + 4 * (size_t)(ref.deg - 1));
+    }
+  };
+  const bool big = nA > kPrefetchRows;
+  auto rows = [&](auto fn, auto pf) {
     if (kbeg >= r1) return;
     Ref ref = ref_of(kbeg, 0);
+    Ref nref = kbeg + kstep < r1 ? ref_of(kbeg + kstep, 1) : ref;
 #pragma unroll 1
     for (int k = kbeg, q = 0;; q++) {
-      const int kn = k + kstep;
-      Ref nref = ref;
-      if (kn < r1) nref = ref_of(kn, q + 1);
+      const int kn = k + kstep, knn = kn + kstep;
+      Ref nnref = nref;
+      if (knn < r1) nnref = ref_of(knn, q + 2);
+      if (big && kn < r1) {
+        prefetch_row(nref);
+        if (knn < r1) pf(knn);
+      }
       fn(k, ref);
       if (kn >= r1) break;
       k = kn;
       ref = nref;
+      nref = nnref;
     }
   };
   // after a block barrier: M^{-1} on this block's line blocks.  The warps share out items: 32 / seg
@@ -893,7 +919,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       lbuf[k - r0] = make_float2((float)bk.x, (float)bk.y);
     else
       zf[k] = bk;
-  });
+  }, [&](int) {});
   lines([&](int k0, int len, const LineFac& f, float2* buf, int seg) {
     V* const dst[1] = {zf};
     if (seg)
@@ -989,6 +1015,16 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       dot_acc(l_rr, rk.y, rk.y);
       dot_acc(l_rv, rhk.x, vv.x);
       dot_acc(l_rv, rhk.y, vv.y);
+    }, [&](int kp) {
+      prefetch_l2(&x[kp]);
+      prefetch_l2(&z[kp]);
+      prefetch_l2(&s[kp]);
+      prefetch_l2(&t[kp]);
+      prefetch_l2(&rh[kp]);
+      prefetch_l2(&tt[kp]);
+      prefetch_l2(&zf[kp]);
+      prefetch_l2(&vto[kp]);
+      prefetch_l2(&yo[kp]);
     });
     lines([&](int k0, int len, const LineFac& f, float2* buf, int seg) {
       V* const dst[1] = {vtn};
@@ -1071,6 +1107,12 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       dot_acc(l_rs, rhk.y, sk.y);
       dot_acc(l_rt, rhk.x, tk.x);
       dot_acc(l_rt, rhk.y, tk.y);
+    }, [&](int kp) {
+      prefetch_l2(&r[kp]);
+      prefetch_l2(&v[kp]);
+      prefetch_l2(&rh[kp]);
+      prefetch_l2(&vtn[kp]);
+      prefetch_l2(&rt[kp]);
     });
     lines([&](int k0, int len, const LineFac& f, float2* buf, int seg) {
       V* const dst[2] = {zf, tt};
