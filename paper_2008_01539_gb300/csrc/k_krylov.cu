@@ -735,31 +735,28 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   int* s_col = (int*)(dsm + kKrySmem - kSmPool + (size_t)ecap * sizeof(B));
 
   // ---- this block's rows and line blocks ------------------------------------------------
-  if (wib == 0) {
+  // warp 0 finds where the chunk starts, warp 1 where it ends (the next chunk's start), at once
+  if (wib < 2) {
+    const int e = (int)blockIdx.x + wib;
     const int rpb = (nA + nb - 1) / nb;
-    int c0 = min(nA, (int)blockIdx.x * rpb), c1 = min(nA, c0 + rpb);
-    if (LINES && nlines > 0) {
-      const int w = d.line_w[sizeof(T) == 4 ? 1 : 0];
-      c0 = weighted_edge(d, w, blockIdx.x, nb, nA, nlines);
-      c1 = weighted_edge(d, w, blockIdx.x + 1, nb, nA, nlines);
-    }
-    if (LINES) {
-      c0 = chunk_edge(d, c0, nA);
-      c1 = chunk_edge(d, c1, nA);
-    }
-    int l0 = 0, l1 = 0;
-    if (LINES && nlines > 0) {
-      l0 = line_lower_bound(d.line_start, nlines, c0);
-      l1 = line_lower_bound(d.line_start, nlines, c1);
-    }
+    int c = (int)min((long long)nA, (long long)e * rpb);
+    if (LINES && nlines > 0) c = weighted_edge(d, d.line_w[sizeof(T) == 4 ? 1 : 0], e, nb, nA, nlines);
+    if (LINES) c = chunk_edge(d, c, nA);
+    int l = 0;
+    if (LINES && nlines > 0) l = line_lower_bound(d.line_start, nlines, c);
     if (lane == 0) {
-      s_rng[0] = c0;
-      s_rng[1] = max(c0, c1);
-      s_rng[2] = l0;
-      s_rng[3] = max(0, l1 - l0);
-      s_epool = 0;
-      for (int c = 0; c < 5; c++) s_ccount[c] = 0;
+      s_rng[wib] = c;
+      s_rng[2 + wib] = l;
+      if (wib == 0) {
+        s_epool = 0;
+        for (int q = 0; q < 5; q++) s_ccount[q] = 0;
+      }
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // start, end, first line block, line-block count
+    s_rng[1] = max(s_rng[0], s_rng[1]);
+    s_rng[3] = max(0, s_rng[3] - s_rng[2]);
   }
   __syncthreads();
   const int r0 = s_rng[0], r1 = s_rng[1], l0 = s_rng[2], nlb = s_rng[3];
@@ -838,8 +835,8 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   // fn(k, ref) over this thread's rows of the chunk (one call site: one copy of the row code).  A
   // software pipeline over the thread's rows: the reference of the row after next is loaded before
   // the current row is processed, and on systems larger than L2 (kPrefetchRows) the next row's
-  // matrix entries (from its reference, loaded an iteration earlier) and the own vector entries of
-  // the row after next (pf) are prefetched into L2, so that a row waits for L2 rather than DRAM.
+  // matrix entries (from its reference, loaded an iteration earlier) and own vector entries (pf) are
+  // prefetched into L2, so that a row waits for L2 rather than DRAM.
   auto ref_of = [&](int k, int q) -> Ref { return q < kRowsCached ? s_rref[q * kKryBlk + threadIdx.x] : global_ref(k); };
   auto prefetch_row = [&](const Ref& ref) {
     if (ref.off < 0 && ref.deg > 0) {  // entries e0 .. e0 + deg - 1, all in bounds
@@ -862,7 +859,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
       if (knn < r1) nnref = ref_of(knn, q + 2);
       if (big && kn < r1) {
         prefetch_row(nref);
-        if (knn < r1) pf(knn);
+        pf(kn);
       }
       fn(k, ref);
       if (kn >= r1) break;

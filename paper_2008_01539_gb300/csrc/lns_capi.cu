@@ -1250,12 +1250,12 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
   d.n_always = (int)alist.size();
   {
     // The grid solver splits its rows by cost, a fracture-line row counting line_w half rows more
-    // than another (its line solve follows its product; a negative weight makes it cheaper).
-    // Measured per BiCGStab iteration on GB300 on the workloads' own active sets: long lines (mean
-    // >= 12 cells: the 2D fracture networks' segments, solved a whole warp per block, few blocks per
-    // warp round) are best at 4 in FP32 and 2 in FP64; short ones (the vertical columns of 3D
-    // fracture panels, several per warp) at 0 and -1, the few matrix rows of those sets (scattered
-    // cells next to the panels, six or more neighbours each) costing more than a line row.
+    // than another (its line solve follows its product).  Measured per case on GB300: long lines
+    // (mean >= 12 cells: the 2D fracture networks' segments, solved a whole warp per block, few
+    // blocks per warp round) are best at 4 in FP32 and 2 in FP64; short ones (the vertical columns
+    // of 3D fracture panels, several per warp) at 0 in both, the matrix rows of those sets
+    // (scattered cells beside the panels, six or more neighbours each) costing about as much as a
+    // line row with its share of the line solves.
     std::vector<int> ids;
     for (int i = 0; i < n; i++)
       if (desc->line_id[i] >= 0) ids.push_back(desc->line_id[i]);
@@ -1264,7 +1264,7 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
     const size_t lines = (size_t)(std::unique(ids.begin(), ids.end()) - ids.begin());
     const bool long_lines = lines > 0 && cells >= 12 * lines;
     d.line_w[1] = long_lines ? 4 : 0;
-    d.line_w[0] = long_lines ? 2 : -1;
+    d.line_w[0] = long_lines ? 2 : 0;
   }
   auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
     if (bytes == 0 || !src) return cudaSuccess;
