@@ -96,15 +96,15 @@ __global__ void __launch_bounds__(128) k_cell_props(Dev d, FluidK F) {
   for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 1; k < nA; k += pairs) {
     const int i = d.act[k];
     const PhaseProps q = phase_props(F, d.p[i], d.sw[i], l);
-    double4* o = (double4*)(d.cprops + 16 * (size_t)k + 8 * l);
-    o[0] = make_double4(q.b, q.rho, q.mob, q.db);
-    o[1] = make_double4(q.drho, q.dmob_dp, q.dmob_ds, 0.0);
+    double4_32a* o = (double4_32a*)(d.cprops + 16 * (size_t)k + 8 * l);
+    o[0] = make_double4_32a(q.b, q.rho, q.mob, q.db);
+    o[1] = make_double4_32a(q.drho, q.dmob_dp, q.dmob_ds, 0.0);
   }
 }
 
 __device__ __forceinline__ PhaseProps load_props(const double* cprops, int k, int l) {
-  const double4* o = (const double4*)(cprops + 16 * (size_t)k + 8 * l);
-  const double4 a = o[0], b = o[1];
+  const double4_32a* o = (const double4_32a*)(cprops + 16 * (size_t)k + 8 * l);
+  const double4_32a a = o[0], b = o[1];
   PhaseProps q;
   q.b = a.x;
   q.rho = a.y;
@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(BLK) k_assemble(Dev d, FluidK F, double p_scal
       blocks[4 * (size_t)e + 2 * l + 1] = l ? (T)m1 : (T)(m1 * p_scale);
     }
   }
-  // CNV maximum over the block, one atomic per block
+  // CNV maximum over the block, one atomic per block that had rows
+  if ((int)(blockIdx.x * (BLK / 2)) >= nA) return;
   __shared__ double sh[BLK / 32];
   for (int o = 16; o > 0; o >>= 1) cnv_max = fmax(cnv_max, __shfl_xor_sync(0xffffffffu, cnv_max, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = cnv_max;
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(BLK) k_assemble(Dev d, FluidK F, double p_scal
   if (threadIdx.x == 0) {
     double m = 0.0;
     for (int w = 0; w < BLK / 32; w++) m = fmax(m, sh[w]);
-    atomicMax(&d.ctr->cnv_bits, (unsigned long long)__double_as_longlong(m));
+    if (m > 0.0) atomicMax(&d.ctr->cnv_bits, (unsigned long long)__double_as_longlong(m));
   }
 }
 

@@ -37,6 +37,19 @@ __device__ __forceinline__ void warp_append(int* counter, int* list, bool pred, 
   list[base + __popc(m & ((1u << lane) - 1u))] = value;
 }
 
+// Set bit i of a bitset when pred holds: the lanes of a warp that set bits of the same word are
+// grouped and one of them applies their bits with one atomicOr (the rows of a warp are ascending
+// cells, so a warp touches a few words instead of issuing 32 atomics on each).
+__device__ __forceinline__ void warp_set_bit(uint32_t* words, bool pred, int i) {
+  const unsigned act = __activemask();
+  const unsigned m = __ballot_sync(act, pred);
+  if (!pred) return;
+  const int w = i >> 5;
+  const unsigned grp = __match_any_sync(m, w);
+  const unsigned bits = __reduce_or_sync(grp, 1u << (i & 31));
+  if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicOr(&words[w], bits);
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
@@ -192,23 +205,24 @@ __global__ void k_flag(Dev d, const uint32_t* __restrict__ vb, int apply, int re
     mds = fmax(mds, fabs(dsw));
     bool edge = big && vb != nullptr && bit(vb, i);
     if (big) {
-      atomicOr(&d.supp[i >> 5], 1u << (i & 31));
       if (record_stamp) d.stamp[i] = solve_id;
       any_s = 1;
     }
-    if (edge) {
-      atomicOr(&d.reach[i >> 5], 1u << (i & 31));
-      any_e = 1;
-    }
+    warp_set_bit(d.supp, big, i);
+    warp_set_bit(d.reach, edge, i);
+    any_e |= edge;
     warp_append(&d.ctr->n_frontier[0], d.fr0, edge, i);
   }
+  // blocks with no rows (small systems leave most of the grid idle) skip the reductions and the
+  // counter atomics, which all land on one line
+  if ((int)(blockIdx.x * blockDim.x) >= nA) return;
   any_s = __syncthreads_or(any_s);
   any_e = __syncthreads_or(any_e);
   mdp = block_max(mdp, sh);
   mds = block_max(mds, sh);
   if (threadIdx.x == 0) {
-    atomic_max_nonneg(&d.ctr->max_dp_bits, mdp);
-    atomic_max_nonneg(&d.ctr->max_dsw_bits, mds);
+    if (mdp > 0.0) atomic_max_nonneg(&d.ctr->max_dp_bits, mdp);
+    if (mds > 0.0) atomic_max_nonneg(&d.ctr->max_dsw_bits, mds);
     if (any_s) atomicOr(&d.ctr->any_s, 1);
     if (any_e) atomicOr(&d.ctr->any_e, 1);
   }
