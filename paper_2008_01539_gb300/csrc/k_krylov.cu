@@ -178,7 +178,9 @@ __device__ __forceinline__ T sc_t(DF a) { return (T)a.hi; }
 
 // Dot products of one thread's rows.  FP64 vectors: fused FP64 products, converted to double-float
 // (after scaling) once per phase.  FP32 vectors: exact FP32 products (p + e, e = fma(a, b, -p))
-// summed in double-float, so the FP32 path issues no FP64 instruction per row.
+// summed in double-float, so the FP32 path issues no FP64 instruction per row: the high part
+// takes each p with an exact two-sum, whose rounding error and e go to the low part (left
+// unnormalised until the block reduction: a thread sums a handful of rows).
 template <typename T>
 struct DotAcc {
   using t = double;
@@ -191,8 +193,14 @@ __device__ __forceinline__ void dot_zero(double& a) { a = 0.0; }
 __device__ __forceinline__ void dot_zero(DF& a) { a = DF{0.f, 0.f}; }
 __device__ __forceinline__ void dot_acc(double& acc, double a, double b) { acc = fma(a, b, acc); }
 __device__ __forceinline__ void dot_acc(DF& acc, float a, float b) {
-  const float p = a * b;
-  acc = df_add(acc, DF{p, fmaf(a, b, -p)});
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bv = __fsub_rn(s, acc.hi);
+  const float av = __fsub_rn(s, bv);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, av), __fsub_rn(p, bv));
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+  acc.hi = s;
 }
 __device__ __forceinline__ DF dot_df(double acc, double scale) { return df_from(acc * scale); }
 __device__ __forceinline__ DF dot_df(DF acc, float scale) { return {acc.hi * scale, acc.lo * scale}; }
@@ -411,47 +419,48 @@ __device__ __forceinline__ float2 mv2(const M2<float>& M, float2 v) {
   return make_float2(M.a * v.x + M.b * v.y, M.c * v.x + M.d * v.y);
 }
 
-// M^{-1} on one line block (len <= kLineBlockRows rows) for NR right-hand sides.  Input q of row
-// k0 + t is buf[q * bstride + t]; results are stored to dst[q][k0 + t].  Lane l holds the
-// kLineRpl consecutive rows starting at kLineRpl * l.  Each sweep composes its rows' affine maps
-// inside the lane, scans the 32 lane maps across the warp (one chain of five shuffle levels for
-// the whole block), and recomputes its rows from the value entering the lane.
-template <typename T, int NR>
-__device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, const float2* buf, int bstride,
-                                           typename V2<T>::t* const (&dst)[NR]) {
-  constexpr int R = kLineRpl;
-  const int lane = threadIdx.x & 31;
-  float2 c[R][NR];
-  M2<float> A[R], B[R];
-  // every load of the lane's rows (both sweeps) is issued first; rows at or beyond len are zero
-  // maps and zero values, so they pass nothing to the rows of the block
+// M^{-1} on line blocks for NR right-hand sides, in segments of seg lanes (4, 8, 16 or 32; one
+// block of len <= seg * RPL rows per segment, 32 / seg blocks per warp; a lane whose segment holds
+// no block has len = 0 and carries zeros).  Input q of row k0 + t is buf[q * bstride + t]; results
+// are stored to dst[q][k0 + t].  Lane t of a segment holds the RPL consecutive rows starting at
+// RPL * t.  Each sweep composes its rows' affine maps inside the lane, scans the lane maps across
+// the segment (log2(seg) shuffle levels for the whole block), and recomputes its rows from the
+// value entering the lane.  Rows at or beyond len are zero maps and zero values, so they pass
+// nothing to the rows of the block.
+template <typename T, int NR, int RPL>
+__device__ __forceinline__ void line_solve_rpl(int seg, int k0, int len, const LineFac& f, const float2* buf,
+                                               int bstride, typename V2<T>::t* const (&dst)[NR]) {
+  const int lane = threadIdx.x & 31, t = lane & (seg - 1);
+  float2 c[RPL][NR];
+  M2<float> A[RPL], B[RPL];
+  // every load of the lane's rows (both sweeps) is issued first
 #pragma unroll
-  for (int j = 0; j < R; j++) {
-    const int t = R * lane + j;
+  for (int j = 0; j < RPL; j++) {
+    const int r = RPL * t + j;
     A[j] = {0.f, 0.f, 0.f, 0.f};
     B[j] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < NR; q++) c[j][q] = make_float2(0.f, 0.f);
-    if (t < len) {
-      const int ft = f.at(t);
-      const float4 Di = f.fd[ft];
-      const float4 a4 = f.fa[ft];
-      const float4 g4 = f.fg[ft];
+    if (r < len) {
+      const int fr = f.at(r);
+      const float4 Di = f.fd[fr];
+      const float4 a4 = f.fa[fr];
+      const float4 g4 = f.fg[fr];
 #pragma unroll
-      for (int q = 0; q < NR; q++) c[j][q] = mv2({Di.x, Di.y, Di.z, Di.w}, buf[q * bstride + t]);
+      for (int q = 0; q < NR; q++) c[j][q] = mv2({Di.x, Di.y, Di.z, Di.w}, buf[q * bstride + r]);
       A[j] = {a4.x, a4.y, a4.z, a4.w};
       B[j] = {-g4.x, -g4.y, -g4.z, -g4.w};
     }
   }
-  // forward sweep w_t = Dinv_t src_t + A_t w_{t-1}: the lane's composite map, the warp scan, then
-  // the rows from the last row of the lane before
+  // forward sweep w_t = Dinv_t src_t + A_t w_{t-1}: the lane's composite map, the segment scan,
+  // then the rows from the last row of the lane before
   {
     M2<float> M = A[0];
     float2 cl[NR];
 #pragma unroll
     for (int q = 0; q < NR; q++) cl[q] = c[0][q];
 #pragma unroll
-    for (int j = 1; j < R; j++) {
+    for (int j = 1; j < RPL; j++) {
 #pragma unroll
       for (int q = 0; q < NR; q++) {
         const float2 u = mv2(A[j], cl[q]);
@@ -459,15 +468,15 @@ __device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, co
       }
       M = mm(A[j], M);
     }
-    scan_fwd<NR>(cl, M, lane);
+    scan_fwd<NR>(cl, M, lane, seg);
 #pragma unroll
     for (int q = 0; q < NR; q++) {
       float2 w;
       w.x = __shfl_up_sync(0xffffffffu, cl[q].x, 1);
       w.y = __shfl_up_sync(0xffffffffu, cl[q].y, 1);
-      if (lane == 0) w = make_float2(0.f, 0.f);
+      if (t == 0) w = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < R; j++) {
+      for (int j = 0; j < RPL; j++) {
         const float2 u = mv2(A[j], w);
         w = make_float2(u.x + c[j][q].x, u.y + c[j][q].y);
         c[j][q] = w;
@@ -476,12 +485,12 @@ __device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, co
   }
   // backward sweep z_t = w_t - G_t z_{t+1}, mirrored
   {
-    M2<float> M = B[R - 1];
+    M2<float> M = B[RPL - 1];
     float2 cl[NR];
 #pragma unroll
-    for (int q = 0; q < NR; q++) cl[q] = c[R - 1][q];
+    for (int q = 0; q < NR; q++) cl[q] = c[RPL - 1][q];
 #pragma unroll
-    for (int j = R - 2; j >= 0; j--) {
+    for (int j = RPL - 2; j >= 0; j--) {
 #pragma unroll
       for (int q = 0; q < NR; q++) {
         const float2 u = mv2(B[j], cl[q]);
@@ -489,68 +498,48 @@ __device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, co
       }
       M = mm(B[j], M);
     }
-    scan_bwd<NR>(cl, M, lane);
+    scan_bwd<NR>(cl, M, lane, seg);
 #pragma unroll
     for (int q = 0; q < NR; q++) {
       float2 z;
       z.x = __shfl_down_sync(0xffffffffu, cl[q].x, 1);
       z.y = __shfl_down_sync(0xffffffffu, cl[q].y, 1);
-      if (lane == 31) z = make_float2(0.f, 0.f);
+      if (t == seg - 1) z = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = R - 1; j >= 0; j--) {
+      for (int j = RPL - 1; j >= 0; j--) {
         const float2 u = mv2(B[j], z);
         z = make_float2(u.x + c[j][q].x, u.y + c[j][q].y);
-        const int t = R * lane + j;
-        if (t < len) dst[q][k0 + t] = mk<T>((T)z.x, (T)z.y);
+        const int r = RPL * t + j;
+        if (r < len) dst[q][k0 + r] = mk<T>((T)z.x, (T)z.y);
       }
     }
   }
 }
 
-// M^{-1} on short line blocks packed into segments of `seg` lanes (4, 8, 16 or 32; a line block of
-// len <= seg rows per segment, 32 / seg blocks per warp): the same two scans, confined to the
-// segment, so one round of loads and log2(seg) shuffle levels per sweep solve them all.  A lane
-// whose segment holds no block (len = 0) carries zeros.
+// a whole warp on one block of up to kLineBlockRows rows (kLineRpl rows per lane)
+template <typename T, int NR>
+__device__ __forceinline__ void line_solve(int k0, int len, const LineFac& f, const float2* buf, int bstride,
+                                           typename V2<T>::t* const (&dst)[NR]) {
+  line_solve_rpl<T, NR, kLineRpl>(32, k0, len, f, buf, bstride, dst);
+}
+
+// short blocks, two rows per lane, 32 / seg of them per warp
+template <typename T, int NR>
+__device__ __forceinline__ void line_solve_seg(int seg, int k0, int len, const LineFac& f, const float2* buf,
+                                               int bstride, typename V2<T>::t* const (&dst)[NR]) {
+  line_solve_rpl<T, NR, 2>(seg, k0, len, f, buf, bstride, dst);
+}
+
 // FP32 solves stop when ||r|| has not halved for this many iterations (see the phase-1 test)
 #ifndef LNS_STAG_ITERS
 #define LNS_STAG_ITERS 40
 #endif
 constexpr int kStagIters = LNS_STAG_ITERS;
 
-// length class of a line block: 0..3 for len <= 4, 8, 16, 32 (segments of 4 << c lanes), 4 above
+// length class of a line block: 0..3 for len <= 8, 16, 32, 64 (segments of 4 << c lanes, two rows
+// per lane), 4 above (a whole warp)
 __device__ __forceinline__ int line_class(int len) {
-  return len <= 4 ? 0 : (len <= 8 ? 1 : (len <= 16 ? 2 : (len <= 32 ? 3 : 4)));
-}
-
-template <typename T, int NR>
-__device__ __forceinline__ void line_solve_seg(int seg, int k0, int len, const LineFac& f, const float2* buf,
-                                               int bstride, typename V2<T>::t* const (&dst)[NR]) {
-  const int lane = threadIdx.x & 31, t = lane & (seg - 1);
-  const bool on = t < len;
-  float2 w[NR];
-  M2<float> P = {0.f, 0.f, 0.f, 0.f};
-  float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int q = 0; q < NR; q++) w[q] = make_float2(0.f, 0.f);
-  if (on) {  // every load of the row (both sweeps) is issued before the first scan
-    const int ft = f.at(t);
-    const float4 Di = f.fd[ft];
-    const float4 a4 = f.fa[ft];
-    g4 = f.fg[ft];
-#pragma unroll
-    for (int q = 0; q < NR; q++) {
-      const float2 u = buf[q * bstride + t];
-      w[q] = make_float2(Di.x * u.x + Di.y * u.y, Di.z * u.x + Di.w * u.y);
-    }
-    P = {a4.x, a4.y, a4.z, a4.w};
-  }
-  scan_fwd<NR>(w, P, lane, seg);
-  P = {-g4.x, -g4.y, -g4.z, -g4.w};
-  scan_bwd<NR>(w, P, lane, seg);
-  if (on) {
-#pragma unroll
-    for (int q = 0; q < NR; q++) dst[q][k0 + t] = mk<T>((T)w[q].x, (T)w[q].y);
-  }
+  return len <= 8 ? 0 : (len <= 16 ? 1 : (len <= 32 ? 2 : (len <= 64 ? 3 : 4)));
 }
 
 // Systems of more rows than this (vectors and matrix of ~500 B a row in FP32: about the 126 MB L2)
@@ -558,6 +547,37 @@ __device__ __forceinline__ void line_solve_seg(int seg, int k0, int len, const L
 constexpr int kPrefetchRows = 200000;
 // L2 prefetch of the line holding a global address (no register result, no wait)
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// row_product over a staged row whose neighbours are given by the shared::cluster address of their
+// entry in the owner CTA's first vector array (0xffffffff: an inactive column), so that no owner
+// search or address map is repeated in the iterations.
+template <typename T, typename LoadF, typename CombF>
+__device__ __forceinline__ typename V2<T>::t row_product_cla(const unsigned* adr, const B4<T>* blk, int deg,
+                                                             typename V2<T>::t own, LoadF load, CombF comb) {
+  using V = typename V2<T>::t;
+  using Raw = decltype(load(0u));
+  constexpr int kBatch = sizeof(T) == 8 ? 2 : 4;
+  V acc0 = own, acc1 = mk<T>(0, 0);
+  for (int j = 0; j < deg; j += kBatch) {
+    unsigned c[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; q++) c[q] = j + q < deg ? adr[j + q] : 0xffffffffu;
+    Raw raw[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; q++)
+      if (c[q] != 0xffffffffu) raw[q] = load(c[q]);
+#pragma unroll
+    for (int q = 0; q < kBatch; q++)
+      if (c[q] != 0xffffffffu) {
+        const V xv = comb(raw[q]);
+        const B4<T> bq = blk[j + q];
+        V& acc = (q & 1) ? acc1 : acc0;
+        acc.x += bq.a * xv.x + bq.b * xv.y;
+        acc.y += bq.c * xv.x + bq.d * xv.y;
+      }
+  }
+  return mk<T>(acc0.x + acc1.x, acc0.y + acc1.y);
+}
 
 // ---- grid barrier --------------------------------------------------------------------------
 // All blocks of the (cooperative, hence co-resident) launch add to one counter (zeroed before the
@@ -701,7 +721,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   __shared__ int s_ctl;       // 0 continue, 1 stop
   __shared__ int s_epool;     // next free entry of the shared-memory pool
   __shared__ int s_rng[4];    // chunk start, chunk end, first line block, line-block count
-  // line blocks by length class c: len <= 4 << c in segments (c < 4), longer ones one per warp (c = 4)
+  // line blocks by length class c: len <= 8 << c in segments (c < 4), longer ones one per warp (c = 4)
   __shared__ int s_ccount[5], s_coff[5], s_cfill[5], s_citem[6];
   const int nA = d.ctr->n_active;
   if (nA <= cl_cap && *d.fault != 1) return;  // the cluster solver takes this system (uniform exit)
@@ -1211,20 +1231,32 @@ __device__ __forceinline__ unsigned cl_size() {
 __device__ __forceinline__ void cl_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// (mapa is a pure address map, so the compiler may schedule it freely)
 __device__ __forceinline__ unsigned cl_addr(const void* local, unsigned rank) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(local);
   unsigned r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
   return r;
 }
+// A vector entry at a shared::cluster address (this CTA's or another's).
+__device__ __forceinline__ void ld_cla(unsigned a, float2& v) {
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+}
+__device__ __forceinline__ void ld_cla(unsigned a, double2& v) {
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+}
+// A neighbour's vector entry in another CTA's shared memory.  Within a phase no thread writes what
+// these loads read (that happened before the last cluster barrier, whose asm orders them), so they
+// carry no memory clobber: the compiler may issue a row's loads ahead of the previous row's
+// arithmetic and stores.
 __device__ __forceinline__ float2 ld_cl(const float2* local, unsigned rank) {
   float2 v;
-  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(cl_addr(local, rank)) : "memory");
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(cl_addr(local, rank)));
   return v;
 }
 __device__ __forceinline__ double2 ld_cl(const double2* local, unsigned rank) {
   double2 v;
-  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(cl_addr(local, rank)) : "memory");
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(cl_addr(local, rank)));
   return v;
 }
 __device__ __forceinline__ double ld_cl(const double* local, unsigned rank) {
@@ -1355,10 +1387,13 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
     }
   }
   // owner CTA of compact row j: the last c with s_cb[c] <= j
+  // (binary search over the C <= 16 ascending boundaries: four dependent shared loads instead of
+  // fifteen compares, on the row phases' instruction-bound path)
   auto owner = [&](int j) -> unsigned {
     unsigned o = 0;
 #pragma unroll
-    for (int c = 1; c < kClMaxCtas; c++) o += (c < (int)C && s_cb[c] <= j) ? 1u : 0u;
+    for (unsigned step = kClMaxCtas / 2; step > 0; step >>= 1)
+      if (o + step < C && s_cb[o + step] <= j) o += step;
     return o;
   };
   auto global_ref = [&](int k) -> Ref {
@@ -1371,16 +1406,26 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
     if (off + g.deg > ecap) return g;
     const int e0 = -(g.off + 1);
     for (int j = 0; j < g.deg; j++) {
-      s_col[off + j] = __ldg(&d.colA[e0 + j]);
+      const int col = __ldg(&d.colA[e0 + j]);
+      unsigned a = 0xffffffffu;
+      if (col >= 0) {
+        const unsigned o = owner(col);
+        a = cl_addr(&s_vec[col - s_cb[o]], o);
+      }
+      s_col[off + j] = (int)a;
       s_blk[off + j] = *(const B*)&blocks[4 * (size_t)(e0 + j)];
     }
     return {off, g.deg, g.line};
   };
-  auto product = [&](const Ref& ref, const V& own, auto load, auto comb) -> V {
-    if (ref.off >= 0) return row_product<T>(s_col + ref.off, s_blk + ref.off, ref.deg, own, load, comb);
+  // staged rows read their neighbours by address (loada), the others by compact row (load)
+  auto product = [&](const Ref& ref, const V& own, auto loada, auto load, auto comb) -> V {
+    if (ref.off >= 0)
+      return row_product_cla<T>((const unsigned*)s_col + ref.off, s_blk + ref.off, ref.deg, own, loada, comb);
     const size_t e0 = (size_t)(-(ref.off + 1));
     return row_product<T>(d.colA + e0, (const B*)&blocks[4 * e0], ref.deg, own, load, comb);
   };
+  // byte offset of a vector array from the first one (the staged addresses point into that one)
+  auto voff = [&](const V* arr) -> unsigned { return (unsigned)((const char*)arr - (const char*)s_vec); };
   __syncthreads();
   const int nlb = LINES ? s_nlb : 0, l0 = LINES ? s_l0 : 0;
   for (int i = threadIdx.x; i < nr; i += kClThreads) {
@@ -1552,10 +1597,22 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
     struct Raw1 {
       V tt, zf, vt, y;
     };
+    // a neighbour in this CTA is read from its own shared memory (a distributed-shared-memory
+    // request costs far more than a local load, and most neighbours are local)
     auto ld1 = [&](int j) {
       const unsigned o = owner(j);
       const int i = j - s_cb[o];
+      if (o == me) return Raw1{stt[i], szf[i], vto[i], yo[i]};
       return Raw1{ld_cl(&stt[i], o), ld_cl(&szf[i], o), ld_cl(&vto[i], o), ld_cl(&yo[i], o)};
+    };
+    const unsigned f_tt = voff(stt), f_zf = voff(szf), f_vt = voff(vto), f_y = voff(yo);
+    auto ld1a = [&](unsigned a) {
+      Raw1 r;
+      ld_cla(a + f_tt, r.tt);
+      ld_cla(a + f_zf, r.zf);
+      ld_cla(a + f_vt, r.vt);
+      ld_cla(a + f_y, r.y);
+      return r;
     };
     auto rt_of = [&](const Raw1& a) { return axpy(nom, a.tt, a.zf); };
     auto y_of = [&](const Raw1& a, const V& rtc) { return axpy(beta, axpy(nom, a.vt, a.y), rtc); };
@@ -1570,7 +1627,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
         const Raw1 own{stt[i], szf[i], vto[i], yo[i]};
         const V rtk = rt_of(own);
         const V ynk = y_of(own, rtk);
-        const V vv = product(oref[q], ynk, ld1, cb1);
+        const V vv = product(oref[q], ynk, ld1a, ld1, cb1);
         const V rk = axpy(nom, ot[q], os[q]);
         ox[q] = mk<T>(ox[q].x + alp * own.y.x + omp * oz[q].x, ox[q].y + alp * own.y.y + omp * oz[q].y);
         o_r[q] = rk;
@@ -1630,7 +1687,15 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
     auto ld2 = [&](int j) {
       const unsigned o = owner(j);
       const int i = j - s_cb[o];
+      if (o == me) return V2pair<V>{vtn[i], srt[i]};
       return V2pair<V>{ld_cl(&vtn[i], o), ld_cl(&srt[i], o)};
+    };
+    const unsigned f_vn = voff(vtn), f_rt = voff(srt);
+    auto ld2a = [&](unsigned a) {
+      V2pair<V> r;
+      ld_cla(a + f_vn, r.a);
+      ld_cla(a + f_rt, r.b);
+      return r;
     };
     auto cb2 = [&](const V2pair<V>& a) { return axpy(nal, a.a, a.b); };
     Acc l_ts, l_tt, l_rs, l_rt;
@@ -1643,7 +1708,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
       const int i = threadIdx.x + q * kClThreads;
       if (i < nr) {
         const V zk = cb2(V2pair<V>{vtn[i], srt[i]});
-        const V tk = product(oref[q], zk, ld2, cb2);
+        const V tk = product(oref[q], zk, ld2a, ld2, cb2);
         const V sk = axpy(nal, ov[q], o_r[q]);
         os[q] = sk;
         oz[q] = zk;
