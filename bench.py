@@ -83,6 +83,8 @@ def parse():
                          "(--kernel-class, its 0-based --launch-index) and the --iteration-log of the same case")
     ap.add_argument("--kernel-class", default="bicgstab", help="kernel class of --write-traffic")
     ap.add_argument("--launch-index", type=int, default=0, help="launch of the class captured (ncu -s)")
+    ap.add_argument("--solver", choices=["grid", "cluster"], default=None,
+                    help="--write-traffic: the solver the captured launch ran (checked against the log)")
     ap.add_argument("--krylov-rtol", type=float, default=None,
                     help="BiCGStab relative tolerance (default: the library's)")
     return ap.parse_args()
@@ -643,6 +645,8 @@ def write_traffic(args):
     its = [json.loads(x) for x in open(args.iteration_log)]
     launches = [r for r in its if r["kernels"].get(args.kernel_class, {}).get("launches", 0) > 0]
     rec = launches[args.launch_index]
+    if args.solver and rec.get("krylov_solver") != {"cluster": 1, "grid": 2}[args.solver]:
+        raise SystemExit(f"iteration {args.launch_index} was not solved by the {args.solver} solver")
     alg = rec["kernels"][args.kernel_class]["bytes"]
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -674,7 +678,7 @@ def iteration_log(model, case, opts, path):
                 kt = {k["name"]: {"launches": k["launches"], "ms": k["total_ms"], "bytes": k["bytes"]}
                       for k in model.lns_kernel_times()}
                 f.write(json.dumps({"step": step, "n_active": st["n_active"], "krylov_iters": st["krylov_iters"],
-                                    "kernels": kt}) + "\n")
+                                    "krylov_solver": st["krylov_solver"], "kernels": kt}) + "\n")
                 if st["step_done"]:
                     break
     model.set_options(opts)

@@ -57,7 +57,8 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
 // ---------------------------------------------------------------------------------------
 // Compaction of a bitset: ascending list of set cells and the inverse map.
 // Pass 1: popcount per block of kBlk words.  Pass 2: each block sums the counts of the
-// blocks before it, scans its words and writes list[] and inv[].
+// blocks before it, scans its words and writes list[] and inv[].  Small bitsets take pass 2 alone,
+// each block counting the earlier words itself.
 // ---------------------------------------------------------------------------------------
 __global__ void k_compact_count(const uint32_t* __restrict__ bits, int W, int* __restrict__ blk_sums) {
   int w = blockIdx.x * kBlk + threadIdx.x;
@@ -73,13 +74,23 @@ __global__ void k_compact_count(const uint32_t* __restrict__ bits, int W, int* _
   }
 }
 
+// FUSED: one pass for small bitsets (kFuseWords words at most): each block counts the set bits of
+// all the words before its own itself (at most kFuseWords / kBlk loads a thread), so the counting
+// pass and its launch go away.
+constexpr int kFuseWords = 8192;
+
+template <bool FUSED>
 __global__ void k_compact_write(const uint32_t* __restrict__ bits, int W, const int* __restrict__ blk_sums,
                                 int* __restrict__ list, int* __restrict__ inv, int* __restrict__ count_out) {
   __shared__ int ws[kBlk / 32];
   __shared__ int s_off;
-  // offset of this block = sum of the counts of earlier blocks
+  // offset of this block = sum of the counts of earlier blocks (of the words before it)
   int part = 0;
-  for (int b = threadIdx.x; b < (int)blockIdx.x; b += kBlk) part += blk_sums[b];
+  if (FUSED) {
+    for (int v = threadIdx.x; v < (int)blockIdx.x * kBlk; v += kBlk) part += __popc(bits[v]);
+  } else {
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kBlk) part += blk_sums[b];
+  }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = part;
   __syncthreads();
@@ -360,10 +371,15 @@ static int set_grid(const LaunchCfg& c) { return (c.set_mult >= 1 && c.set_mult 
 cudaError_t launch_compact(const Dev& d, const uint32_t* bits, int* list, int* inv, int* count_out, LaunchCfg c) {
   int nb = words_grid(d.W);
   if (nb == 0) return cudaMemsetAsync(count_out, 0, sizeof(int), c.stream);
+  if (d.W <= kFuseWords) {
+    count_launches(1);
+    k_compact_write<true><<<nb, kBlk, 0, c.stream>>>(bits, d.W, nullptr, list, inv, count_out);
+    return cudaGetLastError();
+  }
   count_launches(1);
   k_compact_count<<<nb, kBlk, 0, c.stream>>>(bits, d.W, d.blk_sums);
   count_launches(1);
-  k_compact_write<<<nb, kBlk, 0, c.stream>>>(bits, d.W, d.blk_sums, list, inv, count_out);
+  k_compact_write<false><<<nb, kBlk, 0, c.stream>>>(bits, d.W, d.blk_sums, list, inv, count_out);
   return cudaGetLastError();
 }
 
