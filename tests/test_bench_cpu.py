@@ -36,15 +36,18 @@ def test_write_traffic_from_capture_and_iteration_log(tmp_path, monkeypatch):
                                                                                      "bytes": 1.0e6}}},
             {"step": 0, "n_active": 20, "krylov_iters": 3, "kernels": {"assemble": {"launches": 1, "ms": 0.1,
                                                                                       "bytes": 5.0}}},
-            {"step": 1, "n_active": 30, "krylov_iters": 4, "kernels": {"bicgstab": {"launches": 1, "ms": 0.2,
-                                                                                     "bytes": 4.0e6}}}]
+            {"step": 1, "n_active": 30, "krylov_iters": 4, "krylov_solver": 2,
+             "kernels": {"bicgstab": {"launches": 1, "ms": 0.2, "bytes": 4.0e6}}}]
     log.write_text("".join(json.dumps(r) + "\n" for r in recs))
     profiles = tmp_path / "profiles"
     profiles.mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "h1")
     args = type("A", (), dict(write_traffic=str(csv_path), iteration_log=str(log), kernel_class="bicgstab",
-                              launch_index=1, case="config1"))()
+                              launch_index=1, case="config1", solver="cluster"))()
+    with pytest.raises(SystemExit):  # the log says the grid solver ran that system
+        bench.write_traffic(args)
+    args.solver = "grid"
     assert bench.write_traffic(args) == 0
     out = json.load(open(profiles / "traffic.json"))
     k = out["kernels"]["bicgstab"]
