@@ -54,12 +54,15 @@ def test_forced_breakdown_is_reported():
 @pytest.mark.parametrize("mode", [1, 2])
 def test_failed_fp32_solve_is_redone_in_fp64(mode):
     """Every FP32 solve breaks down (injected); with fp64_fallback each iteration's solve is redone
-    in FP64 from the unchanged state and set, so the run equals an FP64 run bit for bit."""
+    in FP64 from the unchanged state and set, so the run equals an FP64 run bit for bit (both
+    models on the same solver choice: the tuning cache of each precision class may pick another)."""
     case = cg.config0()
     base = dict(mode=mode, krylov_rtol=1e-6)
     m = lns.Model(case, lns.Options(**base, krylov_fp32=1))
+    m.lns_set_tuning(cluster_max_rows=-1)
     m.lns_debug_fault(3)
     ref = lns.Model(case, lns.Options(**base))
+    ref.lns_set_tuning(cluster_max_rows=-1)
     ref.lns_debug_fault(3)  # affects FP32 solves only: the FP64 run is the plain one
     for dt in case.dt_schedule[:3]:
         st = m.lns_timestep(float(dt))
