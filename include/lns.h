@@ -314,7 +314,8 @@ lns_status lns_set_support(lns_model* model, const uint32_t* bits);
  * code 1 makes the solver's first grid barrier miss one block's arrival, so every bounded wait of
  * that barrier runs out (2 s) and the next solve returns LNS_ETIMEOUT with the context intact;
  * code 2 starts BiCGStab with rho = 0, a breakdown (LNS_EKRYLOV); code 3 does so in FP32 solves
- * only (exercises fp64_fallback); 0 clears the fault. */
+ * only (exercises fp64_fallback); code 4 stops FP32 solves after their first iteration as if
+ * they had stalled (exercises the FP64 redo that starts from the FP32 iterate); 0 clears it. */
 lns_status lns_debug_fault(lns_model* model, int32_t code);
 /* Move the model to another CUDA stream (after the work queued on the current one finishes). */
 lns_status lns_set_stream(lns_model* model, void* cuda_stream);

@@ -273,8 +273,9 @@ __device__ __forceinline__ void grid_sum(const double* part, int slot, int nb, D
     for (int q = 0; q < NV; q++) out[q] = df_add(out[q], df_shfl_xor(out[q], o));
 }
 
-// ||b||^2 (once per solve, before the scale is known): FP64 block partial and grid sum.
-__device__ __forceinline__ void block_store_f64(double a, double* sh, double* part, int nb) {
+// ||b||^2 and ||r_0||^2 (once per solve, before the scale is known): FP64 block partial in a slot
+// and its grid sum.
+__device__ __forceinline__ void block_store_f64(double a, double* sh, double* part, int nb, int slot) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   if (lane == 0) sh[w] = a;
@@ -282,14 +283,14 @@ __device__ __forceinline__ void block_store_f64(double a, double* sh, double* pa
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int k = 0; k < kWarps; k++) s += sh[k];
-    part[(size_t)kSlotInit * nb + blockIdx.x] = s;
+    part[(size_t)slot * nb + blockIdx.x] = s;
   }
 }
 
-__device__ __forceinline__ double grid_sum_f64(const double* part, int nb) {
+__device__ __forceinline__ double grid_sum_f64(const double* part, int nb, int slot) {
   double a = 0.0;
   if (threadIdx.x < 32) {
-    for (int k = threadIdx.x; k < nb; k += 32) a += __ldcg(&part[(size_t)kSlotInit * nb + k]);
+    for (int k = threadIdx.x; k < nb; k += 32) a += __ldcg(&part[(size_t)slot * nb + k]);
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   }
   return a;
@@ -918,24 +919,39 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
     }
   };
 
-  // ---- initialisation: x = z = t = t~ = y_0 = v~_0 = 0, s = r^ = b, z^ = M^{-1} b -------------
-  double l_bb = 0.0;
+  // ---- initialisation: x = x_0 (0, or with krylov_warm the FP32 iterate in kx0), z = t = t~ =
+  // y_0 = v~_0 = 0, s = r^ = r_0 = b - A x_0, z^ = M^{-1} r_0 ----------------------------------
+  const bool warm = d.krylov_warm != 0;
+  auto x0_of = [&](int j) -> V {
+    const float2 f = ((const float2*)d.kx0)[j];
+    return mk<T>((T)f.x, (T)f.y);
+  };
+  double l_bb = 0.0, l_rr0 = 0.0;
   rows([&](int k, const Ref& ref) {
     const V bk = b[k];
     const V o = mk<T>(0, 0);
-    x[k] = o;
+    V rk = bk;
+    if (warm) {
+      const V xk = x0_of(k);
+      const V ax = product(ref, xk, x0_of, [](const V& u) { return u; });
+      rk = mk<T>(bk.x - ax.x, bk.y - ax.y);
+      x[k] = xk;
+    } else {
+      x[k] = o;
+    }
     z[k] = o;
     t[k] = o;
     tt[k] = o;
     y0[k] = o;
     vt0[k] = o;
-    s[k] = bk;
-    rh[k] = bk;
+    s[k] = rk;
+    rh[k] = rk;
     l_bb += (double)bk.x * bk.x + (double)bk.y * bk.y;
+    l_rr0 += (double)rk.x * rk.x + (double)rk.y * rk.y;
     if (LINES && ref.line)
-      lbuf[k - r0] = make_float2((float)bk.x, (float)bk.y);
+      lbuf[k - r0] = make_float2((float)rk.x, (float)rk.y);
     else
-      zf[k] = bk;
+      zf[k] = rk;
   }, [&](int) {});
   lines([&](int k0, int len, const LineFac& f, float2* buf, int seg) {
     V* const dst[1] = {zf};
@@ -947,17 +963,26 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   // injected faults (failure tests): 1 = block 0 never arrives at this barrier, 2 = rho_1 = 0,
   // 3 = rho_1 = 0 in FP32 solves only
   const int fault = *d.fault;
-  block_store_f64(l_bb, sh, part, nb);
+  block_store_f64(l_bb, sh, part, nb, kSlotInit);
+  if (warm) {
+    __syncthreads();
+    block_store_f64(l_rr0, sh, part, nb, kSlotInit + 1);
+  }
   grid_barrier(d.ctr, nb, ++bar_gen, fault == 1 && blockIdx.x == 0);
   const bool timed_out = *(volatile int*)&d.ctr->bar_timeout;
-  // ||b||^2 is summed by warp 0; every thread scales its dot products by the same power of two
-  __shared__ double s_bbv;
+  // ||b||^2 (and ||r_0||^2) are summed by warp 0; every thread scales its dot products by the same
+  // power of two
+  __shared__ double s_bbv, s_rrv;
   {
-    const double bb0 = grid_sum_f64(part, nb);
-    if (threadIdx.x == 0) s_bbv = bb0;
+    const double bb0 = grid_sum_f64(part, nb, kSlotInit);
+    const double rr0 = warm ? grid_sum_f64(part, nb, kSlotInit + 1) : bb0;
+    if (threadIdx.x == 0) {
+      s_bbv = bb0;
+      s_rrv = rr0;
+    }
   }
   __syncthreads();
-  const double bb = s_bbv;
+  const double bb = s_bbv, rr0 = s_rrv;
   // Dots are scaled by an exact power of two near 1/bb before they are carried in double-float,
   // so that the reductions and the scalar arithmetic stay far from the FP32 range limits (the
   // scalars are ratios of dots and do not depend on the scale).  2^(1023 - E) with E the unbiased
@@ -980,9 +1005,9 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   sc_zero(rr_ref);
   int it_ref = 0;  // FP32 stagnation test: iteration at which ||r||^2 last fell below rr_ref / 4
   if (threadIdx.x == 0) {  // thread 0 tracks the scalars
-    rho = sc_from(df_from(fault == 2 || (fault == 3 && sizeof(T) == 4) ? 0.0 : bb * dscale), S{});
+    rho = sc_from(df_from(fault == 2 || (fault == 3 && sizeof(T) == 4) ? 0.0 : rr0 * dscale), S{});
     stop2 = sc_from(df_from(rtol * rtol * bb * dscale), S{});
-    rr_ref = sc_from(df_from(bb * dscale), S{});
+    rr_ref = sc_from(df_from(rr0 * dscale), S{});
     sc_zero(s_sc[0]);  // beta_1
     sc_zero(s_sc[1]);  // alpha_0
     sc_zero(s_sc[2]);  // omega_0
@@ -1071,7 +1096,7 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
         } else if (sc_le(rr_last, stop2)) {
           s_ctl = 1;
           status = 0;
-        } else if (it > maxit) {
+        } else if (it > maxit || (!kF64 && fault == 4 && it > 1)) {  // (4: an injected stall)
           s_ctl = 1;
           status = 1;
         } else if (!kF64 && it - it_ref > kStagIters) {
@@ -1324,8 +1349,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
   const int nA = d.ctr->n_active;
   if (nA > cap || *d.fault == 1) return;  // the grid solver takes this system (uniform exit)
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ double sh[kClWarps];
-  __shared__ double s_bb;
+  __shared__ double sh[kClWarps], sh2[kClWarps];
+  __shared__ double s_bb, s_rr0;
   __shared__ DF s_df[4 * kClWarps];
   __shared__ float2 s_part[2][4];  // this CTA's partial sums: [0] phase 1 / init, [1] phase 2
   using S = std::conditional_t<kF64, double, DF>;
@@ -1500,7 +1525,13 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
   V ox[RPT], o_r[RPT], orh[RPT], ov[RPT], os[RPT], ot[RPT], oz[RPT];
   Ref oref[RPT];
   const V zero = mk<T>(0, 0);
-  double l_bb = 0.0;
+  // x_0 = 0, or with krylov_warm the FP32 iterate in kx0 (r_0 = b - A x_0 over the global rows)
+  const bool warm = d.krylov_warm != 0;
+  auto x0_of = [&](int j) -> V {
+    const float2 f = ((const float2*)d.kx0)[j];
+    return mk<T>((T)f.x, (T)f.y);
+  };
+  double l_bb = 0.0, l_rr0 = 0.0;
 #pragma unroll
   for (int q = 0; q < RPT; q++) {
     const int i = threadIdx.x + q * kClThreads;
@@ -1514,17 +1545,27 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
     oref[q] = Ref{0, 0, 0};
     if (i < nr) {
       const V bk = b[c0 + i];
+      V rk = bk;
+      if (warm) {
+        const Ref g = global_ref(c0 + i);
+        const size_t e0 = (size_t)(-(g.off + 1));
+        ox[q] = x0_of(c0 + i);
+        const V ax = row_product<T>(d.colA + e0, (const B*)&blocks[4 * e0], g.deg, ox[q], x0_of,
+                                    [](const V& u) { return u; });
+        rk = mk<T>(bk.x - ax.x, bk.y - ax.y);
+      }
       oref[q] = s_ref[i];
-      os[q] = bk;
-      orh[q] = bk;
+      os[q] = rk;
+      orh[q] = rk;
       l_bb += (double)bk.x * bk.x + (double)bk.y * bk.y;
+      l_rr0 += (double)rk.x * rk.x + (double)rk.y * rk.y;
       stt[i] = zero;
       sy[0][i] = zero;
       svt[0][i] = zero;
       if (LINES && oref[q].line)
-        lbuf[i] = make_float2((float)bk.x, (float)bk.y);
+        lbuf[i] = make_float2((float)rk.x, (float)rk.y);
       else
-        szf[i] = bk;
+        szf[i] = rk;
     }
   }
   lines([&](int k0, int len, const LineFac& f, const float2* buf, int seg) {
@@ -1534,27 +1575,44 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
     else
       line_solve<T, 1>(k0, len, f, buf, R, dst);
   });
-  // ||b||^2 over the cluster in FP64
+  // ||b||^2 (and ||r_0||^2) over the cluster in FP64
   {
-    double a = l_bb;
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) sh[wib] = a;
+    double a = l_bb, a2 = l_rr0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (lane == 0) {
+      sh[wib] = a;
+      sh2[wib] = a2;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int k = 0; k < kClWarps; k++) t += sh[k];
+      double t = 0.0, t2 = 0.0;
+      for (int k = 0; k < kClWarps; k++) {
+        t += sh[k];
+        t2 += sh2[k];
+      }
       s_bb = t;
+      s_rr0 = t2;
     }
   }
   cl_sync();
-  __shared__ double s_bbv;  // the cluster sum, read by every thread (all scale their dots alike)
+  __shared__ double s_bbv, s_rrv;  // the cluster sums, read by every thread (all scale their dots alike)
   if (threadIdx.x < 32) {
     double a = threadIdx.x < C ? ld_cl(&s_bb, threadIdx.x) : 0.0;
-    for (int o = kClMaxCtas / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (threadIdx.x == 0) s_bbv = a;
+    double a2 = warm && threadIdx.x < C ? ld_cl(&s_rr0, threadIdx.x) : 0.0;
+    for (int o = kClMaxCtas / 2; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (threadIdx.x == 0) {
+      s_bbv = a;
+      s_rrv = warm ? a2 : a;
+    }
   }
   __syncthreads();
-  const double bb = s_bbv;
+  const double bb = s_bbv, rr0 = s_rrv;
   long long eb = bb > 0.0 ? ((__double_as_longlong(bb) >> 52) & 0x7ff) - 1023 : 0;
   eb = eb < -126 ? -126 : (eb > 126 ? 126 : eb);
   const double dscale = __longlong_as_double((1023 - eb) << 52);
@@ -1574,9 +1632,9 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
   sc_zero(rr_ref);
   int it_ref = 0;
   if (threadIdx.x == 0) {
-    rho = sc_from(df_from(fault == 2 || (fault == 3 && sizeof(T) == 4) ? 0.0 : bb * dscale), S{});
+    rho = sc_from(df_from(fault == 2 || (fault == 3 && sizeof(T) == 4) ? 0.0 : rr0 * dscale), S{});
     stop2 = sc_from(df_from(rtol * rtol * bb * dscale), S{});
-    rr_ref = sc_from(df_from(bb * dscale), S{});
+    rr_ref = sc_from(df_from(rr0 * dscale), S{});
     sc_zero(s_sc[0]);
     sc_zero(s_sc[1]);
     sc_zero(s_sc[2]);
@@ -1665,7 +1723,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
         if (sc_le(rr_last, stop2)) {
           s_ctl = 1;
           status = 0;
-        } else if (it > maxit) {
+        } else if (it > maxit || (!kF64 && fault == 4 && it > 1)) {
           s_ctl = 1;
           status = 1;
         } else if (!kF64 && it - it_ref > kStagIters) {

@@ -518,11 +518,20 @@ bool wants_fp64_retry(const lns_model* m) {
   return m->o.krylov_fp32 && m->o.fp64_fallback && h.solve_failed && h.krylov_status != 3;
 }
 
-// Run `body` with the FP64 Krylov path (direct launches), then restore the FP32 option.
+// Run `body` with the FP64 Krylov path (direct launches), then restore the FP32 option.  The redo
+// solves the same system (same state and set); after a stop above krylov_fail_rtol (stagnation or
+// krylov_maxit, a finite iterate) its BiCGStab starts from the FP32 iterate (kept in kx0) instead of
+// zero, and after a breakdown from zero (the plain FP64 solve, bit for bit).
 template <typename F>
 lns_status with_fp64_krylov(lns_model* m, F body) {
+  Dev& d = m->d;
+  const size_t nA = (size_t)std::max(d.ctr_h->n_active, 0);
+  const bool warm = d.ctr_h->krylov_status == 1 && std::isfinite(d.ctr_h->krylov_relres) && nA > 0;
+  if (warm) CK(cudaMemcpyAsync(d.kx0, d.kx, nA * 2 * sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
   m->o.krylov_fp32 = 0;
+  d.krylov_warm = warm ? 1 : 0;
   const lns_status r = body();
+  d.krylov_warm = 0;
   m->o.krylov_fp32 = 1;
   return r;
 }
@@ -1219,6 +1228,11 @@ lns_status lns_model_create(const lns_model_desc* desc, const lns_options* opts,
                          (double**)&d.kvt1, (double**)&d.krt, (double**)&d.kzf, (double**)&d.ktt};
     for (auto v : vecs) AL(*v, N * 2);
     AL(d.kls, N * 2);
+    {
+      float* t3;
+      AL(t3, N * 2);
+      d.kx0 = t3;
+    }
     AL(d.partials, (size_t)8 * 4 * m->sms + 64);
   }
   AL(d.ctr, 1);
@@ -1404,7 +1418,7 @@ lns_status lns_set_support(lns_model* m, const uint32_t* bits) {
 
 lns_status lns_debug_fault(lns_model* m, int32_t code) {
   TRY(check_model(m));
-  if (code < 0 || code > 3) return fail(LNS_EINVAL, "fault code must be 0..3");
+  if (code < 0 || code > 4) return fail(LNS_EINVAL, "fault code must be 0..4");
   CK(cudaMemcpyAsync(m->d.fault, &code, sizeof(int), cudaMemcpyHostToDevice, m->stream));
   m->fault_h = code;
   return sync(m);

@@ -105,6 +105,10 @@ struct Dev {
   // Krylov vectors
   void *kx, *kr, *krh, *ky0, *ky1, *kv, *ks, *kt, *kz, *kvt0, *kvt1, *krt, *kzf, *ktt;
   double* kls;  // 2n: line-solve inputs of chunks too long for shared memory
+  // the FP32 iterate of a failed solve (float2 per compact row), which the FP64 redo starts from
+  // when krylov_warm is set (0: every solve starts from x = 0)
+  void* kx0;
+  int krylov_warm;
   double* partials;
   IterCounters* ctr;   // device
   IterCounters* ctr_h; // pinned host mirror

@@ -75,6 +75,32 @@ def test_failed_fp32_solve_is_redone_in_fp64(mode):
     ref.close()
 
 
+@pytest.mark.parametrize("cluster", [0, -1])
+def test_stalled_fp32_solve_is_redone_in_fp64_from_its_iterate(cluster):
+    """FP32 solves stop after their first iteration as if stalled (injected), above
+    krylov_fail_rtol; each is redone in FP64 starting from the FP32 iterate (grid and cluster
+    solvers), and the steps end at the FP64 run's solution to the Krylov tolerance."""
+    case = cg.config0()
+    base = dict(mode=1, krylov_rtol=1e-12, krylov_maxit=5000, tol_dp=1.0, tol_cnv=1e-10)
+    m = lns.Model(case, lns.Options(**base, krylov_fp32=1, krylov_fail_rtol=1e-11))
+    m.lns_set_tuning(cluster_max_rows=cluster)
+    m.lns_debug_fault(4)
+    ref = lns.Model(case, lns.Options(**base))
+    ref.lns_set_tuning(cluster_max_rows=cluster)
+    retries = iters = 0
+    for dt in case.dt_schedule[:4]:
+        st = m.lns_timestep(float(dt))
+        retries += st["fp64_retries"]
+        iters += st["iterations"]
+        ref.lns_timestep(float(dt))
+    assert 0 < retries <= iters  # (a system the first iteration solves is not redone)
+    (p, sw), (pr, swr) = m.lns_get_state(), ref.lns_get_state()
+    assert np.max(np.abs(p - pr) / pr) < 1e-9
+    assert np.max(np.abs(sw - swr)) < 1e-9
+    m.close()
+    ref.close()
+
+
 def test_failed_fp32_solve_without_fallback_is_reported():
     case = cg.config0()
     m = lns.Model(case, lns.Options(mode=1, krylov_fp32=1, fp64_fallback=0))
