@@ -546,9 +546,22 @@ lns_status finish_iteration(lns_model* m, lns_iter_stats* st) {
   TRY(ev_flush(m));
   const IterCounters& h = *d.ctr_h;
   int retry = 0, kit_fp32 = 0;
+  if (wants_fp64_retry(m) && h.krylov_status == 1 && std::isfinite(h.krylov_relres) && h.n_active > 0) {
+    // a stall: one more FP32 solve from the stalled iterate first (the same system: the iteration
+    // is enqueued again from the unchanged state and set), then FP64 if that stalls too
+    kit_fp32 += h.krylov_iters;
+    CK(cudaMemcpyAsync(d.kx0, d.kx, (size_t)h.n_active * 2 * sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
+    d.krylov_warm = 1;
+    const lns_status r = enqueue_iteration(m);
+    d.krylov_warm = 0;
+    TRY(r);
+    CK(cudaStreamSynchronize(m->stream));
+    annotate_pending(m);
+    TRY(ev_flush(m));
+  }
   if (wants_fp64_retry(m)) {
     retry = 1;
-    kit_fp32 = h.krylov_iters;
+    kit_fp32 += h.krylov_iters;
     TRY(with_fp64_krylov(m, [&]() -> lns_status {
       TRY(enqueue_iteration(m));
       CK(cudaStreamSynchronize(m->stream));
