@@ -536,6 +536,25 @@ lns_status with_fp64_krylov(lns_model* m, F body) {
   return r;
 }
 
+// A stalled FP32 solve (a stop above krylov_fail_rtol at stagnation or krylov_maxit, with a finite
+// iterate) is solved once more in FP32 from its iterate before any FP64 redo: `body` enqueues the
+// same solve again (same state and set) and waits for it.  *kit gets the stalled attempt's Krylov
+// iterations (0 when nothing was stalled).
+template <typename F>
+lns_status fp32_restart(lns_model* m, F body, int* kit) {
+  Dev& d = m->d;
+  const IterCounters& h = *d.ctr_h;
+  *kit = 0;
+  if (!(wants_fp64_retry(m) && h.krylov_status == 1 && std::isfinite(h.krylov_relres) && h.n_active > 0))
+    return LNS_OK;
+  *kit = h.krylov_iters;
+  CK(cudaMemcpyAsync(d.kx0, d.kx, (size_t)h.n_active * 2 * sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
+  d.krylov_warm = 1;
+  const lns_status r = body();
+  d.krylov_warm = 0;
+  return r;
+}
+
 // Host side of one pass of Algorithm 1 lines 4-21 (or of standard Newton), after its device work
 // has completed and the counter block is on the host: an FP32 solve that failed is redone in FP64,
 // then the model's iteration state and the caller's statistics are updated.
@@ -546,19 +565,14 @@ lns_status finish_iteration(lns_model* m, lns_iter_stats* st) {
   TRY(ev_flush(m));
   const IterCounters& h = *d.ctr_h;
   int retry = 0, kit_fp32 = 0;
-  if (wants_fp64_retry(m) && h.krylov_status == 1 && std::isfinite(h.krylov_relres) && h.n_active > 0) {
-    // a stall: one more FP32 solve from the stalled iterate first (the same system: the iteration
-    // is enqueued again from the unchanged state and set), then FP64 if that stalls too
-    kit_fp32 += h.krylov_iters;
-    CK(cudaMemcpyAsync(d.kx0, d.kx, (size_t)h.n_active * 2 * sizeof(float), cudaMemcpyDeviceToDevice, m->stream));
-    d.krylov_warm = 1;
-    const lns_status r = enqueue_iteration(m);
-    d.krylov_warm = 0;
-    TRY(r);
+  // a stall: one more FP32 solve from the stalled iterate first (the iteration is enqueued again
+  // from the unchanged state and set), then FP64 if that stalls too
+  TRY(fp32_restart(m, [&]() -> lns_status {
+    TRY(enqueue_iteration(m));
     CK(cudaStreamSynchronize(m->stream));
     annotate_pending(m);
-    TRY(ev_flush(m));
-  }
+    return ev_flush(m);
+  }, &kit_fp32));
   if (wants_fp64_retry(m)) {
     retry = 1;
     kit_fp32 += h.krylov_iters;
@@ -677,8 +691,9 @@ lns_status residual_timestep(lns_model* m, double dt, lns_step_stats* out) {
     };
     TRY(solve());
     int kit_fp32 = 0;
+    TRY(fp32_restart(m, solve, &kit_fp32));
     if (wants_fp64_retry(m)) {
-      kit_fp32 = h.krylov_iters;
+      kit_fp32 += h.krylov_iters;
       TRY(with_fp64_krylov(m, solve));
       m->cur.fp64_retries += 1;
     }
@@ -742,8 +757,9 @@ lns_status dd_solve(lns_model* m, uint32_t* va_k, const uint32_t* vb, int solve_
   TRY(once());
   const IterCounters& h = *d.ctr_h;
   int kit_fp32 = 0;
+  TRY(fp32_restart(m, once, &kit_fp32));
   if (wants_fp64_retry(m)) {  // a failed solve scattered nothing and stamped nothing
-    kit_fp32 = h.krylov_iters;
+    kit_fp32 += h.krylov_iters;
     TRY(with_fp64_krylov(m, once));
     m->cur.fp64_retries += 1;
   }

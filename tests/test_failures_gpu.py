@@ -75,13 +75,15 @@ def test_failed_fp32_solve_is_redone_in_fp64(mode):
     ref.close()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("cluster", [0, -1])
-def test_stalled_fp32_solve_is_redone_in_fp64_from_its_iterate(cluster):
+def test_stalled_fp32_solve_is_redone_in_fp64_from_its_iterate(cluster, mode):
     """FP32 solves stop after their first iteration as if stalled (injected), above
-    krylov_fail_rtol; each is redone in FP64 starting from the FP32 iterate (grid and cluster
-    solvers), and the steps end at the FP64 run's solution to the Krylov tolerance."""
+    krylov_fail_rtol; each is solved again in FP32 from its iterate (stalling again) and then
+    redone in FP64 from the latest iterate (grid and cluster solvers, Algorithm 1 and 2), and the
+    steps end at the FP64 run's solution to the Krylov tolerance."""
     case = cg.config0()
-    base = dict(mode=1, krylov_rtol=1e-12, krylov_maxit=5000, tol_dp=1.0, tol_cnv=1e-10)
+    base = dict(mode=mode, krylov_rtol=1e-12, krylov_maxit=5000, tol_dp=1.0, tol_cnv=1e-10)
     m = lns.Model(case, lns.Options(**base, krylov_fp32=1, krylov_fail_rtol=1e-11))
     m.lns_set_tuning(cluster_max_rows=cluster)
     m.lns_debug_fault(4)
