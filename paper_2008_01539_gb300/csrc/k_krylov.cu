@@ -299,14 +299,15 @@ __device__ __forceinline__ double grid_sum_f64(const double* part, int nb, int s
 // ---- product of one row ------------------------------------------------------------------
 // own + sum over the row's active columns j of B_kj x_j, where x_j = comb(load(j)) is formed from
 // vectors written before the last barrier.  The loads of up to kBatch neighbours are issued before
-// any is used, so a row of degree <= kBatch costs one L2 round trip (4 neighbours at a time in
-// FP32; 2 in FP64, whose gathered values take twice the registers).
-template <typename T, typename LoadF, typename CombF>
+// any is used, so a row of degree <= kBatch costs one L2 round trip: BATCH neighbours at a time in
+// FP32 (4, or 6 in the grid solver on models of more than 5 neighbours a cell, which fits its 255
+// registers), 2 in FP64, whose gathered values take twice the registers.
+template <typename T, int BATCH = 4, typename LoadF, typename CombF>
 __device__ __forceinline__ typename V2<T>::t row_product(const int* col, const B4<T>* blk, int deg,
                                                          typename V2<T>::t own, LoadF load, CombF comb) {
   using V = typename V2<T>::t;
   using Raw = decltype(load(0));
-  constexpr int kBatch = sizeof(T) == 8 ? 2 : 4;
+  constexpr int kBatch = sizeof(T) == 8 ? 2 : BATCH;
   V acc0 = own, acc1 = mk<T>(0, 0);
   for (int j = 0; j < deg; j += kBatch) {
     int c[kBatch];
@@ -707,7 +708,7 @@ __device__ __forceinline__ int weighted_edge(const Dev& d, int w, int b, int nb,
   return (int)min(s + len + (T - ke) / 2, (long long)nA);
 }
 
-template <typename T, bool LINES>
+template <typename T, bool LINES, int BATCH>
 __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int maxit, int cl_cap) {
   using V = typename V2<T>::t;
   using B = B4<T>;
@@ -807,9 +808,9 @@ __global__ void __launch_bounds__(kKryBlk, 1) k_bicgstab(Dev d, double rtol, int
   // product of a row with a vector whose own value is `own` and whose neighbour values are
   // comb(load(j))
   auto product = [&](const Ref& ref, const V& own, auto load, auto comb) -> V {
-    if (ref.off >= 0) return row_product<T>(s_col + ref.off, s_blk + ref.off, ref.deg, own, load, comb);
+    if (ref.off >= 0) return row_product<T, BATCH>(s_col + ref.off, s_blk + ref.off, ref.deg, own, load, comb);
     const size_t e0 = (size_t)(-(ref.off + 1));
-    return row_product<T>(d.colA + e0, (const B*)&blocks[4 * e0], ref.deg, own, load, comb);
+    return row_product<T, BATCH>(d.colA + e0, (const B*)&blocks[4 * e0], ref.deg, own, load, comb);
   };
   for (int q = 0; q < kRowsCached; q++) {
     const int k = kbeg + q * kstep;
@@ -1837,11 +1838,11 @@ __global__ void __launch_bounds__(kClThreads, 1) k_bicgstab_cl(Dev d, double rto
   cl_sync();
 }
 
-template <typename T, bool L>
+template <typename T, bool L, int BATCH = 4>
 int max_blocks(int sms) {
   int nb = 0;
-  cudaFuncSetAttribute(k_bicgstab<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKrySmem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bicgstab<T, L>, kKryBlk, kKrySmem);
+  cudaFuncSetAttribute(k_bicgstab<T, L, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKrySmem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bicgstab<T, L, BATCH>, kKryBlk, kKrySmem);
   if (nb > 2) nb = 2;
   if (nb < 1) nb = 1;
   return nb * sms;
@@ -1852,6 +1853,11 @@ int max_blocks(int sms) {
 int krylov_grid(int fp32, int sms) {
   int a = fp32 ? max_blocks<float, true>(sms) : max_blocks<double, true>(sms);
   int b = fp32 ? max_blocks<float, false>(sms) : max_blocks<double, false>(sms);
+  if (fp32) {  // the wide-batch variants (Dev::wide_rows)
+    const int a6 = max_blocks<float, true, 6>(sms), b6 = max_blocks<float, false, 6>(sms);
+    a = a6 < a ? a6 : a;
+    b = b6 < b ? b6 : b;
+  }
   return a < b ? a : b;
 }
 
@@ -1974,8 +1980,9 @@ cudaError_t launch_bicgstab(const Dev& d, int fp32, int lines, double rtol, int 
   }
   void* args[] = {&dd, &rtol, &maxit, &cap};
   count_launches(1);
-  void* fn = fp32 ? (lines ? (void*)k_bicgstab<float, true> : (void*)k_bicgstab<float, false>)
-                  : (lines ? (void*)k_bicgstab<double, true> : (void*)k_bicgstab<double, false>);
+  void* fn = fp32 ? (d.wide_rows ? (lines ? (void*)k_bicgstab<float, true, 6> : (void*)k_bicgstab<float, false, 6>)
+                                  : (lines ? (void*)k_bicgstab<float, true, 4> : (void*)k_bicgstab<float, false, 4>))
+                  : (lines ? (void*)k_bicgstab<double, true, 4> : (void*)k_bicgstab<double, false, 4>);
   cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
   e = cudaStreamIsCapturing(c.stream, &cap_st);
   if (e != cudaSuccess) return e;

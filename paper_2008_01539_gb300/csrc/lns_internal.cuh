@@ -99,6 +99,9 @@ struct Dev {
   // extra cost of a fracture-line row in the grid solver's row split, in half rows, for FP64 [0] and
   // FP32 [1] solves (chosen per model from its fracture lines' mean length)
   int line_w[2];
+  // 1: the grid solver's FP32 products gather 6 neighbours of a row per round trip (models whose
+  // cells have more than 5 neighbours on average, the 3D ones), else 4
+  int wide_rows;
   int2* lnk;  // per compact row: CSR entries of its couplings to the previous / next row of its line (-1)
   int2* arow;  // per compact row: first CSR entry, and degree | line flag << 24 (written by the assembly)
   uint32_t* lblk;
