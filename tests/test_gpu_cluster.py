@@ -112,6 +112,20 @@ def test_cluster_and_grid_agree_with_oracle_on_config1_sets(big, fp32, precond):
     _check(case, va, fp32, 0, precond=precond, expect=GRID, seed=1)
 
 
+def test_grid_solver_on_3d_model_fp64():
+    """The grid solver on a 3D model of more than five neighbours a cell (3,059 cells, 5.48 a cell;
+    fracture cells of seven and eight) in FP64: the whole model and its fracture-support set against
+    the oracle's sparse LU.  (Its FP32 solves, whose six-neighbour gathers this model selects, stop
+    at the FP32 floor of these systems; they are checked through Newton timesteps against the
+    oracle in test_gpu_parity.py.)"""
+    case = cg.small_dfn3d(24, 20, 6)
+    deg = np.diff(case.row_ptr)
+    assert case.n_adj > 5 * case.n and deg.max() > 6
+    om = O.Model(case)
+    for va in (np.ones(case.n, np.uint8), O.dilate(om, case.always_active, 2)):
+        _check(case, va, 0, 0, expect=GRID)
+
+
 def test_cluster_capacity_boundary(big):
     """FP32 with the line preconditioner: 16 CTAs x (1024 - 128) rows = 14,336.  A set just below
     the capacity runs in the cluster, one just above in the grid solver; both match the oracle."""
