@@ -9,6 +9,8 @@ What it computes (paper passages in ``lns_oracle.h``): the oil-water backward-Eu
 TPFA residual and Jacobian (Appendix A), standard Newton (Section 4.1), localized
 Newton (Section 4.3, Algorithm 1), adaptive nonlinear domain decomposition
 (Section 4.4, Algorithm 2), with a hand-written block sparse LU as the linear step.
+``blackoil.py`` holds the three-phase black-oil model with primary-variable switching (the
+black-oil form of Section 3.1's variable substitution), in numpy.
 """
 from __future__ import annotations
 

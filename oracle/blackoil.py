@@ -1,0 +1,413 @@
+"""CPU FP64 oracle of the three-phase black-oil model with primary-variable switching.
+
+TEST INFRASTRUCTURE ONLY.  Like the rest of ``oracle/``, it exists to check the CUDA path and is
+called by the tests, the smoke check and the benchmark's CPU-baseline leg, never by the library.
+It shares no code with the CUDA path.  It reuses the oil-water oracle's active-set logic
+(Algorithm 1, steps 3-4, and the initial set), which is pinned on its own.
+
+What it computes, in plain vectorised numpy, double precision:
+
+* Appendix A's backward-Euler TPFA residual with phase-potential upwinding, for three phases and
+  three components (water, oil, gas; surface volumes), gas dissolving in oil:
+      R_c,i = [M_c(u_i) - M_c(u_i^n)] / dt + sum_j F_c,ij + q_c,i
+      M_w = PV b_w Sw,  M_o = PV b_o So,  M_g = PV (b_g Sg + Rs b_o So),  So = 1 - Sw - Sg
+      F_l,ij = T_ij (lambda_l b_l)_up dPhi_l,ij  for l = w, o, g (free gas),
+      F_g,ij += T_ij (Rs lambda_o b_o)_up(o) dPhi_o,ij  (dissolved gas moves with the oil)
+      dPhi_l,ij = (p_i - p_j) - g (rho_l,i + rho_l,j) / 2 (z_i - z_j)
+      up = i if dPhi > 0, j if dPhi < 0, min(i, j) on a tie
+      q_c,i = WI (lambda_c b_c)_i max(p_i - BHP, 0), and q_g += Rs_i q_o.
+  Fluid functions: casegen.BlackOilFluid.  Equations in the order (oil, water, gas).
+* Primary variables (p, Sw, X) per cell, X = Sg where free gas is present (saturated: Rs =
+  Rs_sat(p)) and X = Rs where it is not (undersaturated: Sg = 0).  Section 3.1's variable
+  substitution between Newton iterations, in its black-oil form: a cell without free gas whose
+  oil holds more gas than Rs_sat(p) splits (free gas appears at Sg = 0, Rs = Rs_sat(p)); a cell
+  whose Sg turns negative loses its gas phase (Sg = 0, Rs = Rs_sat(p) at that pressure).
+* The Jacobian by forward-mode differentiation (dual numbers carrying d/d(p, Sw, X) of the cell,
+  or of both cells of a face), so it is exact up to rounding; blocks 3 x 3, row = equation,
+  column = unknown.
+* Newton's method (Section 4.1) and localized Newton (Section 4.3, Algorithm 1) with the linear
+  step J_A du_A = -F_A solved by scipy's sparse direct solver.  A cell whose variable set changed
+  in an update counts as a non-negligible update (its unknowns changed meaning); an iteration
+  that switched any cell is not converged.
+
+Parity pins: tests/test_oracle_blackoil.py (reduction to the oil-water oracle at uniform Rs
+without free gas; the gas equation equal to Rs times the oil equation there; central
+differences; conservation of every component over a closed model; the two switches on a
+closed cell whose solution is known; quadratic Newton convergence; planted mistakes).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import Model as _SetModel
+from . import Options as _SetOptions
+from . import active_set_update as _active_set_update
+from . import initial_set as _initial_set
+
+
+# ---------------------------------------------------------------------------------------
+# Dual numbers over arrays: value v (m,) and derivatives d (m, k)
+# ---------------------------------------------------------------------------------------
+class D:
+    __slots__ = ("v", "d")
+    __array_ufunc__ = None  # ndarray (op) D defers to D's reflected operators
+
+    def __init__(self, v, d):
+        self.v = np.asarray(v, dtype=np.float64)
+        self.d = np.asarray(d, dtype=np.float64)
+
+    @staticmethod
+    def var(v, slot: int, k: int) -> "D":
+        d = np.zeros((np.shape(v)[0], k))
+        d[:, slot] = 1.0
+        return D(v, d)
+
+    def _lift(self, b) -> "D":
+        if isinstance(b, D):
+            return b
+        return D(np.broadcast_to(np.asarray(b, dtype=np.float64), self.v.shape), np.zeros_like(self.d))
+
+    def __add__(self, b):
+        b = self._lift(b)
+        return D(self.v + b.v, self.d + b.d)
+
+    __radd__ = __add__
+
+    def __neg__(self):
+        return D(-self.v, -self.d)
+
+    def __sub__(self, b):
+        b = self._lift(b)
+        return D(self.v - b.v, self.d - b.d)
+
+    def __rsub__(self, b):
+        return self._lift(b) - self
+
+    def __mul__(self, b):
+        b = self._lift(b)
+        return D(self.v * b.v, self.d * b.v[:, None] + b.d * self.v[:, None])
+
+    __rmul__ = __mul__
+
+    def __truediv__(self, b):
+        b = self._lift(b)
+        return D(self.v / b.v, (self.d * b.v[:, None] - b.d * self.v[:, None]) / (b.v * b.v)[:, None])
+
+    def __rtruediv__(self, b):
+        return self._lift(b) / self
+
+    def powi(self, k: int) -> "D":
+        return D(self.v ** k, (k * self.v ** (k - 1))[:, None] * self.d)
+
+    def __getitem__(self, idx) -> "D":
+        return D(self.v[idx], self.d[idx])
+
+
+def where(mask, a: D, b: D) -> D:
+    mask = np.asarray(mask, dtype=bool)
+    return D(np.where(mask, a.v, b.v), np.where(mask[:, None], a.d, b.d))
+
+
+def clip01(a: D) -> D:
+    """a clamped to [0, 1]; zero derivative outside (as the oil-water oracle's Corey clamps)."""
+    lo, hi = a.v <= 0.0, a.v >= 1.0
+    v = np.where(lo, 0.0, np.where(hi, 1.0, a.v))
+    d = np.where((lo | hi)[:, None], 0.0, a.d)
+    return D(v, d)
+
+
+def widen(a: D, left: bool) -> D:
+    """A cell quantity (3 derivative slots) as a face quantity (6 slots: the row cell, then the
+    neighbour)."""
+    z = np.zeros_like(a.d)
+    return D(a.v, np.concatenate([a.d, z], axis=1) if left else np.concatenate([z, a.d], axis=1))
+
+
+# ---------------------------------------------------------------------------------------
+# State and cell properties
+# ---------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class State:
+    """p, Sw, Sg, Rs and the variable set per cell (sat = 1: free gas, X = Sg; 0: X = Rs)."""
+
+    p: np.ndarray
+    sw: np.ndarray
+    sg: np.ndarray
+    rs: np.ndarray
+    sat: np.ndarray
+
+    def copy(self) -> "State":
+        return State(self.p.copy(), self.sw.copy(), self.sg.copy(), self.rs.copy(), self.sat.copy())
+
+    @property
+    def x(self) -> np.ndarray:
+        return np.where(self.sat == 1, self.sg, self.rs)
+
+
+def initial_state(bo) -> State:
+    return State(np.array(bo.p0, np.float64), np.array(bo.sw0, np.float64), np.array(bo.sg0, np.float64),
+                 np.array(bo.rs0, np.float64), np.array(bo.sat0, np.uint8))
+
+
+def rs_sat(fl, p):
+    """Saturated solution gas-oil ratio, linear in p (rs_max at the bubble point)."""
+    return fl.rs_max * p / fl.p_bubble
+
+
+def cell_props(fl, pv_ref, st: State) -> Dict[str, D]:
+    """Per-cell properties as dual numbers in (p, Sw, X)."""
+    k = 3
+    P = D.var(st.p, 0, k)
+    SW = D.var(st.sw, 1, k)
+    X = D.var(st.x, 2, k)
+    sat = st.sat == 1
+    zero = D(np.zeros_like(st.p), np.zeros((st.p.shape[0], k)))
+    SG = where(sat, X, zero)
+    RS = where(sat, rs_sat(fl, P), X)
+    SO = 1.0 - SW - SG
+    dpr = P - fl.p_ref
+    PV = pv_ref * (1.0 + fl.c_r * dpr)
+    BW = fl.b_w_ref * (1.0 + fl.c_w * dpr)
+    BO = fl.b_o_ref * (1.0 + fl.c_o * dpr) / (1.0 + fl.kappa * RS)
+    BG = fl.b_g_per_pa * P
+    span = 1.0 - fl.swc - fl.sor
+    krw = clip01((SW - fl.swc) / span).powi(fl.n_w)
+    kro = clip01((SO - fl.sor) / span).powi(fl.n_o)
+    krg = clip01(SG / span).powi(fl.n_g)
+    q = dict(P=P, SW=SW, SG=SG, SO=SO, RS=RS, PV=PV, BW=BW, BO=BO, BG=BG)
+    q["rho_w"] = fl.rho_w_sc * BW
+    q["rho_o"] = BO * (fl.rho_o_sc + fl.rho_g_sc * RS)
+    q["rho_g"] = fl.rho_g_sc * BG
+    q["mob_w"] = krw / fl.mu_w * BW
+    q["mob_o"] = kro / fl.mu_o * BO
+    q["mob_g"] = krg / fl.mu_g * BG
+    q["mass_o"] = PV * BO * SO
+    q["mass_w"] = PV * BW * SW
+    q["mass_g"] = PV * (BG * SG + RS * BO * SO)
+    return q
+
+
+# ---------------------------------------------------------------------------------------
+# Residual and Jacobian (Appendix A)
+# ---------------------------------------------------------------------------------------
+EQ = ("o", "w", "g")  # equation order: oil, water, gas
+
+
+def assemble(bo, st: State, old: State, dt: float) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Full-domain residual F (n, 3) and Jacobian blocks: diagonal (n, 3, 3) and off-diagonal per
+    adjacency entry (n_adj, 3, 3) (row i = the entry's row, column nbr[e]), in (p, Sw, X) of the
+    current variable sets."""
+    c, fl = bo.case, bo.fluid
+    n = c.n
+    q = cell_props(fl, c.pv_ref, st)
+    qn = cell_props(fl, c.pv_ref, old)
+    F = np.zeros((n, 3))
+    Jd = np.zeros((n, 3, 3))
+    for r, comp in enumerate(EQ):
+        acc = (q["mass_" + comp] - qn["mass_" + comp].v) / dt
+        F[:, r] += acc.v
+        Jd[:, r, :] += acc.d
+    rows = np.repeat(np.arange(n), np.diff(c.row_ptr))
+    cols = np.asarray(c.nbr, dtype=np.int64)
+    T = np.asarray(c.trans, dtype=np.float64)
+    dz = c.depth[rows] - c.depth[cols]
+    g = fl.gravity
+    Jo = np.zeros((cols.shape[0], 3, 3))
+
+    def face(name):
+        a = q[name]
+        return widen(a[rows], True), widen(a[cols], False)
+
+    Pi, Pj = face("P")
+    up_oil = None
+    flux = {}
+    for ph in ("o", "w", "g"):
+        ri, rj = face("rho_" + ph)
+        dphi = (Pi - Pj) - g * dz * (0.5 * (ri + rj))
+        up = (dphi.v > 0.0) | ((dphi.v == 0.0) & (rows < cols))
+        mi, mj = face("mob_" + ph)
+        flux[ph] = T * where(up, mi, mj) * dphi
+        if ph == "o":
+            up_oil, dphi_oil = up, dphi
+    # dissolved gas travels with the oil, upwinded with it
+    rmi, rmj = widen((q["RS"] * q["mob_o"])[rows], True), widen((q["RS"] * q["mob_o"])[cols], False)
+    flux["dg"] = T * where(up_oil, rmi, rmj) * dphi_oil
+    for r, comp in enumerate(EQ):
+        f = flux[comp] if comp != "g" else flux["g"] + flux["dg"]
+        np.add.at(F[:, r], rows, f.v)
+        np.add.at(Jd[:, r, :], rows, f.d[:, :3])
+        Jo[:, r, :] = f.d[:, 3:]
+    # producers at fixed bottom-hole pressure
+    for w in range(c.well_cell.shape[0]):
+        i = int(c.well_cell[w])
+        dpw = q["P"][[i]] - float(c.well_bhp[w])
+        if dpw.v[0] <= 0.0:
+            continue
+        wi = float(c.well_wi[w])
+        qo = wi * q["mob_o"][[i]] * dpw
+        terms = dict(o=qo, w=wi * q["mob_w"][[i]] * dpw, g=wi * q["mob_g"][[i]] * dpw + q["RS"][[i]] * qo)
+        for r, comp in enumerate(EQ):
+            F[i, r] += terms[comp].v[0]
+            Jd[i, r, :] += terms[comp].d[0]
+    return F, Jd, Jo
+
+
+def residual(bo, st: State, old: State, dt: float) -> np.ndarray:
+    return assemble(bo, st, old, dt)[0]
+
+
+def cnv(bo, st: State, F: np.ndarray, dt: float) -> np.ndarray:
+    """CNV_i = max over components of |R_c,i| dt / (PV_i b_c,i) (b of the phase carrying c)."""
+    q = cell_props(bo.fluid, bo.case.pv_ref, st)
+    pv = q["PV"].v
+    scale = np.stack([q["BO"].v, q["BW"].v, q["BG"].v], axis=1) * pv[:, None]
+    return np.max(np.abs(F) * dt / scale, axis=1)
+
+
+# ---------------------------------------------------------------------------------------
+# Newton step on an active set, update with variable switching
+# ---------------------------------------------------------------------------------------
+def local_solve(bo, st: State, old: State, dt: float, va: np.ndarray, sat_chop: float = 0.2):
+    """One Newton step restricted to V_A (J_A du_A = -F_A, Section 4.3; inactive cells are fixed).
+    Returns (du (n, 3) in (p, Sw, X), zero outside V_A and chopped, max CNV over V_A at the input
+    state, max |dp| over V_A)."""
+    c = bo.case
+    n = c.n
+    F, Jd, Jo = assemble(bo, st, old, dt)
+    cv = cnv(bo, st, F, dt)
+    act = np.flatnonzero(np.asarray(va) != 0)
+    na = act.shape[0]
+    du = np.zeros((n, 3))
+    if na == 0:
+        return du, 0.0, 0.0
+    idx = -np.ones(n, np.int64)
+    idx[act] = np.arange(na)
+    rows = np.repeat(np.arange(n), np.diff(c.row_ptr))
+    cols = np.asarray(c.nbr, dtype=np.int64)
+    keep = (idx[rows] >= 0) & (idx[cols] >= 0)
+    bi = np.concatenate([idx[act], idx[rows[keep]]])
+    bj = np.concatenate([idx[act], idx[cols[keep]]])
+    blocks = np.concatenate([Jd[act], Jo[keep]])
+    # scatter the 3 x 3 blocks into a CSR matrix of order 3 n_A
+    r3 = (3 * bi[:, None, None] + np.arange(3)[None, :, None]) + 0 * np.arange(3)[None, None, :]
+    c3 = (3 * bj[:, None, None] + np.arange(3)[None, None, :]) + 0 * np.arange(3)[None, :, None]
+    A = sp.csr_matrix((blocks.ravel(), (r3.ravel(), c3.ravel())), shape=(3 * na, 3 * na))
+    x = spla.spsolve(A.tocsc(), -F[act].ravel())
+    x = np.asarray(x).reshape(na, 3)
+    if not np.all(np.isfinite(x)):
+        raise ArithmeticError("singular local system in the black-oil oracle")
+    if sat_chop > 0.0:
+        x[:, 1] = np.clip(x[:, 1], -sat_chop, sat_chop)
+        s = st.sat[act] == 1
+        x[s, 2] = np.clip(x[s, 2], -sat_chop, sat_chop)
+    du[act] = x
+    return du, float(cv[act].max()), float(np.abs(x[:, 0]).max())
+
+
+def apply_update(fl, st: State, du: np.ndarray, va: np.ndarray) -> Tuple[State, np.ndarray]:
+    """u <- u + du on V_A, then Section 3.1's switch on every updated cell.  Returns the new state
+    and the mask of cells whose variable set changed."""
+    out = st.copy()
+    a = np.asarray(va) != 0
+    out.p[a] += du[a, 0]
+    out.sw[a] += du[a, 1]
+    s = a & (st.sat == 1)
+    u = a & (st.sat == 0)
+    out.sg[s] += du[s, 2]
+    out.rs[s] = rs_sat(fl, out.p[s])
+    out.rs[u] += du[u, 2]
+    # gas phase disappears: Sg < 0 -> no free gas, the oil holds the saturated amount
+    gone = s & (out.sg < 0.0)
+    out.sat[gone] = 0
+    out.sg[gone] = 0.0
+    out.rs[gone] = rs_sat(fl, out.p[gone])
+    # gas phase appears: the oil holds more than it can at this pressure -> free gas at Sg = 0
+    split = u & (out.rs > rs_sat(fl, out.p))
+    out.sat[split] = 1
+    out.sg[split] = 0.0
+    out.rs[split] = rs_sat(fl, out.p[split])
+    return out, gone | split
+
+
+# ---------------------------------------------------------------------------------------
+# Timesteps: standard Newton and Algorithm 1
+# ---------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Options:
+    """mode 0 standard Newton, 1 Algorithm 1; cutoffs and tolerances as the oil-water oracle's
+    (eps_sw, when > 0, applies to max(|dSw|, |dSg|))."""
+
+    mode: int = 1
+    eps_p: float = 0.3 * 6894.757293168
+    eps_sw: float = 0.0
+    m_layers: int = 2
+    tol_dp: float = 0.3 * 6894.757293168
+    tol_cnv: float = 1e-6
+    max_newton: int = 25
+    sat_chop: float = 0.2
+
+    def sets(self) -> _SetOptions:
+        return _SetOptions(mode=self.mode, eps_p=self.eps_p, eps_sw=self.eps_sw, m_layers=self.m_layers,
+                           tol_dp=self.tol_dp, tol_cnv=self.tol_cnv, max_newton=self.max_newton,
+                           sat_chop=self.sat_chop)
+
+
+class Sim:
+    """Stateful black-oil oracle simulation: the state and the previous step's support set."""
+
+    def __init__(self, bo, opts: Optional[Options] = None) -> None:
+        self.bo = bo
+        self.o = opts or Options()
+        self.sm = _SetModel(bo.case)
+        self.st = initial_state(bo)
+        self.prev_supp = np.zeros(bo.n, np.uint8)
+        self.has_prev = False
+
+    def _big(self, dp, ds, switched) -> np.ndarray:
+        """Non-negligible update: |dp| >= eps_p, or |dS| >= eps_sw when enabled, or a switch."""
+        big = np.abs(dp) >= self.o.eps_p
+        if self.o.eps_sw > 0.0:
+            big |= ds >= self.o.eps_sw
+        return big | switched
+
+    def timestep(self, dt: float) -> Dict:
+        bo, o, n = self.bo, self.o, self.bo.n
+        old = self.st.copy()
+        st = self.st.copy()
+        stats = dict(status=0, iterations=0, cell_updates=0, switches=0, trace=[])
+        if o.mode == 0:
+            va = np.ones(n, np.uint8)
+        else:
+            va = _initial_set(self.sm, o.sets(), self.prev_supp, self.has_prev)
+        is_expand, converged = 1, False
+        while (o.mode == 1 and is_expand) or not converged:
+            if stats["iterations"] >= o.max_newton:
+                stats["status"] = -4
+                break
+            na = int(np.count_nonzero(va))
+            du, cnv_max, dp_max = local_solve(bo, st, old, dt, va, o.sat_chop)
+            new, switched = apply_update(bo.fluid, st, du, va)
+            stats["iterations"] += 1
+            stats["cell_updates"] += na
+            stats["switches"] += int(switched.sum())
+            stats["trace"].append(na)
+            converged = dp_max < o.tol_dp and cnv_max < o.tol_cnv and not switched.any()
+            if o.mode == 1:
+                ds = np.maximum(np.abs(new.sw - st.sw), np.abs(new.sg - st.sg))
+                dp_eff = np.where(switched, np.maximum(np.abs(du[:, 0]), o.eps_p), du[:, 0])
+                ds_eff = np.where(switched, np.maximum(ds, max(o.eps_sw, 0.0)), ds)
+                va, _, is_expand = _active_set_update(self.sm, o.sets(), va, dp_eff, ds_eff, converged)
+            st = new
+        self.st = st
+        ds = np.maximum(np.abs(st.sw - old.sw), np.abs(st.sg - old.sg))
+        self.prev_supp = self._big(st.p - old.p, ds, st.sat != old.sat).astype(np.uint8)
+        self.has_prev = True
+        return stats
+
+    def run(self, dts) -> list:
+        return [self.timestep(float(dt)) for dt in dts]

@@ -646,3 +646,96 @@ def serving_model_3d(index: int, cells: int, dx: float = 5.0, dz: float = 2.0, n
     return dfn3d_case(nn, nn, nz, dx, dz, max(4, nn // 2), 30_000 + index, hf=hf, wells=wells,
                       nf_layers=(2, max(2, nz - 2)), dts=np.array([DAY]), name=f"serve3d{index}_{nn}x{nn}x{nz}")
 
+
+
+# ---------------------------------------------------------------------------------------
+# Three-phase black-oil inputs (the 3D workload's physics: gas liberation below a bubble
+# point, primary variables switched between p/Sw/Sg and p/Sw/Rs)
+# ---------------------------------------------------------------------------------------
+SCF_PER_STB = 0.028316846592 / 0.158987294928  # m^3 of gas per m^3 of oil, per scf/stb
+
+
+@dataclasses.dataclass
+class BlackOilFluid:
+    """Black-oil fluid and rock constants (SI; gas-oil ratios in surface m^3 per surface m^3).
+
+    Water as in ``Fluid``; oil b_o(p, Rs) = b_o_ref (1 + c_o (p - p_ref)) / (1 + kappa Rs) with
+    density b_o (rho_o_sc + Rs rho_g_sc); gas b_g(p) = b_g_per_pa p (ideal gas at constant z and
+    temperature) with density rho_g_sc b_g; saturated solution gas-oil ratio
+    Rs_sat(p) = rs_max p / p_bubble (linear, rs_max at the bubble point); rock
+    phi(p) = phi_ref (1 + c_r (p - p_ref)).  Relative permeabilities: Corey in the normalised
+    saturations (Sw - swc) / span, (So - sor) / span and Sg / span, span = 1 - swc - sor.
+    """
+
+    p_ref: float = 5500.0 * PSI
+    c_r: float = 1.0e-6 / PSI
+    b_w_ref: float = 1.0
+    c_w: float = 3.0e-6 / PSI
+    rho_w_sc: float = 1000.0
+    mu_w: float = 0.5 * CP
+    b_o_ref: float = 1.0
+    c_o: float = 1.0e-5 / PSI
+    kappa: float = 0.4 / (800.0 * SCF_PER_STB)  # b_o(p_ref, rs_max) = 1 / 1.4
+    rho_o_sc: float = 800.0
+    mu_o: float = 1.0 * CP
+    b_g_per_pa: float = 288.7 / (101325.0 * 0.9 * 350.0)  # T_sc / (p_sc z T)
+    rho_g_sc: float = 0.9
+    mu_g: float = 0.02 * CP
+    rs_max: float = 800.0 * SCF_PER_STB
+    p_bubble: float = 3500.0 * PSI
+    swc: float = 0.2
+    sor: float = 0.2
+    n_w: int = 2
+    n_o: int = 2
+    n_g: int = 2
+    gravity: float = GRAVITY
+
+
+@dataclasses.dataclass
+class BlackOilCase:
+    """A model (``case``: graph, pore volumes, depths, wells, schedule; its oil-water ``fluid`` is not
+    used) with black-oil constants and an initial state: p0, sw0, and per cell either free gas
+    (sat0 = 1, sg0 >= 0, rs0 = Rs_sat(p0)) or none (sat0 = 0, sg0 = 0, rs0 <= Rs_sat(p0))."""
+
+    case: Case
+    fluid: BlackOilFluid
+    p0: np.ndarray
+    sw0: np.ndarray
+    sg0: np.ndarray
+    rs0: np.ndarray
+    sat0: np.ndarray  # uint8
+
+    @property
+    def n(self) -> int:
+        return self.case.n
+
+
+def blackoil(case: Case, fluid: Optional[BlackOilFluid] = None, *, p_init: float = 5500.0 * PSI,
+             bhp: Optional[float] = 2000.0 * PSI, rs_init: Optional[float] = None, sw_init: Optional[float] = None,
+             rho_init: float = 640.0) -> BlackOilCase:
+    """The black-oil version of a model: undersaturated oil (Rs = rs_init, default the fluid's
+    rs_max, i.e. the bubble point at p_bubble) at p_init at the shallowest cell, increasing with depth
+    at rho_init g (about the live oil's density), producers at ``bhp`` (None: the model's own)."""
+    fl = fluid or BlackOilFluid()
+    c = dataclasses.replace(case)
+    if bhp is not None:
+        c.well_bhp = np.full_like(case.well_bhp, bhp)
+    n = case.n
+    p0 = p_init + rho_init * fl.gravity * (case.depth - case.depth.min())
+    rs = fl.rs_max if rs_init is None else rs_init
+    sw0 = np.array(case.sw0, dtype=np.float64) if sw_init is None else np.full(n, sw_init)
+    return BlackOilCase(case=c, fluid=fl, p0=p0, sw0=sw0, sg0=np.zeros(n), rs0=np.full(n, rs),
+                        sat0=np.zeros(n, np.uint8))
+
+
+def config2_blackoil(seed: int = 2) -> BlackOilCase:
+    """The 3D workload with its black-oil physics: the config-2 geometry (200 x 200 x 20 + 10 hydraulic
+    fractures + 2000 natural fractures), 5500 psi initially, producers at 2000 psi, bubble point
+    3500 psi, Rs up to 800 scf/stb."""
+    return blackoil(config2(seed))
+
+
+def small_blackoil3d(nx: int = 10, ny: int = 8, nz: int = 3, seed: int = 5, n_steps: int = 5) -> BlackOilCase:
+    """A few-hundred-cell 3D black-oil model for tests (the producer draws the fracture below the
+    bubble point within the first steps)."""
+    return blackoil(small_dfn3d(nx, ny, nz, seed=seed, n_steps=n_steps), p_init=3700.0 * PSI, bhp=2000.0 * PSI)
