@@ -3,6 +3,7 @@
 // links it.
 #include <cstring>
 
+#include "../../paper_2008_01539_gb300/csrc/blk3.cuh"
 #include "../../paper_2008_01539_gb300/csrc/bo_physics.cuh"
 
 using namespace lns::bo;
@@ -49,5 +50,30 @@ int bo_host_update(const Fluid* f, double chop, int n, const double* du, double*
     k += switched[i];
   }
   return k;
+}
+
+// 3x3 block inverse; returns 0 on a singular block
+int b3_host_inv(const double* a, double* r) { return lns::b3::inv(a, r) ? 1 : 0; }
+
+// factor a line block (L, U: len x 9) and solve M z = r, in FP64 (fp32 = 0) or FP32 (inputs
+// rounded to float, as the FP32 preconditioner stores them); returns 0 on a singular pivot
+int b3_host_line(int len, const double* L, const double* U, const double* r, double* z, int fp32) {
+  if (len <= 0 || len > 256) return 0;
+  if (!fp32) {
+    static double Di[9 * 256], A[9 * 256], G[9 * 256];
+    if (!lns::b3::line_factor(len, L, U, Di, A, G)) return 0;
+    lns::b3::line_solve(len, Di, A, G, r, z);
+    return 1;
+  }
+  static float Lf[9 * 256], Uf[9 * 256], rf[3 * 256], zf[3 * 256], Di[9 * 256], A[9 * 256], G[9 * 256];
+  for (int k = 0; k < 9 * len; k++) {
+    Lf[k] = (float)L[k];
+    Uf[k] = (float)U[k];
+  }
+  for (int k = 0; k < 3 * len; k++) rf[k] = (float)r[k];
+  if (!lns::b3::line_factor(len, Lf, Uf, Di, A, G)) return 0;
+  lns::b3::line_solve(len, Di, A, G, rf, zf);
+  for (int k = 0; k < 3 * len; k++) z[k] = zf[k];
+  return 1;
 }
 }

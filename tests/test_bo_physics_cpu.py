@@ -1,6 +1,8 @@
 """The black-oil physics of the CUDA path (csrc/bo_physics.cuh: cell properties, face fluxes,
 producer terms, CNV and the update with Section 3.1's variable switch), built for the host, against
-the black-oil oracle (oracle/blackoil.py).
+the black-oil oracle (oracle/blackoil.py); and its 3x3 block arithmetic (csrc/blk3.cuh: block
+inverse, the fracture-line block's block Thomas factorization and solve) against numpy's dense
+inverse and solve.
 
 The header's derivatives are written out by hand; the oracle's come from forward-mode dual
 numbers, so the Jacobians agree only if every hand-written chain rule is right.  Residuals and
@@ -159,3 +161,44 @@ def test_update_and_switch_match_oracle_bit_for_bit(host, chop):
     assert np.array_equal(h.sat, ref.sat)
     for a, b in ((h.p, ref.p), (h.sw, ref.sw), (h.sg, ref.sg), (h.rs, ref.rs)):
         assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------------------
+# 3x3 block arithmetic of the black-oil preconditioner (csrc/blk3.cuh)
+# ---------------------------------------------------------------------------------------
+def test_block_inverse_matches_numpy(host):
+    rng = np.random.default_rng(11)
+    host.b3_host_inv.restype = C.c_int
+    for _ in range(50):
+        a = rng.normal(size=(3, 3)) + 3.0 * np.eye(3)
+        r = np.zeros((3, 3))
+        assert host.b3_host_inv(_p(np.ascontiguousarray(a)), _p(r)) == 1
+        assert np.max(np.abs(r - np.linalg.inv(a))) <= 1e-13 * np.max(np.abs(np.linalg.inv(a)))
+    s = np.array([[1.0, 2.0, 3.0], [2.0, 4.0, 6.0], [0.0, 1.0, 1.0]])  # rank 2
+    assert host.b3_host_inv(_p(s), _p(np.zeros((3, 3)))) == 0
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("length", [1, 2, 7, 40])
+def test_line_block_thomas_matches_dense_solve(host, fp32, length):
+    """The fracture-line block of the row-scaled system (identity diagonal blocks, couplings L_t to
+    the previous row and U_t to the next) solved by the block Thomas factorization, against a dense
+    solve of the assembled block-tridiagonal matrix."""
+    rng = np.random.default_rng(100 + length)
+    host.b3_host_line.restype = C.c_int
+    L = 0.3 * rng.normal(size=(length, 3, 3)) / 3.0
+    U = 0.3 * rng.normal(size=(length, 3, 3)) / 3.0
+    r = rng.normal(size=(length, 3))
+    M = np.eye(3 * length)
+    for t in range(length):
+        if t > 0:
+            M[3 * t:3 * t + 3, 3 * (t - 1):3 * t] = L[t]
+        if t + 1 < length:
+            M[3 * t:3 * t + 3, 3 * (t + 1):3 * t + 6] = U[t]
+    want = np.linalg.solve(M, r.ravel()).reshape(length, 3)
+    z = np.zeros((length, 3))
+    ok = host.b3_host_line(length, _p(np.ascontiguousarray(L)), _p(np.ascontiguousarray(U)),
+                           _p(np.ascontiguousarray(r)), _p(z), fp32)
+    assert ok == 1
+    tol = 2e-5 if fp32 else 1e-12
+    assert np.max(np.abs(z - want)) <= tol * np.max(np.abs(want))
