@@ -25,10 +25,12 @@ What it computes, in plain vectorised numpy, double precision:
 * The Jacobian by forward-mode differentiation (dual numbers carrying d/d(p, Sw, X) of the cell,
   or of both cells of a face), so it is exact up to rounding; blocks 3 x 3, row = equation,
   column = unknown.
-* Newton's method (Section 4.1) and localized Newton (Section 4.3, Algorithm 1) with the linear
-  step J_A du_A = -F_A solved by scipy's sparse direct solver.  A cell whose variable set changed
-  in an update counts as a non-negligible update (its unknowns changed meaning); an iteration
-  that switched any cell is not converged.
+* Newton's method (Section 4.1), localized Newton (Section 4.3, Algorithm 1), adaptive nonlinear
+  domain decomposition (Section 4.4, Algorithm 2, one Newton step per subdomain visit) and the
+  residual-based active sets the paper compares against (mode 3), with the linear step
+  J_A du_A = -F_A solved by scipy's sparse direct solver.  A cell whose variable set changed in an
+  update counts as a non-negligible update (its unknowns changed meaning); an update that switched
+  any cell is not converged.
 
 Parity pins: tests/test_oracle_blackoil.py (reduction to the oil-water oracle at uniform Rs
 without free gas; the gas equation equal to Rs times the oil equation there; central
@@ -47,7 +49,11 @@ import scipy.sparse.linalg as spla
 from . import Model as _SetModel
 from . import Options as _SetOptions
 from . import active_set_update as _active_set_update
+from . import boundary as _boundary
+from . import dd_expand as _dd_expand
+from . import dilate as _dilate
 from . import initial_set as _initial_set
+from . import outer_halo as _outer_halo
 
 
 # ---------------------------------------------------------------------------------------
@@ -339,8 +345,8 @@ def apply_update(fl, st: State, du: np.ndarray, va: np.ndarray) -> Tuple[State, 
 # ---------------------------------------------------------------------------------------
 @dataclasses.dataclass
 class Options:
-    """mode 0 standard Newton, 1 Algorithm 1; cutoffs and tolerances as the oil-water oracle's
-    (eps_sw, when > 0, applies to max(|dSw|, |dSg|))."""
+    """mode 0 standard Newton, 1 Algorithm 1, 2 Algorithm 2, 3 residual-based sets; cutoffs and
+    tolerances as the oil-water oracle's (eps_sw, when > 0, applies to max(|dSw|, |dSg|))."""
 
     mode: int = 1
     eps_p: float = 0.3 * 6894.757293168
@@ -350,11 +356,12 @@ class Options:
     tol_cnv: float = 1e-6
     max_newton: int = 25
     sat_chop: float = 0.2
+    max_dd_outer: int = 25
 
     def sets(self) -> _SetOptions:
         return _SetOptions(mode=self.mode, eps_p=self.eps_p, eps_sw=self.eps_sw, m_layers=self.m_layers,
                            tol_dp=self.tol_dp, tol_cnv=self.tol_cnv, max_newton=self.max_newton,
-                           sat_chop=self.sat_chop)
+                           sat_chop=self.sat_chop, max_dd_outer=self.max_dd_outer)
 
 
 class Sim:
@@ -375,34 +382,116 @@ class Sim:
             big |= ds >= self.o.eps_sw
         return big | switched
 
+    def _solve(self, st: State, old: State, dt: float, va: np.ndarray):
+        """One step on V_A: returns the new state, the update, the switched cells, the step's
+        convergence test and |dp|, |dS| as the set logic reads them (a switch counts as big)."""
+        o = self.o
+        du, cnv_max, dp_max = local_solve(self.bo, st, old, dt, va, o.sat_chop)
+        new, switched = apply_update(self.bo.fluid, st, du, va)
+        converged = dp_max < o.tol_dp and cnv_max < o.tol_cnv and not switched.any()
+        ds = np.maximum(np.abs(new.sw - st.sw), np.abs(new.sg - st.sg))
+        dp_eff = np.where(switched, np.maximum(np.abs(du[:, 0]), o.eps_p), du[:, 0])
+        ds_eff = np.where(switched, np.maximum(ds, max(o.eps_sw, 0.0)), ds)
+        return new, switched, converged, dp_eff, ds_eff
+
     def timestep(self, dt: float) -> Dict:
         bo, o, n = self.bo, self.o, self.bo.n
         old = self.st.copy()
         st = self.st.copy()
-        stats = dict(status=0, iterations=0, cell_updates=0, switches=0, trace=[])
-        if o.mode == 0:
-            va = np.ones(n, np.uint8)
-        else:
-            va = _initial_set(self.sm, o.sets(), self.prev_supp, self.has_prev)
-        is_expand, converged = 1, False
-        while (o.mode == 1 and is_expand) or not converged:
-            if stats["iterations"] >= o.max_newton:
-                stats["status"] = -4
-                break
+        stats = dict(status=0, iterations=0, cell_updates=0, switches=0, trace=[], n_subdomains=0, dd_outer=0)
+
+        def count(va, switched):
             na = int(np.count_nonzero(va))
-            du, cnv_max, dp_max = local_solve(bo, st, old, dt, va, o.sat_chop)
-            new, switched = apply_update(bo.fluid, st, du, va)
             stats["iterations"] += 1
             stats["cell_updates"] += na
             stats["switches"] += int(switched.sum())
             stats["trace"].append(na)
-            converged = dp_max < o.tol_dp and cnv_max < o.tol_cnv and not switched.any()
-            if o.mode == 1:
-                ds = np.maximum(np.abs(new.sw - st.sw), np.abs(new.sg - st.sg))
-                dp_eff = np.where(switched, np.maximum(np.abs(du[:, 0]), o.eps_p), du[:, 0])
-                ds_eff = np.where(switched, np.maximum(ds, max(o.eps_sw, 0.0)), ds)
-                va, _, is_expand = _active_set_update(self.sm, o.sets(), va, dp_eff, ds_eff, converged)
-            st = new
+
+        if o.mode in (0, 1):  # Section 4.1; Algorithm 1
+            va = np.ones(n, np.uint8) if o.mode == 0 else _initial_set(self.sm, o.sets(), self.prev_supp,
+                                                                        self.has_prev)
+            is_expand, converged = 1, False
+            while (o.mode == 1 and is_expand) or not converged:
+                if stats["iterations"] >= o.max_newton:
+                    stats["status"] = -4
+                    break
+                st_new, switched, converged, dp_eff, ds_eff = self._solve(st, old, dt, va)
+                count(va, switched)
+                if o.mode == 1:
+                    va, _, is_expand = _active_set_update(self.sm, o.sets(), va, dp_eff, ds_eff, converged)
+                st = st_new
+        elif o.mode == 3:  # residual-based sets: unconverged cells inflated by m layers
+            va = np.zeros(n, np.uint8)
+            last_ok = False
+            while True:
+                F = residual(bo, st, old, dt)
+                unconv = (cnv(bo, st, F, dt) >= o.tol_cnv).astype(np.uint8)
+                if not unconv.any() and (stats["iterations"] == 0 or last_ok):
+                    break
+                if stats["iterations"] >= o.max_newton:
+                    stats["status"] = -4
+                    break
+                if unconv.any():
+                    va = _dilate(self.sm, unconv, o.m_layers)
+                du, _, dp_max = local_solve(bo, st, old, dt, va, o.sat_chop)
+                st, switched = apply_update(bo.fluid, st, du, va)
+                last_ok = dp_max < o.tol_dp and not switched.any()
+                count(va, switched)
+        else:  # Algorithm 2: expansion into disjoint subdomains, then multiplicative Schwarz passes
+            cap = max(o.max_newton, 1)
+            it_cap = o.max_newton * (o.max_dd_outer + 1)
+            VA = [_initial_set(self.sm, o.sets(), self.prev_supp, self.has_prev)]
+            VB = [_boundary(self.sm, VA[0])]
+            VD = [_outer_halo(self.sm, VA[0])]
+            vt = VA[0].copy()
+            last_solve, own_big = [], []
+            big_stamp = np.zeros(n, np.int64)
+            solve_id = 0
+
+            def visit(k, st):
+                nonlocal solve_id
+                st_new, switched, conv1, dp_eff, ds_eff = self._solve(st, old, dt, VA[k])
+                count(VA[k], switched)
+                solve_id += 1
+                big = (VA[k] != 0) & self._big(dp_eff, ds_eff, switched)
+                big_stamp[big] = solve_id
+                return st_new, conv1, dp_eff, ds_eff, bool(big.any())
+
+            is_expand, k = 1, 0
+            while is_expand:
+                if k >= cap:
+                    stats["status"] = -4
+                    break
+                st, _, dp_eff, ds_eff, ob = visit(k, st)
+                last_solve.append(solve_id)
+                own_big.append(ob)
+                vt, va_n, vb_n, vd_n, is_expand = _dd_expand(self.sm, o.sets(), VB[k], dp_eff, ds_eff, vt)
+                VA.append(va_n)
+                VB.append(vb_n)
+                VD.append(vd_n)
+                k += 1
+            N = k
+            stats["n_subdomains"] = N
+            converged, nu = False, 0
+            while stats["status"] == 0 and not converged:
+                if nu >= o.max_dd_outer:
+                    stats["status"] = -4
+                    break
+                all_ok = True
+                for s_ in range(N):
+                    halo_big = bool(np.any((VD[s_] != 0) & (big_stamp > last_solve[s_])))
+                    if not (own_big[s_] or halo_big):
+                        continue
+                    if stats["iterations"] >= it_cap:
+                        stats["status"] = -4
+                        break
+                    st, conv1, _, _, ob = visit(s_, st)
+                    last_solve[s_] = solve_id
+                    own_big[s_] = ob
+                    all_ok = all_ok and conv1
+                nu += 1
+                converged = all_ok
+            stats["dd_outer"] = nu
         self.st = st
         ds = np.maximum(np.abs(st.sw - old.sw), np.abs(st.sg - old.sg))
         self.prev_supp = self._big(st.p - old.p, ds, st.sat != old.sat).astype(np.uint8)
