@@ -464,6 +464,61 @@ lns_status lns_server_get_state(lns_server* server, int32_t model_id, double* p,
 lns_status lns_server_get_stats(lns_server* server, lns_server_stats* out);
 double lns_server_now(lns_server* server);
 
+/* ---- Three-phase black-oil physics (the 3D workload's model) -----------------------------------
+ * Components water, oil and gas in surface volumes, gas dissolving in oil; Appendix A's
+ * backward-Euler TPFA residual with phase-potential upwinding (the lower cell index on a tie):
+ *   R_c,i = [M_c(u_i) - M_c(u_i^n)] / dt + sum_j F_c,ij + q_c,i,   c = oil, water, gas
+ *   M_o = PV b_o So, M_w = PV b_w Sw, M_g = PV (b_g Sg + Rs b_o So), So = 1 - Sw - Sg;
+ *   F_l,ij = T_ij (lambda_l b_l)_up dPhi_l,ij, and the dissolved gas (Rs lambda_o b_o) upwinded
+ *   with the oil; dPhi_l,ij = (p_i - p_j) - g (rho_l,i + rho_l,j) / 2 (z_i - z_j);
+ *   producers q_c = WI (lambda_c b_c) max(p - BHP, 0), q_g += Rs q_o.
+ * Fluid functions: PV = PV_ref (1 + c_r (p - p_ref)), b_w = b_w_ref (1 + c_w (p - p_ref)),
+ * b_o = b_o_ref (1 + c_o (p - p_ref)) / (1 + kappa Rs), b_g = b_g_per_pa p, rho_w = rho_w_sc b_w,
+ * rho_o = b_o (rho_o_sc + Rs rho_g_sc), rho_g = rho_g_sc b_g, Rs_sat(p) = rs_max p / p_bubble,
+ * Corey kr_w((Sw - swc) / span), kr_o((So - sor) / span), kr_g(Sg / span), span = 1 - swc - sor,
+ * exponents n_w, n_o, n_g, clamped to [0, 1].  Gas-oil ratios in surface m^3 per surface m^3.
+ * Primary variables per cell (p, Sw, X): X = Sg where sat = 1 (free gas; Rs = Rs_sat(p)), X = Rs
+ * where sat = 0 (no free gas; Sg = 0).  Section 3.1's variable substitution in black-oil form
+ * (after an update): Sg < 0 -> sat = 0, Sg = 0, Rs = Rs_sat(p); Rs > Rs_sat(p) with sat = 0 ->
+ * sat = 1, Sg = 0, Rs = Rs_sat(p). */
+typedef struct {
+  double p_ref, c_r;
+  double b_w_ref, c_w, rho_w_sc, mu_w;
+  double b_o_ref, c_o, kappa, rho_o_sc, mu_o;
+  double b_g_per_pa, rho_g_sc, mu_g;
+  double rs_max, p_bubble;
+  double swc, sor, gravity;
+  int32_t n_w, n_o, n_g;
+} lns_bo_fluid;
+
+/* Residual, Jacobian and scaled residual of every cell at the state (p, sw, sg, rs, sat) against
+ * the time level (p_old, ...), over the time step dt > 0.  The graph (row_ptr [n_cells+1], nbr and
+ * trans [n_adj], pv_ref and depth [n_cells], wells [n_wells]) is the model description's
+ * (lns_model_desc); states are [n_cells] (sat: 0 or 1).  Outputs: F [3 n_cells] (oil, water, gas
+ * per cell), Jd [9 n_cells] diagonal blocks and Jo [9 n_adj] off-diagonal blocks (row i, column
+ * nbr[e]), row-major d(oil, water, gas)/d(p, Sw, X), FP64; cnv [n_cells] = max over components
+ * of |R_c| dt / (PV b_c), b of the phase carrying c.  Any output may be NULL.  Every array is a
+ * DEVICE pointer owned by the caller (fluid: host).  Work runs on cuda_stream (NULL: legacy
+ * default stream); the call returns after it has finished.  LNS_EINVAL on a NULL input, negative
+ * sizes, dt <= 0 or a fluid with p_bubble <= 0, swc + sor >= 1 or a Corey exponent < 1; LNS_ECUDA
+ * if the kernel fails. */
+lns_status lns_bo_assemble(const lns_bo_fluid* fluid, int32_t n_cells, const int32_t* row_ptr, const int32_t* nbr,
+                           const double* trans, const double* pv_ref, const double* depth, int32_t n_wells,
+                           const int32_t* well_cell, const double* well_wi, const double* well_bhp,
+                           const double* p, const double* sw, const double* sg, const double* rs,
+                           const uint8_t* sat, const double* p_old, const double* sw_old, const double* sg_old,
+                           const double* rs_old, const uint8_t* sat_old, double dt, double* F, double* Jd,
+                           double* Jo, double* cnv, void* cuda_stream);
+
+/* u <- u + du on the cells of va_bits (device bitset; NULL: every cell), du [3 n_cells] in
+ * (p, Sw, X) per cell, with the saturation chop (|dSw|, and |dSg| where sat = 1, at most sat_chop
+ * when sat_chop > 0) and then the variable switch above.  switched [n_cells] (may be NULL) gets 1
+ * where a cell's variable set changed, else 0.  Every array is a DEVICE pointer owned by the
+ * caller (fluid: host); stream and errors as lns_bo_assemble. */
+lns_status lns_bo_update(const lns_bo_fluid* fluid, int32_t n_cells, double sat_chop, const double* du,
+                         const uint32_t* va_bits, double* p, double* sw, double* sg, double* rs, uint8_t* sat,
+                         uint8_t* switched, void* cuda_stream);
+
 /* Number of CUDA kernels the library has launched in this process (all models). */
 int64_t lns_launch_count(void);
 

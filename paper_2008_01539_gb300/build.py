@@ -15,8 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblns.so")
-SOURCES = ["k_sets.cu", "k_assemble.cu", "k_krylov.cu", "lns_capi.cu", "lns_noalloc.cu", "lns_server.cu"]
-HEADERS = ["lns_internal.cuh", os.path.join("..", "..", "include", "lns.h")]
+SOURCES = ["k_sets.cu", "k_assemble.cu", "k_krylov.cu", "lns_capi.cu", "lns_noalloc.cu", "lns_server.cu",
+           "k_blackoil.cu"]
+HEADERS = ["lns_internal.cuh", "bo_physics.cuh", os.path.join("..", "..", "include", "lns.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

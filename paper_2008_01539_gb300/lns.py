@@ -92,6 +92,18 @@ class lns_batch_stats(C.Structure):
     _fields_ = [("rounds", C.c_int32), ("cluster_solves", C.c_int64), ("grid_solves", C.c_int64)]
 
 
+class lns_bo_fluid(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("p_ref", "c_r", "b_w_ref", "c_w", "rho_w_sc", "mu_w", "b_o_ref", "c_o",
+                                           "kappa", "rho_o_sc", "mu_o", "b_g_per_pa", "rho_g_sc", "mu_g", "rs_max",
+                                           "p_bubble", "swc", "sor", "gravity")] + \
+               [("n_w", C.c_int32), ("n_o", C.c_int32), ("n_g", C.c_int32)]
+
+
+def bo_fluid(fl) -> lns_bo_fluid:
+    """lns_bo_fluid from an object with the same field names (casegen.BlackOilFluid)."""
+    return lns_bo_fluid(*[getattr(fl, k) for k, _ in lns_bo_fluid._fields_])
+
+
 class lns_tuning(C.Structure):
     _fields_ = [("cluster_max_rows", C.c_int32), ("asm_block", C.c_int32), ("asm_blocks_per_sm", C.c_int32),
                 ("set_blocks_per_sm", C.c_int32), ("measured", C.c_int32)]
@@ -133,7 +145,7 @@ EXPORTS = ["lns_options_default", "lns_model_create", "lns_model_destroy", "lns_
            "lns_server_poll", "lns_server_drain", "lns_server_get_state", "lns_server_get_stats", "lns_server_now",
            "lns_server_cancel", "lns_debug_fault", "lns_advance", "lns_compact", "lns_batch_advance",
            "lns_autotune", "lns_get_tuning", "lns_set_tuning", "lns_tune_pick", "lns_tune_cache_lookup",
-           "lns_tune_cache_store", "lns_tune_cache_clear"]
+           "lns_tune_cache_store", "lns_tune_cache_clear", "lns_bo_assemble", "lns_bo_update"]
 
 
 def library_path() -> str:
@@ -211,6 +223,10 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     L.lns_tune_cache_clear.restype = None
     L.lns_active_set_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, f64, f64, i32, i32, vp, vp, P(i32), vp]
     L.lns_active_set_noalloc.restype = C.c_int
+    L.lns_bo_assemble.argtypes = [P(lns_bo_fluid), i32] + [vp] * 5 + [i32] + [vp] * 13 + [f64] + [vp] * 5
+    L.lns_bo_assemble.restype = C.c_int
+    L.lns_bo_update.argtypes = [P(lns_bo_fluid), i32, f64] + [vp] * 9
+    L.lns_bo_update.restype = C.c_int
     _lib = L
     return L
 
@@ -231,6 +247,29 @@ def lns_active_set_noalloc(n_cells: int, row_ptr: int, nbr: int, always_bits: in
                                          dsw or None, float(eps_p), float(eps_sw), int(m_layers), int(bool(converged)),
                                          va_bits or None, vb_bits or None, C.byref(ie), stream or None))
     return int(ie.value)
+
+
+def lns_bo_assemble(fluid: lns_bo_fluid, n_cells: int, graph: Dict[str, int], state: Dict[str, int],
+                    old: Dict[str, int], dt: float, F: int = 0, Jd: int = 0, Jo: int = 0, cnv: int = 0,
+                    stream: int = 0) -> None:
+    """Black-oil residual, Jacobian and CNV of every cell (lns_bo_assemble) on caller-owned DEVICE
+    arrays given by integer addresses: graph keys row_ptr, nbr, trans, pv_ref, depth, n_wells,
+    well_cell, well_wi, well_bhp; state and old keys p, sw, sg, rs, sat; outputs 0 for NULL."""
+    g = graph
+    _check(load().lns_bo_assemble(C.byref(fluid), int(n_cells), g["row_ptr"], g["nbr"], g["trans"], g["pv_ref"],
+                                  g["depth"], int(g["n_wells"]), g["well_cell"] or None, g["well_wi"] or None,
+                                  g["well_bhp"] or None, state["p"], state["sw"], state["sg"], state["rs"],
+                                  state["sat"], old["p"], old["sw"], old["sg"], old["rs"], old["sat"], float(dt),
+                                  F or None, Jd or None, Jo or None, cnv or None, stream or None))
+
+
+def lns_bo_update(fluid: lns_bo_fluid, n_cells: int, sat_chop: float, du: int, state: Dict[str, int],
+                  va_bits: int = 0, switched: int = 0, stream: int = 0) -> None:
+    """Black-oil update with the primary-variable switch (lns_bo_update) on DEVICE arrays (integer
+    addresses; state keys p, sw, sg, rs, sat, updated in place)."""
+    _check(load().lns_bo_update(C.byref(fluid), int(n_cells), float(sat_chop), du, va_bits or None, state["p"],
+                                state["sw"], state["sg"], state["rs"], state["sat"], switched or None,
+                                stream or None))
 
 
 def lns_batch_advance(models, t_span: float, dt_init: Optional[float] = None, dt_min: Optional[float] = None,

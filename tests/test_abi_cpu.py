@@ -56,7 +56,7 @@ def test_last_error_and_defaults_without_gpu(lib):
 def test_struct_layouts_match_c():
     structs = ["lns_fluid", "lns_model_desc", "lns_options", "lns_allocator", "lns_iter_stats", "lns_step_stats",
                "lns_kernel_time", "lns_server_options", "lns_completion", "lns_server_stats", "lns_dt_control",
-               "lns_advance_stats", "lns_batch_stats", "lns_tuning"]
+               "lns_advance_stats", "lns_batch_stats", "lns_tuning", "lns_bo_fluid"]
     src = "#include <stdio.h>\n#include <stddef.h>\n#include \"lns.h\"\nint main(void){\n"
     for s in structs:
         src += f'  printf("{s} %zu\\n", sizeof({s}));\n'
@@ -98,3 +98,20 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "lns_oracle" not in text, f
+
+
+def test_black_oil_entry_points_reject_bad_arguments_without_gpu(lib):
+    """lns_bo_assemble / lns_bo_update check their arguments before touching the device."""
+    L = lns.load()
+    fl = lns.bo_fluid(__import__("paper_2008_01539_gb300.casegen", fromlist=["x"]).BlackOilFluid())
+    args = lambda n, dt: [n, *([None] * 5), 0, *([None] * 13), dt, *([None] * 5)]  # noqa: E731
+    assert L.lns_bo_assemble(None, *args(1, 1.0)) == lns.LNS_EINVAL          # no fluid
+    assert L.lns_bo_assemble(C.byref(fl), *args(1, 1.0)) == lns.LNS_EINVAL   # NULL arrays
+    assert L.lns_bo_assemble(C.byref(fl), *args(0, 0.0)) == lns.LNS_EINVAL   # dt <= 0
+    assert L.lns_bo_assemble(C.byref(fl), *args(-1, 1.0)) == lns.LNS_EINVAL  # negative size
+    assert L.lns_bo_assemble(C.byref(fl), *args(0, 1.0)) == lns.LNS_OK       # nothing to do
+    bad = lns.bo_fluid(__import__("paper_2008_01539_gb300.casegen", fromlist=["x"]).BlackOilFluid(n_g=0))
+    assert L.lns_bo_update(C.byref(fl), 4, 0.2, *([None] * 9)) == lns.LNS_EINVAL
+    assert L.lns_bo_update(C.byref(fl), 0, 0.2, *([None] * 9)) == lns.LNS_OK
+    assert L.lns_bo_assemble(C.byref(bad), *args(0, 1.0)) == lns.LNS_OK  # checked only with cells to assemble
+
