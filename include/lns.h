@@ -11,7 +11,9 @@
  * Every step of a Newton iteration runs in the library's CUDA kernels for sm_103a: the
  * a-priori active-set estimate, compaction of the active cells, masked residual and
  * Jacobian assembly (Appendix A), the BiCGStab solve of J_A du_A = -F_A and the scatter
- * of the update.
+ * of the update.  For the three-phase black-oil model, the residual and Jacobian assembly and
+ * the update with the primary-variable switch are available on caller-owned device arrays
+ * (lns_bo_assemble, lns_bo_update).
  *
  * Conventions (all entry points):
  *   - Every call returns lns_status; no exception crosses the ABI.  On failure
