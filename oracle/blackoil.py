@@ -204,30 +204,49 @@ def cell_props(fl, pv_ref, st: State) -> Dict[str, D]:
 EQ = ("o", "w", "g")  # equation order: oil, water, gas
 
 
-def assemble(bo, st: State, old: State, dt: float) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
-    """Full-domain residual F (n, 3) and Jacobian blocks: diagonal (n, 3, 3) and off-diagonal per
-    adjacency entry (n_adj, 3, 3) (row i = the entry's row, column nbr[e]), in (p, Sw, X) of the
-    current variable sets."""
+def _sub(st: State, idx: np.ndarray) -> State:
+    return State(st.p[idx], st.sw[idx], st.sg[idx], st.rs[idx], st.sat[idx])
+
+
+def assemble_cells(bo, st: State, old: State, dt: float, cells) -> Tuple[np.ndarray, np.ndarray, np.ndarray,
+                                                                           np.ndarray]:
+    """The rows of the given cells (ascending or not, no repeats): residual F (m, 3), diagonal blocks
+    (m, 3, 3), the off-diagonal blocks of their adjacency entries (k, 3, 3) and those entries'
+    indices e (k,) in CSR order of the given cells (row cells[i] for the entries of row i, column
+    nbr[e]), in (p, Sw, X) of the current variable sets.  Only the given cells and their
+    neighbours are evaluated, so a sample of rows of a large model costs little."""
     c, fl = bo.case, bo.fluid
     n = c.n
-    q = cell_props(fl, c.pv_ref, st)
-    qn = cell_props(fl, c.pv_ref, old)
-    F = np.zeros((n, 3))
-    Jd = np.zeros((n, 3, 3))
+    cells = np.asarray(cells, dtype=np.int64)
+    m = cells.shape[0]
+    row_ptr = np.asarray(c.row_ptr, dtype=np.int64)
+    cnt = row_ptr[cells + 1] - row_ptr[cells]
+    first = np.cumsum(cnt) - cnt
+    e_idx = np.repeat(row_ptr[cells], cnt) + (np.arange(int(cnt.sum())) - np.repeat(first, cnt))
+    loc_row = np.repeat(np.arange(m), cnt)
+    rows = cells[loc_row]
+    cols = np.asarray(c.nbr, dtype=np.int64)[e_idx]
+    need = np.unique(np.concatenate([cells, cols]))
+    at = -np.ones(n, np.int64)
+    at[need] = np.arange(need.shape[0])
+    q = cell_props(fl, c.pv_ref[need], _sub(st, need))
+    qn = cell_props(fl, c.pv_ref[cells], _sub(old, cells))
+    own = at[cells]
+    F = np.zeros((m, 3))
+    Jd = np.zeros((m, 3, 3))
     for r, comp in enumerate(EQ):
-        acc = (q["mass_" + comp] - qn["mass_" + comp].v) / dt
+        acc = (q["mass_" + comp][own] - qn["mass_" + comp].v) / dt
         F[:, r] += acc.v
         Jd[:, r, :] += acc.d
-    rows = np.repeat(np.arange(n), np.diff(c.row_ptr))
-    cols = np.asarray(c.nbr, dtype=np.int64)
-    T = np.asarray(c.trans, dtype=np.float64)
+    T = np.asarray(c.trans, dtype=np.float64)[e_idx]
     dz = c.depth[rows] - c.depth[cols]
     g = fl.gravity
-    Jo = np.zeros((cols.shape[0], 3, 3))
+    Jo = np.zeros((e_idx.shape[0], 3, 3))
+    ai, aj = at[rows], at[cols]
 
     def face(name):
         a = q[name]
-        return widen(a[rows], True), widen(a[cols], False)
+        return widen(a[ai], True), widen(a[aj], False)
 
     Pi, Pj = face("P")
     up_oil = None
@@ -241,25 +260,40 @@ def assemble(bo, st: State, old: State, dt: float) -> Tuple[np.ndarray, np.ndarr
         if ph == "o":
             up_oil, dphi_oil = up, dphi
     # dissolved gas travels with the oil, upwinded with it
-    rmi, rmj = widen((q["RS"] * q["mob_o"])[rows], True), widen((q["RS"] * q["mob_o"])[cols], False)
+    rs_mob = q["RS"] * q["mob_o"]
+    rmi, rmj = widen(rs_mob[ai], True), widen(rs_mob[aj], False)
     flux["dg"] = T * where(up_oil, rmi, rmj) * dphi_oil
     for r, comp in enumerate(EQ):
         f = flux[comp] if comp != "g" else flux["g"] + flux["dg"]
-        np.add.at(F[:, r], rows, f.v)
-        np.add.at(Jd[:, r, :], rows, f.d[:, :3])
+        np.add.at(F[:, r], loc_row, f.v)
+        np.add.at(Jd[:, r, :], loc_row, f.d[:, :3])
         Jo[:, r, :] = f.d[:, 3:]
     # producers at fixed bottom-hole pressure
+    pos = -np.ones(n, np.int64)
+    pos[cells] = np.arange(m)
     for w in range(c.well_cell.shape[0]):
         i = int(c.well_cell[w])
-        dpw = q["P"][[i]] - float(c.well_bhp[w])
+        if pos[i] < 0:
+            continue
+        k = int(pos[i])
+        j = [int(at[i])]
+        dpw = q["P"][j] - float(c.well_bhp[w])
         if dpw.v[0] <= 0.0:
             continue
         wi = float(c.well_wi[w])
-        qo = wi * q["mob_o"][[i]] * dpw
-        terms = dict(o=qo, w=wi * q["mob_w"][[i]] * dpw, g=wi * q["mob_g"][[i]] * dpw + q["RS"][[i]] * qo)
+        qo = wi * q["mob_o"][j] * dpw
+        terms = dict(o=qo, w=wi * q["mob_w"][j] * dpw, g=wi * q["mob_g"][j] * dpw + q["RS"][j] * qo)
         for r, comp in enumerate(EQ):
-            F[i, r] += terms[comp].v[0]
-            Jd[i, r, :] += terms[comp].d[0]
+            F[k, r] += terms[comp].v[0]
+            Jd[k, r, :] += terms[comp].d[0]
+    return F, Jd, Jo, e_idx
+
+
+def assemble(bo, st: State, old: State, dt: float) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Full-domain residual F (n, 3) and Jacobian blocks: diagonal (n, 3, 3) and off-diagonal per
+    adjacency entry (n_adj, 3, 3) (row i = the entry's row, column nbr[e]), in (p, Sw, X) of the
+    current variable sets."""
+    F, Jd, Jo, _ = assemble_cells(bo, st, old, dt, np.arange(bo.case.n))
     return F, Jd, Jo
 
 
@@ -267,9 +301,14 @@ def residual(bo, st: State, old: State, dt: float) -> np.ndarray:
     return assemble(bo, st, old, dt)[0]
 
 
-def cnv(bo, st: State, F: np.ndarray, dt: float) -> np.ndarray:
-    """CNV_i = max over components of |R_c,i| dt / (PV_i b_c,i) (b of the phase carrying c)."""
-    q = cell_props(bo.fluid, bo.case.pv_ref, st)
+def cnv(bo, st: State, F: np.ndarray, dt: float, cells=None) -> np.ndarray:
+    """CNV_i = max over components of |R_c,i| dt / (PV_i b_c,i) (b of the phase carrying c); F holds
+    the rows of ``cells`` (default: every cell)."""
+    if cells is None:
+        q = cell_props(bo.fluid, bo.case.pv_ref, st)
+    else:
+        cells = np.asarray(cells, dtype=np.int64)
+        q = cell_props(bo.fluid, bo.case.pv_ref[cells], _sub(st, cells))
     pv = q["PV"].v
     scale = np.stack([q["BO"].v, q["BW"].v, q["BG"].v], axis=1) * pv[:, None]
     return np.max(np.abs(F) * dt / scale, axis=1)

@@ -150,3 +150,30 @@ def test_bo_update_matches_oracle_bit_for_bit(chop, masked):
     assert np.array_equal(sw_d.cpu().numpy().astype(bool), ref_sw)
     for k, a in (("p", ref.p), ("sw", ref.sw), ("sg", ref.sg), ("rs", ref.rs), ("sat", ref.sat)):
         assert np.array_equal(keep[k].cpu().numpy(), a), k
+
+
+def test_bo_assemble_full_size_3d_sampled():
+    """The 3D workload's geometry with its black-oil physics (1,064,029 cells, 6.2M CSR entries; 8,313
+    blocks): the whole model assembled on the device, 20,000 random rows plus the producers' rows
+    recomputed by the oracle one by one (its full assembly takes minutes) and compared as above."""
+    import torch
+
+    bo = cg.config2_blackoil()
+    st, old = _mixed(bo, 5), _mixed(bo, 6)
+    dt = 5.0 * cg.DAY
+    F, Jd, Jo, cv = _assemble_gpu(bo, st, old, dt)
+    rng = np.random.default_rng(7)
+    cells = np.unique(np.concatenate([rng.choice(bo.n, 20000, replace=False),
+                                      bo.case.well_cell.astype(np.int64)]))
+    Fr, Jdr, Jor, e = B.assemble_cells(bo, st, old, dt, cells)
+    cvr = B.cnv(bo, st, Fr, dt, cells)
+    F, Jd, Jo, cv = F[cells], Jd[cells], Jo[e], cv[cells]
+    for r in range(3):
+        assert np.max(np.abs(F[:, r] - Fr[:, r])) <= 1e-11 * np.max(np.abs(Fr[:, r])), ("F", r)
+        for k in range(3):
+            for J, Jr, name in ((Jd, Jdr, "Jd"), (Jo, Jor, "Jo")):
+                sc = np.max(np.abs(Jr[:, r, k]))
+                assert np.max(np.abs(J[:, r, k] - Jr[:, r, k])) <= 1e-11 * sc + 1e-300, (name, r, k)
+    assert np.max(np.abs(cv - cvr)) <= 1e-11 * np.max(cvr)
+    torch.cuda.synchronize()
+
